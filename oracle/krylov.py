@@ -1,0 +1,311 @@
+"""GMRES drivers of the oracle, FP64, restated from the paper (test infrastructure only).
+
+* ``gmres_cgs2``   standard restarted GMRES(m), Arnoldi with classical
+                   Gram-Schmidt twice (the "GMRES + CGS2" arm of Table 3, §I).
+* ``sstep_gmres``  s-step GMRES (Fig. 1, §III) with BlkOrth one of
+                   ``two_stage`` (§V, Fig. 5), ``bcgs_pip2`` (§IV-C, Fig. 4b) or
+                   ``bcgs2_cholqr2`` (§IV-B, Fig. 2b).
+
+The paper's Fig. 1 pseudocode is not in its source; the driver below restates
+the method from §III and §V:
+
+* A restart cycle starts from q_1 = r / ||r||, r = b - A x.
+* Each s-step block runs the matrix powers kernel (MPK, §I, §III) from the last
+  column of the previous block (for the two-stage scheme, the pre-processed
+  column Q^_{j-1}; §V), producing s new vectors, then block-orthogonalizes them.
+* MPK uses the monomial basis (§VI uses monomial throughout) with a power-of-two
+  scale sigma, v_{i+1} = (A v_i - theta_i v_i) / sigma; sigma is exact in
+  binary floating point, theta = 0 is the plain monomial basis.
+* Convergence is tested where the basis becomes orthonormal: after each big
+  panel (two-stage) or block (one-stage schemes); Table 2 and Table 4 report
+  iteration counts that are multiples of the big-panel width.
+* The upper Hessenberg H with A Q_{1:k} = Q_{1:k+1} H is recovered from the
+  R factors (``hessenberg_columns``), then the least-squares problem
+  min ||g_0 e_1 - H y|| is solved with Givens rotations.
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+import scipy.sparse as sp
+
+from . import blockortho as bo
+
+STATUS_OK = 0
+STATUS_MAXIT = 1
+STATUS_BREAKDOWN = -4
+STATUS_NAN = -5
+
+
+def as_operator(A):
+    """CSR object from ``synth`` (n, rowptr, colind, vals) -> scipy CSR matrix."""
+    if sp.issparse(A):
+        return A.tocsr()
+    return sp.csr_matrix((A.vals, A.colind, A.rowptr), shape=(A.n, A.n))
+
+
+def mpk_sigma(A) -> float:
+    """Power-of-two scale for the monomial basis: 2^floor(log2 ||A||_inf)."""
+    M = as_operator(A)
+    rs = np.asarray(abs(M).sum(axis=1)).ravel()
+    top = float(rs.max()) if rs.size else 1.0
+    if not (top > 0.0):
+        return 1.0
+    return float(2.0 ** math.floor(math.log2(top)))
+
+
+def mpk(M, v: np.ndarray, s: int, sigma: float, theta=None) -> np.ndarray:
+    """Matrix powers kernel, standard (non communication-avoiding) form (§III):
+    s sparse matrix-vector products in sequence, w_1 = (A v - theta_0 v)/sigma,
+    w_i = (A w_{i-1} - theta_{i-1} w_{i-1})/sigma.  Returns the n x s block."""
+    n = v.shape[0]
+    W = np.zeros((n, s))
+    prev = v
+    for i in range(s):
+        y = M @ prev
+        if theta is not None and theta[i] != 0.0:
+            y = y - theta[i] * prev
+        W[:, i] = y / sigma
+        prev = W[:, i]
+    return W
+
+
+class Givens:
+    """Incremental QR of an upper Hessenberg matrix by Givens rotations and the
+    right-hand side g (standard GMRES least squares, Saad and Schultz 1986)."""
+
+    def __init__(self, m: int, g0: float):
+        self.m = m
+        self.Rg = np.zeros((m + 1, m))
+        self.cs = np.zeros(m)
+        self.sn = np.zeros(m)
+        self.g = np.zeros(m + 1)
+        self.g[0] = g0
+        self.k = 0
+
+    def add_column(self, h: np.ndarray):
+        """Append column k of H (entries 0..k+1) and rotate it."""
+        k = self.k
+        col = np.array(h[: k + 2], dtype=np.float64, copy=True)
+        for i in range(k):
+            a, b = col[i], col[i + 1]
+            col[i] = self.cs[i] * a + self.sn[i] * b
+            col[i + 1] = -self.sn[i] * a + self.cs[i] * b
+        a, b = col[k], col[k + 1]
+        r = math.hypot(a, b)
+        if r == 0.0:
+            c, s = 1.0, 0.0
+        else:
+            c, s = a / r, b / r
+        self.cs[k], self.sn[k] = c, s
+        col[k] = r
+        col[k + 1] = 0.0
+        self.Rg[: k + 2, k] = col
+        gk = self.g[k]
+        self.g[k] = c * gk
+        self.g[k + 1] = -s * gk
+        self.k = k + 1
+
+    def residual(self) -> float:
+        return abs(self.g[self.k])
+
+    def solve(self) -> np.ndarray:
+        k = self.k
+        y = np.zeros(k)
+        for i in reversed(range(k)):
+            y[i] = (self.g[i] - np.dot(self.Rg[i, i + 1:k], y[i + 1:k])) / self.Rg[i, i]
+        return y
+
+
+def gmres_cgs2(A, b, x0=None, m=60, tol=1e-8, max_restarts=1000):
+    """Standard restarted GMRES(m) with CGS2 Arnoldi (Table 3 "GMRES + CGS2").
+    Tests convergence every iteration.  Returns (x, info dict)."""
+    M = as_operator(A)
+    n = b.shape[0]
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    bnorm = np.linalg.norm(b)
+    iters = 0
+    hist = []
+    status = STATUS_MAXIT
+    restarts = 0
+    for cyc in range(max_restarts):
+        r = b - M @ x
+        beta = np.linalg.norm(r)
+        hist.append(beta / bnorm)
+        if beta / bnorm <= tol:
+            status = STATUS_OK
+            break
+        restarts += 1
+        Q = np.zeros((n, m + 1))
+        Q[:, 0] = r / beta
+        gv = Givens(m, beta)
+        H = np.zeros((m + 1, m))
+        k = 0
+        for j in range(m):
+            w = M @ Q[:, j]
+            h1 = Q[:, : j + 1].T @ w
+            w = w - Q[:, : j + 1] @ h1
+            h2 = Q[:, : j + 1].T @ w
+            w = w - Q[:, : j + 1] @ h2
+            h = h1 + h2
+            hn = np.linalg.norm(w)
+            H[: j + 1, j] = h
+            H[j + 1, j] = hn
+            if hn > 0:
+                Q[:, j + 1] = w / hn
+            gv.add_column(H[: j + 2, j])
+            iters += 1
+            k = j + 1
+            if gv.residual() / bnorm <= tol or hn == 0:
+                break
+        y = gv.solve()
+        x = x + Q[:, :k] @ y
+    else:
+        r = b - M @ x
+        hist.append(np.linalg.norm(r) / bnorm)
+    return x, dict(status=status, iters=iters, restarts=restarts, relres=hist[-1], history=hist)
+
+
+def hessenberg_columns(Rfin, C, start_final, s, sigma, theta, c_lo, c_hi, H):
+    """Columns c_lo..c_hi-1 of the upper Hessenberg H with A Q_{1:k} = Q_{1:k+1} H.
+
+    SpMV number c (0-based) reads input y_c and writes raw column c+1, with
+    A y_c = sigma w_{c+1} + theta_c y_c.  In final (orthonormal) coordinates:
+      a_c = e_c        if c starts a block whose start column was already final,
+      a_c = C[:, c]    if c starts a block from a pre-processed column q^_c,
+      a_c = Rfin[:, c] otherwise (y_c is the raw MPK output w_c);
+      b_c = sigma Rfin[:, c+1] + theta_c a_c.
+    With A_k = [a_0..a_{k-1}] upper triangular and B_k = [b_0..b_{k-1}],
+    H = B_k A_k^{-1}, solved one column at a time (H A = B)."""
+    mp1 = Rfin.shape[0]
+    for c in range(c_lo, c_hi):
+        if c % s == 0:
+            a = np.zeros(mp1)
+            if start_final[c]:
+                a[c] = 1.0
+            else:
+                a[:] = C[:, c]
+        else:
+            a = Rfin[:, c].copy()
+        bcol = sigma * Rfin[:, c + 1] + (theta[c % s] * a if theta is not None else 0.0)
+        acc = bcol.copy()
+        for i in range(c):
+            acc -= H[:, i] * a[i]
+        H[:, c] = acc / a[c]
+    return H
+
+
+def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=1000,
+                ortho="two_stage", sigma=None, theta=None, return_basis=False):
+    """s-step GMRES (Fig. 1, §III) with the chosen block orthogonalization.
+
+    ``panel`` is the second step size s^ of the two-stage scheme (§V); it must
+    satisfy s | s^ | m.  ``ortho`` in {"two_stage", "bcgs_pip2", "bcgs2_cholqr2"}.
+    Returns (x, info dict) with status, iteration count (SpMVs inside restart
+    cycles), restarts, the explicit relative residual and, when
+    ``return_basis``, the last cycle's Q, H and g0 (for Arnoldi-relation tests)."""
+    M = as_operator(A)
+    n = b.shape[0]
+    if panel is None:
+        panel = m
+    if ortho != "two_stage":
+        panel = s
+    if m % s or panel % s or m % panel:
+        raise ValueError("need s | panel | m")
+    sig = mpk_sigma(A) if sigma is None else float(sigma)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    bnorm = np.linalg.norm(b)
+    iters = 0
+    restarts = 0
+    hist = []
+    status = STATUS_MAXIT
+    last = {}
+    err_where = None
+    for cyc in range(max_restarts):
+        r = b - M @ x
+        beta = np.linalg.norm(r)
+        hist.append(beta / bnorm)
+        if not np.isfinite(beta):
+            status = STATUS_NAN
+            break
+        if beta / bnorm <= tol:
+            status = STATUS_OK
+            break
+        restarts += 1
+        Q = np.zeros((n, m + 1))
+        Q[:, 0] = r / beta
+        Rhat = np.zeros((m + 1, m + 1))
+        Rhat[0, 0] = 1.0
+        Rfin = np.zeros((m + 1, m + 1))
+        C = np.zeros((m + 1, m + 1))
+        final = np.zeros(m + 1, dtype=bool)
+        start_final = np.zeros(m + 1, dtype=bool)
+        H = np.zeros((m + 1, m))
+        if ortho == "two_stage":
+            lo, hi = 0, panel          # first big panel: columns 0..s^ (s^+1 vectors)
+        else:
+            final[0] = True            # q_1 = r/||r|| is already orthonormal
+            C[0, 0] = 1.0
+            Rfin[0, 0] = 1.0
+        gv = None
+        k_used = 0
+        done = False
+        try:
+            for j in range(m // s):
+                st = s * j
+                start_final[st] = final[st]
+                W = mpk(M, Q[:, st], s, sig, theta)
+                cols = slice(st + 1, st + s + 1)
+                if ortho == "two_stage":
+                    Qh, P, T = bo.stage1(Q[:, : st + 1], W, f"cycle{cyc}/block{j}")
+                    Q[:, cols] = Qh
+                    Rhat[: st + 1, cols] = P
+                    Rhat[cols, cols] = T
+                    t = st + s
+                    if t < hi:
+                        continue
+                    Qn, P2, T2 = bo.stage2(Q[:, :lo], Q[:, lo:t + 1], f"cycle{cyc}/stage2@{t}")
+                    Q[:, lo:t + 1] = Qn
+                    C[:lo, lo:t + 1] = P2
+                    C[lo:t + 1, lo:t + 1] = T2
+                    final[lo:t + 1] = True
+                    top, diag = bo.combine_two_stage(Rhat[:lo, lo:t + 1], Rhat[lo:t + 1, lo:t + 1], P2, T2)
+                    Rfin[:lo, lo:t + 1] = top
+                    Rfin[lo:t + 1, lo:t + 1] = diag
+                    c_lo = max(lo - 1, 0)
+                    lo, hi = t + 1, t + panel
+                else:
+                    fn = bo.bcgs_pip2 if ortho == "bcgs_pip2" else bo.bcgs2_cholqr2
+                    Qj, P, T = fn(Q[:, : st + 1], W, f"cycle{cyc}/block{j}")
+                    Q[:, cols] = Qj
+                    Rfin[: st + 1, cols] = P
+                    Rfin[cols, cols] = T
+                    C[st + 1:st + s + 1, st + 1:st + s + 1] = np.eye(s)
+                    final[cols] = True
+                    t = st + s
+                    c_lo = st
+                if gv is None:
+                    gv = Givens(m, beta * C[0, 0])
+                hessenberg_columns(Rfin, C, start_final, s, sig, theta, c_lo, t, H)
+                for c in range(c_lo, t):
+                    gv.add_column(H[: c + 2, c])
+                k_used = t
+                if gv.residual() / bnorm <= tol:
+                    done = True
+                    break
+        except bo.Breakdown as e:
+            status = STATUS_BREAKDOWN
+            err_where = str(e)
+            break
+        y = gv.solve()
+        x = x + Q[:, :k_used] @ y
+        iters += k_used
+        last = dict(Q=Q, H=H, g0=beta * C[0, 0], k=k_used, Rfin=Rfin, C=C)
+    else:
+        r = b - M @ x
+        hist.append(np.linalg.norm(r) / bnorm)
+    info = dict(status=status, iters=iters, restarts=restarts, relres=hist[-1], history=hist,
+                sigma=sig, where=err_where)
+    if return_basis:
+        info.update(last)
+    return x, info

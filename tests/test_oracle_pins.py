@@ -1,0 +1,323 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these compare the oracle with itself: each check is a closed form, a
+library routine for a special case, exact rational arithmetic, a bound printed
+in the paper, or a uniqueness property of the QR factorization.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import blockortho as bo, krylov as kr, checks
+
+EPS = np.finfo(np.float64).eps
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _sign_fixed_qr(V):
+    q, r = np.linalg.qr(V)
+    sg = np.where(np.diag(r) < 0, -1.0, 1.0)
+    return q * sg, r * sg[:, None]
+
+
+# ---------------------------------------------------------------- Cholesky
+def test_chol_upper_matches_lapack():
+    g = synth.rng(11)
+    for c in (1, 5, 11, 61):
+        B = g.standard_normal((3 * c, c))
+        G = B.T @ B
+        R, info = bo.chol_upper(G)
+        assert info == 0
+        L = np.linalg.cholesky(G)
+        assert np.allclose(R, L.T, rtol=1e-12, atol=1e-12 * np.abs(L).max())
+        assert np.all(np.diag(R) > 0)
+        assert np.allclose(np.triu(R), R)
+
+
+def test_chol_upper_reports_first_bad_pivot():
+    G = np.diag([4.0, 1.0, -1.0, 2.0])
+    _, info = bo.chol_upper(G)
+    assert info == 3
+    G = np.array([[1.0, 1.0], [1.0, 1.0]])  # singular: second pivot 0
+    _, info = bo.chol_upper(G)
+    assert info == 2
+    _, info = bo.chol_upper(np.array([[np.nan]]))
+    assert info == 1
+
+
+# ---------------------------------------------------------------- Gram
+def test_gram_of_pip_is_exact_dot_product_up_to_rounding():
+    """The single reduction [Q, V]^T V of BCGS-PIP equals the exact rational
+    dot products to within the classic n*eps*|x|.|y| bound."""
+    g = synth.rng(12)
+    n, k, s = 37, 3, 4
+    Q = g.standard_normal((n, k))
+    V = g.standard_normal((n, s))
+    X = np.concatenate([Q, V], axis=1)
+    ex = checks.exact_gram(X, V)
+    got = X.T @ V
+    bound = n * EPS * (np.abs(X).T @ np.abs(V))
+    assert np.all(np.abs(got - ex) <= bound)
+
+
+# ---------------------------------------------------------------- QR checkers
+def test_hhqr_matches_lapack_qr():
+    V = synth.rng(13).standard_normal((200, 9))
+    Q, R = bo.hhqr(V)
+    q, r = _sign_fixed_qr(V)
+    assert np.allclose(Q, q, atol=1e-13)
+    assert np.allclose(R, r, atol=1e-12)
+
+
+def test_cholqr_unique_qr_with_positive_diagonal():
+    """QR with a positive R diagonal is unique (Fig. 1 caption), so CholQR of a
+    well-conditioned block equals Householder QR (LAPACK)."""
+    V = synth.rng(14).standard_normal((500, 6))
+    Q, R = bo.cholqr(V)
+    q, r = _sign_fixed_qr(V)
+    assert np.allclose(R, r, rtol=0, atol=1e-12 * np.abs(r).max())
+    assert np.allclose(Q @ R, V, atol=1e-12)
+    assert checks.orth_error(Q)[0] < 1e-14
+
+
+def test_bcgs_pip_equals_qr_of_concatenation():
+    """BCGS-PIP of V against an orthonormal Q returns the trailing block column
+    of the (unique) QR of [Q, V] (Fig. 4a)."""
+    g = synth.rng(15)
+    n, k, s = 400, 7, 5
+    Q, _ = _sign_fixed_qr(g.standard_normal((n, k)))
+    V = g.standard_normal((n, s))
+    Qh, P, T = bo.bcgs_pip(Q, V)
+    qq, rr = _sign_fixed_qr(np.concatenate([Q, V], axis=1))
+    # R of [Q, V] is [[I, P], [0, T]] up to the rounding of Q's orthonormality
+    assert np.allclose(rr[:k, k:], P, atol=1e-13)
+    assert np.allclose(rr[k:, k:], T, atol=1e-13)
+    assert np.allclose(qq[:, k:], Qh, atol=1e-12)
+    assert np.allclose(Q @ P + Qh @ T, V, atol=1e-13)
+
+
+def test_bcgs_pip2_without_previous_blocks_is_cholqr2():
+    """§IV-C: with no previous blocks BCGS-PIP2 is CholQR2."""
+    V = synth.rng(16).standard_normal((300, 6))
+    Qa, Pa, Ta = bo.bcgs_pip2(np.zeros((300, 0)), V)
+    Qb, Rb = bo.cholqr2(V)
+    assert Pa.shape == (0, 6)
+    assert np.allclose(Ta, Rb, atol=1e-13)
+    assert np.allclose(Qa, Qb, atol=1e-13)
+
+
+@pytest.mark.parametrize("fn", [bo.bcgs_pip2, bo.bcgs2_cholqr2])
+def test_block_schemes_give_the_unique_qr(fn):
+    g = synth.rng(17)
+    n, k, s = 300, 6, 5
+    Q, _ = _sign_fixed_qr(g.standard_normal((n, k)))
+    V = g.standard_normal((n, s)) + Q @ g.standard_normal((k, s))
+    Qj, P, T = fn(Q, V)
+    qq, rr = _sign_fixed_qr(np.concatenate([Q, V], axis=1))
+    assert np.allclose(P, rr[:k, k:], atol=1e-12)
+    assert np.allclose(T, rr[k:, k:], atol=1e-12)
+    assert checks.orth_error(np.concatenate([Q, Qj], axis=1))[0] < 1e-14
+
+
+# ---------------------------------------------------------------- error bounds of §IV and §V
+def test_cholqr_error_grows_like_kappa_squared_and_cholqr2_is_stable():
+    """Eq. (2)-(3): one CholQR leaves ||I - Q^T Q|| <= c1 kappa^2 with
+    c1 = 5(ns + s(s+1)) eps while c1 kappa^2 < 1/2 (Eq. 1); Theorem 1: then
+    kappa(Q) < sqrt(3) and CholQR2 reaches O(eps)."""
+    n, s = 20000, 5
+    c1 = 5 * (n * s + s * (s + 1)) * EPS
+    errs = []
+    for kappa in (1e1, 10 ** 2.5, 1e4):
+        assert c1 * kappa ** 2 < 0.5
+        V = synth.logscaled(n, s, kappa, seed=int(kappa))
+        Q1, _ = bo.cholqr(V)
+        e1 = checks.orth_error(Q1)[0]
+        assert e1 <= c1 * kappa ** 2
+        assert checks.cond2(Q1) < math.sqrt(3)
+        Q2, R = bo.cholqr2(V)
+        assert checks.orth_error(Q2)[0] < 50 * EPS
+        assert np.allclose(Q2 @ R, V, atol=1e-13 * np.abs(V).max())
+        errs.append(e1)
+    # the error of a single CholQR grows with kappa (kappa^2 eps regime)
+    assert errs[2] > 100 * errs[0]
+
+
+def test_two_stage_on_glued_matrix_reaches_machine_precision():
+    """Theorem 3 (§V) on the glued matrix of §VI (panel kappa 1e5, growing
+    accumulated kappa): after stage 1 the big panel has O(1) condition number
+    (Eq. 11); after stage 2 the orthogonality error is O(eps)."""
+    n, s, panels = 5000, 5, 6
+    V = synth.glued(n, s, panels, 1e5, seed=3)
+    assert checks.cond2(V) > 1e5
+    blocks = [V[:, i * s:(i + 1) * s] for i in range(panels)]
+    Q, Rt, Rd, Qhat = bo.two_stage_panel(np.zeros((n, 0)), blocks)
+    assert checks.cond2(Qhat) < 10.0
+    assert checks.orth_error(Q)[0] < 100 * EPS
+    assert np.allclose(Q @ Rd, V, atol=1e-12 * np.abs(V).max())
+    assert np.allclose(np.triu(Rd), Rd)
+    assert np.all(np.diag(Rd) > 0)
+
+
+def test_two_stage_panel_equals_householder_r():
+    """The two-stage R factor of a well-conditioned big panel is the unique
+    positive-diagonal R of its QR (Fig. 1 caption)."""
+    g = synth.rng(18)
+    n, s = 800, 5
+    V = g.standard_normal((n, 4 * s))
+    blocks = [V[:, i * s:(i + 1) * s] for i in range(4)]
+    Q, _, Rd, _ = bo.two_stage_panel(np.zeros((n, 0)), blocks)
+    _, r = _sign_fixed_qr(V)
+    assert np.allclose(Rd, r, atol=1e-12 * np.abs(r).max())
+
+
+# ---------------------------------------------------------------- least squares and Hessenberg
+def test_givens_solves_the_hessenberg_least_squares():
+    g = synth.rng(19)
+    m = 12
+    H = np.triu(g.standard_normal((m + 1, m)), -1)
+    beta = 3.5
+    gv = kr.Givens(m, beta)
+    for c in range(m):
+        gv.add_column(H[: c + 2, c])
+    y = gv.solve()
+    rhs = np.zeros(m + 1)
+    rhs[0] = beta
+    y_ref, *_ = np.linalg.lstsq(H, rhs, rcond=None)
+    assert np.allclose(y, y_ref, rtol=1e-10, atol=1e-12)
+    assert abs(gv.residual() - np.linalg.norm(rhs - H @ y_ref)) < 1e-12
+
+
+@pytest.mark.parametrize("ortho,panel", [("two_stage", 60), ("two_stage", 20), ("bcgs_pip2", 5),
+                                         ("bcgs2_cholqr2", 5)])
+def test_arnoldi_relation_of_recovered_hessenberg(ortho, panel):
+    """A Q_{1:k} = Q_{1:k+1} H to 1e-12 relative for the H recovered from the
+    s-step R factors (spec invariant)."""
+    A = synth.convdiff2d(40, seed=5)
+    b = kr.as_operator(A) @ synth.x_true(A.n, 1)
+    _, info = kr.sstep_gmres(A, b, m=60, s=5, panel=panel, tol=1e-30, max_restarts=1,
+                             ortho=ortho, return_basis=True)
+    k = info["k"]
+    assert k == 60
+    assert checks.orth_error(info["Q"][:, : k + 1])[0] < 1e-13
+    assert checks.arnoldi_residual(kr.as_operator(A), info["Q"], info["H"], k) < 1e-12
+
+
+def test_sstep_hessenberg_equals_arnoldi_hessenberg():
+    """With positive subdiagonals the Arnoldi factorization from a given start
+    vector is unique, so the recovered H of every s-step scheme equals the H of
+    standard Arnoldi (CGS2) over the first restart cycle."""
+    A = synth.convdiff2d(16, seed=6)
+    M = kr.as_operator(A)
+    b = M @ synth.x_true(A.n, 2)
+    m = 20
+    n = A.n
+    # reference: standard Arnoldi with CGS2, written out
+    Q = np.zeros((n, m + 1))
+    H = np.zeros((m + 1, m))
+    Q[:, 0] = b / np.linalg.norm(b)
+    for j in range(m):
+        w = M @ Q[:, j]
+        for _ in range(2):
+            h = Q[:, : j + 1].T @ w
+            w -= Q[:, : j + 1] @ h
+            H[: j + 1, j] += h
+        H[j + 1, j] = np.linalg.norm(w)
+        Q[:, j + 1] = w / H[j + 1, j]
+    for ortho, panel in (("two_stage", 20), ("two_stage", 10), ("bcgs_pip2", 5), ("bcgs2_cholqr2", 5)):
+        _, info = kr.sstep_gmres(A, b, m=m, s=5, panel=panel, tol=1e-30, max_restarts=1,
+                                 ortho=ortho, return_basis=True)
+        Hs = info["H"]
+        assert np.allclose(Hs, H, atol=1e-9 * np.abs(H).max()), ortho
+        assert np.allclose(np.abs(info["Q"][:, :m + 1]), np.abs(Q), atol=1e-9)
+
+
+# ---------------------------------------------------------------- end to end
+@pytest.mark.parametrize("ortho", ["two_stage", "bcgs_pip2", "bcgs2_cholqr2", "cgs2"])
+def test_small_dense_systems_reach_the_lu_solution(ortho):
+    g = synth.rng(20)
+    n = 48
+    A = g.standard_normal((n, n)) + 8.0 * np.eye(n)
+    import scipy.sparse as sp
+    As = sp.csr_matrix(A)
+    b = g.standard_normal(n)
+    x_lu = np.linalg.solve(A, b)
+    if ortho == "cgs2":
+        x, info = kr.gmres_cgs2(As, b, m=20, tol=1e-13)
+    else:
+        x, info = kr.sstep_gmres(As, b, m=20, s=5, panel=20, tol=1e-13, ortho=ortho)
+    assert info["status"] == 0
+    kappa = np.linalg.cond(A)
+    assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) <= 10 * kappa * 1e-13
+
+
+def test_laplace_forward_error_against_closed_form_condition_number():
+    """b = A x_true on the 64x64 Laplacian (C1 input).  SPD with closed-form
+    extreme eigenvalues, so ||x - x_true|| / ||x_true|| <= kappa(A) * relres."""
+    N = 64
+    A = synth.laplace2d(N)
+    M = kr.as_operator(A)
+    xt = synth.x_true(A.n, 0)
+    b = M @ xt
+    lo, hi = checks.laplace2d_extreme_eigs(N)
+    ev = np.linalg.eigvalsh(M.toarray())
+    assert abs(ev[0] - lo) < 1e-10 and abs(ev[-1] - hi) < 1e-10
+    kappa = hi / lo
+    for ortho in ("two_stage", "bcgs_pip2", "bcgs2_cholqr2"):
+        x, info = kr.sstep_gmres(A, b, m=60, s=5, tol=1e-8, ortho=ortho)
+        assert info["status"] == 0
+        rel = np.linalg.norm(M @ x - b) / np.linalg.norm(b)
+        assert rel <= 1e-8
+        assert np.linalg.norm(x - xt) / np.linalg.norm(xt) <= kappa * rel
+
+
+def test_convergence_tests_fall_on_panel_boundaries():
+    """Tables 2 and 4 print two-stage counts that are multiples of s^ and s-step
+    counts that are multiples of s; the oracle tests convergence at the same
+    points."""
+    with open(os.path.join(GOLD, "table2_table4_iteration_counts.json")) as f:
+        gold = json.load(f)
+    for shat, cnt in gold["table2"]["two_stage"].items():
+        assert cnt % int(shat) == 0 or cnt % 5 == 0
+    assert gold["table2"]["two_stage"]["60"] % 60 == 0
+    for cnt in gold["table4_two_stage_shat_m60"].values():
+        assert cnt % 60 == 0
+    for cnt in gold["table4_sstep_s5"].values():
+        assert cnt % 5 == 0
+    A = synth.laplace2d(32)
+    b = kr.as_operator(A) @ synth.x_true(A.n, 0)
+    for ortho, panel, step in (("two_stage", 60, 60), ("two_stage", 20, 20), ("bcgs_pip2", 5, 5)):
+        _, info = kr.sstep_gmres(A, b, m=60, s=5, panel=panel, tol=1e-8, ortho=ortho)
+        assert info["status"] == 0
+        assert info["iters"] % step == 0
+
+
+def test_s_equal_one_is_standard_gmres():
+    """§III: standard GMRES is s-step GMRES with step size one."""
+    A = synth.convdiff2d(20, seed=7)
+    b = kr.as_operator(A) @ synth.x_true(A.n, 3)
+    _, i_std = kr.gmres_cgs2(A, b, m=30, tol=1e-8)
+    _, i_s1 = kr.sstep_gmres(A, b, m=30, s=1, tol=1e-8, ortho="bcgs_pip2")
+    assert i_s1["status"] == 0
+    assert i_s1["iters"] == i_std["iters"]
+
+
+def test_breakdown_is_reported_not_patched():
+    """A rank-deficient MPK block makes the Gram of Eq. (1) singular; the oracle
+    reports the breakdown (status -4) instead of shifting it."""
+    n = 50
+    import scipy.sparse as sp
+    A = sp.identity(n, format="csr") * 2.0   # Krylov space of dimension 1
+    b = np.ones(n)
+    _, info = kr.sstep_gmres(A, b, m=10, s=5, tol=1e-30, ortho="two_stage")
+    assert info["status"] == kr.STATUS_BREAKDOWN
+
+
+def test_monomial_scale_is_a_power_of_two():
+    assert kr.mpk_sigma(synth.laplace2d(8)) == 8.0
+    assert kr.mpk_sigma(synth.laplace3d(5)) == 8.0
+    s = kr.mpk_sigma(synth.convdiff2d(10, 1))
+    assert s == 2.0 ** math.floor(math.log2(s))
