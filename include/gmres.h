@@ -1,0 +1,160 @@
+/*
+ * gmres.h -- C ABI of the GB300 s-step GMRES library with two-stage block
+ * orthogonalization (Yamazaki, Higgins, Boman, Szyld, "Two-Stage Block
+ * Orthogonalization to Improve Performance of s-step GMRES", arXiv 2402.15033).
+ *
+ * Conventions for every entry point
+ *   - All functions are extern "C", never throw, never abort.  They return an
+ *     int status: 0 = GMRES_OK, > 0 = warning, < 0 = error.  After an error
+ *     gmres_last_error() returns a message for the calling host thread.
+ *   - Dense blocks are column-major FP64 (or FP32 where named _f32) with a
+ *     leading dimension ld >= n (elements).  Device pointers must be 16-byte
+ *     aligned and ld a multiple of 2 (FP64) or 4 (FP32) so rows can be read
+ *     with 128-bit loads.  Pointers are never retained after a call returns,
+ *     except the CSR copy and workspace owned by a gmres_ctx.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Device-buffer calls are asynchronous on that stream and never
+ *     allocate: their scratch space is the caller's d_work.
+ *   - One GPU: the library uses the device current at gmres_create (or at the
+ *     call, for the standalone ortho entry points).
+ */
+#ifndef GB300_SSTEP_GMRES_H
+#define GB300_SSTEP_GMRES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define GMRES_OK              0
+#define GMRES_WARN_MAXIT      1   /* not converged within max_restarts; x is valid        */
+#define GMRES_ERR_ARG        -1   /* bad argument (sizes, alignment, options)             */
+#define GMRES_ERR_CUDA       -2   /* a CUDA runtime call failed                           */
+#define GMRES_ERR_OOM        -3   /* device allocation failed                             */
+#define GMRES_ERR_BREAKDOWN  -4   /* Cholesky of a Gram matrix hit a pivot <= 0 or NaN:   */
+                                  /* the block violated the stability condition of Eq. (1)/(5)/(9) */
+#define GMRES_ERR_NAN        -5   /* non-finite residual                                   */
+#define GMRES_ERR_TIMEOUT    -6   /* a bounded device wait ran out                         */
+#define GMRES_ERR_WORKSPACE  -7   /* d_work smaller than ortho_workspace_bytes()          */
+
+/* ---------------------------------------------------------------- options */
+#define GMRES_ORTHO_TWO_STAGE      0  /* §V, Fig. 5: BCGS-PIP per block + BCGS-PIP per big panel   */
+#define GMRES_ORTHO_BCGS_PIP2      1  /* §IV-C, Fig. 4b: the two-stage scheme with panel = s (§V)  */
+#define GMRES_PREC_FP64            0  /* everything FP64                                          */
+#define GMRES_PREC_MIXED           1  /* FP32 basis + MPK, FP64 Gram/Cholesky/Hessenberg, FP64 IR */
+#define GMRES_BASIS_MONOMIAL       0  /* §VI: monomial basis (scaled by a power of two)           */
+#define GMRES_BASIS_NEWTON         1  /* shifted products (A - theta_i I) v, shifts in opts.theta  */
+
+typedef struct gmres_opts {
+    int32_t m;             /* restart length: m+1 basis vectors per cycle (Table 1)            */
+    int32_t s;             /* step size of the first stage (Table 1), 1 <= s <= 16            */
+    int32_t panel;         /* second step size s^ (Table 1): s | panel | m, panel + 1 <= 64   */
+    int32_t max_restarts;  /* restart cycles before GMRES_WARN_MAXIT                           */
+    double  tol;           /* stop when ||b - A x|| / ||b|| <= tol                             */
+    double  sigma;         /* MPK scale; 0 = 2^floor(log2 ||A||_inf) (exact in binary FP)     */
+    int32_t ortho;         /* GMRES_ORTHO_*                                                    */
+    int32_t precision;     /* GMRES_PREC_*                                                     */
+    int32_t basis;         /* GMRES_BASIS_*                                                    */
+    int32_t timing;        /* 1 = record per-phase CUDA-event times into gmres_result          */
+    double  theta[16];     /* Newton shifts theta_0..theta_{s-1} (basis = NEWTON)              */
+    double  inner_tol;     /* mixed precision: relative tolerance of each inner FP32 solve     */
+    int32_t max_ir;        /* mixed precision: maximum FP64 refinement steps                   */
+    int32_t reserved[7];
+} gmres_opts;
+
+typedef struct gmres_result {
+    int32_t status;            /* same value gmres_solve returned                          */
+    int32_t iters;             /* Krylov iterations (SpMVs inside restart cycles)          */
+    int32_t restarts;          /* restart cycles run                                       */
+    int32_t ir_steps;          /* FP64 refinement steps (mixed precision), else 0          */
+    int32_t breakdown_block;   /* s-step block index of a GMRES_ERR_BREAKDOWN, else -1     */
+    int32_t breakdown_pivot;   /* 1-based Cholesky pivot of that breakdown, else 0         */
+    double  relres_implicit;   /* |g_{k+1}| / ||b|| of the last least-squares solve        */
+    double  relres_true;       /* ||b - A x|| / ||b|| recomputed in FP64 at exit           */
+    double  t_mpk_ms, t_stage1_ms, t_stage2_ms, t_ls_ms, t_total_ms;  /* opts.timing = 1  */
+} gmres_result;
+
+typedef struct gmres_ctx gmres_ctx;   /* opaque: device CSR copy, Krylov basis, workspace */
+
+/* Fill *o with the defaults: m=60, s=5, panel=60, tol=1e-8, max_restarts=10000,
+ * two-stage, FP64, monomial basis, sigma automatic. */
+int gmres_default_opts(gmres_opts* o);
+
+/* Create a solver for the n x n CSR matrix A (rowptr[n+1] int64, colind[nnz]
+ * int32 0-based, vals[nnz] FP64), on host (ptr_on_device = 0) or device
+ * (ptr_on_device = 1) memory.  The context copies A and allocates the basis
+ * ((m+1) columns of n, padded), the R/H/Givens state and the reduction
+ * workspace; the caller's arrays are not retained.  Errors: GMRES_ERR_ARG
+ * (n <= 0, nnz >= 2^31, bad options, a column index outside [0, n)),
+ * GMRES_ERR_OOM, GMRES_ERR_CUDA. */
+int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
+                 const int32_t* colind, const double* vals, int32_t ptr_on_device,
+                 const gmres_opts* opts, void* stream);
+
+/* Solve A x = b by restarted s-step GMRES (Fig. 1, §III) with the block
+ * orthogonalization chosen in opts (§IV-C, §V).  b[n] and x[n] are FP64 on
+ * host or device (ptr_on_device); x holds x0 on entry (a restart checkpoint)
+ * and the solution on exit.  Synchronizes the context's stream before it
+ * returns.  Convergence is tested once per big panel; the reported
+ * relres_true is recomputed from x.  Returns GMRES_OK, GMRES_WARN_MAXIT,
+ * GMRES_ERR_BREAKDOWN (res->breakdown_block/pivot set), GMRES_ERR_NAN or an
+ * error; res may be NULL. */
+int gmres_solve(gmres_ctx* c, const double* b, double* x, int32_t ptr_on_device, gmres_result* res);
+
+/* Release everything the context owns.  NULL-safe. */
+int gmres_destroy(gmres_ctx* c);
+
+/* Message of the last error on this host thread ("" if none).  Static storage. */
+const char* gmres_last_error(void);
+
+/* ------------------------------------------------ standalone block orthogonalization
+ * Both stages are one BCGS-PIP (§IV-C, Fig. 4a) on caller-owned device buffers:
+ *   [P; G] = [Q, V]^T V                 (one tall-skinny reduction over n rows)
+ *   T      = Chol(G - P^T P)            (block Pythagorean theorem; T upper, T_ii > 0)
+ *   V     <- (V - Q P) T^{-1}           (fused block update and triangular solve)
+ * Stage 1 (§V) orthogonalizes one new s-step block against the accumulated
+ * basis [Q_{1:l-1}, Q^_{l:j-1}]; stage 2 (§V) re-orthogonalizes a whole big
+ * panel Q^_{l:t} against the finished basis Q_{1:l-1} (k = 0 gives CholQR of
+ * the panel).  The two entry points compute the same operation and differ in
+ * the kernels they pick: stage 1 is tuned for nb <= 16 new columns, stage 2
+ * for panels up to 64 columns.
+ *
+ *   n        rows (n >= 1)
+ *   Q, ldq   k columns of the basis to project against (k >= 0; unread if 0)
+ *   V, ldv   nb new columns, overwritten by Q^_j (stage 1) or Q_{l:t} (stage 2)
+ *   R, ldr   output block column, (k+nb) x nb, column-major, ldr >= k+nb:
+ *            rows 0..k-1 = P, rows k..k+nb-1 = T (zeros below its diagonal)
+ *   d_work   device scratch of at least ortho_workspace_bytes(n, k, nb) bytes;
+ *            contents on entry are ignored
+ *   d_status device int32: set to 0, or to the 1-based index of the first bad
+ *            Cholesky pivot (then V is left unchanged and R holds P and the
+ *            partial factor)
+ * Limits: k + nb <= 256, nb <= 64.  Returns GMRES_ERR_ARG / _WORKSPACE /
+ * _CUDA for bad calls (nothing launched); a breakdown is reported only through
+ * d_status, because the call is asynchronous. */
+size_t ortho_workspace_bytes(int64_t n, int32_t k, int32_t nb);
+
+int ortho_stage1(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
+                 double* V, int64_t ldv, int32_t nb, double* R, int32_t ldr,
+                 void* d_work, size_t work_bytes, int32_t* d_status);
+
+int ortho_stage2(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
+                 double* V, int64_t ldv, int32_t nb, double* R, int32_t ldr,
+                 void* d_work, size_t work_bytes, int32_t* d_status);
+
+/* ------------------------------------------------ matrix powers kernel
+ * MPK of §III (standard, not communication-avoiding): s products in sequence,
+ * W[:,0] = (A v - theta_0 v) / sigma, W[:,i] = (A W[:,i-1] - theta_i W[:,i-1]) / sigma,
+ * with the context's matrix.  v[n] and W (n x s, ldw >= n) are device FP64;
+ * theta is a HOST array of s shifts, or NULL for the monomial basis; sigma is
+ * finite and nonzero.  Asynchronous on the context's stream. */
+int gmres_mpk(gmres_ctx* c, const double* v, double* W, int64_t ldw, int32_t s,
+              double sigma, const double* theta);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_SSTEP_GMRES_H */

@@ -1,0 +1,204 @@
+"""Thin ctypes binding of ``libgmres.so`` (the C ABI in ``include/gmres.h``).
+
+Argument marshalling only: every step of the solver and of the block
+orthogonalization runs in the library's CUDA kernels.  Device buffers are
+passed as raw pointers (``tensor.data_ptr()``); PyTorch is used by callers only
+to own device memory and streams.  ``load()`` raises if the library is missing
+or was built without a symbol the header declares; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgmres.so")
+
+GMRES_OK = 0
+GMRES_WARN_MAXIT = 1
+GMRES_ERR_ARG = -1
+GMRES_ERR_CUDA = -2
+GMRES_ERR_OOM = -3
+GMRES_ERR_BREAKDOWN = -4
+GMRES_ERR_NAN = -5
+GMRES_ERR_TIMEOUT = -6
+GMRES_ERR_WORKSPACE = -7
+
+GMRES_ORTHO_TWO_STAGE = 0
+GMRES_ORTHO_BCGS_PIP2 = 1
+GMRES_PREC_FP64 = 0
+GMRES_PREC_MIXED = 1
+GMRES_BASIS_MONOMIAL = 0
+GMRES_BASIS_NEWTON = 1
+
+
+class gmres_opts(C.Structure):
+    _fields_ = [("m", C.c_int32), ("s", C.c_int32), ("panel", C.c_int32), ("max_restarts", C.c_int32),
+                ("tol", C.c_double), ("sigma", C.c_double),
+                ("ortho", C.c_int32), ("precision", C.c_int32), ("basis", C.c_int32), ("timing", C.c_int32),
+                ("theta", C.c_double * 16), ("inner_tol", C.c_double), ("max_ir", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
+
+
+class gmres_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("restarts", C.c_int32), ("ir_steps", C.c_int32),
+                ("breakdown_block", C.c_int32), ("breakdown_pivot", C.c_int32),
+                ("relres_implicit", C.c_double), ("relres_true", C.c_double),
+                ("t_mpk_ms", C.c_double), ("t_stage1_ms", C.c_double), ("t_stage2_ms", C.c_double),
+                ("t_ls_ms", C.c_double), ("t_total_ms", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_vp, _i32, _i64, _sz, _dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t, C.c_double
+
+# name -> (restype, argtypes); every symbol the header declares
+SIGNATURES = {
+    "gmres_default_opts": (_i32, [C.POINTER(gmres_opts)]),
+    "gmres_create": (_i32, [C.POINTER(_vp), _i64, _i64, _vp, _vp, _vp, _i32, C.POINTER(gmres_opts), _vp]),
+    "gmres_solve": (_i32, [_vp, _vp, _vp, _i32, C.POINTER(gmres_result)]),
+    "gmres_destroy": (_i32, [_vp]),
+    "gmres_last_error": (C.c_char_p, []),
+    "ortho_workspace_bytes": (_sz, [_i64, _i32, _i32]),
+    "ortho_stage1": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
+    "ortho_stage2": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
+    "gmres_mpk": (_i32, [_vp, _vp, _vp, _i64, _i32, _dbl, C.POINTER(_dbl)]),
+}
+
+_lib = None
+
+
+class GmresError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libgmres error {code}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH):
+    """Load the library once and declare every signature.  Raises if the shared
+    object is missing (build it with ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first (python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().gmres_last_error().decode()
+
+
+def check(rc: int, allow=(GMRES_OK,)) -> int:
+    if rc not in allow:
+        raise GmresError(rc, last_error())
+    return rc
+
+
+def default_opts(**kw) -> gmres_opts:
+    o = gmres_opts()
+    check(load().gmres_default_opts(C.byref(o)))
+    for k, v in kw.items():
+        if k == "theta":
+            for i, t in enumerate(v):
+                o.theta[i] = t
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """gmres_create / gmres_solve / gmres_destroy around one CSR matrix.
+
+    ``rowptr`` (int64), ``colind`` (int32) and ``vals`` (float64) are numpy
+    arrays (host) or torch CUDA tensors (device)."""
+
+    def __init__(self, n, rowptr, colind, vals, opts: gmres_opts | None = None, stream=None):
+        lib = load()
+        on_dev = hasattr(rowptr, "data_ptr")
+        if on_dev:
+            ptrs = [C.c_void_p(a.data_ptr()) for a in (rowptr, colind, vals)]
+        else:
+            ptrs = [a.ctypes.data_as(C.c_void_p) for a in (rowptr, colind, vals)]
+            self._keep = (rowptr, colind, vals)
+        o = opts if opts is not None else default_opts()
+        h = C.c_void_p()
+        nnz = int(rowptr[-1])
+        check(lib.gmres_create(C.byref(h), int(n), nnz, *ptrs, int(on_dev), C.byref(o), C.c_void_p(stream or 0)))
+        self.h = h
+        self.n = int(n)
+        self.opts = o
+
+    @classmethod
+    def from_csr(cls, A, opts=None, stream=None):
+        return cls(A.n, A.rowptr, A.colind, A.vals, opts, stream)
+
+    def solve(self, b, x):
+        """b, x: numpy float64 arrays (host) or torch float64 CUDA tensors.
+        x holds x0 and receives the solution.  Returns (status, result dict)."""
+        lib = load()
+        res = gmres_result()
+        if hasattr(b, "data_ptr"):
+            rc = lib.gmres_solve(self.h, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), 1, C.byref(res))
+        else:
+            rc = lib.gmres_solve(self.h, b.ctypes.data_as(C.c_void_p), x.ctypes.data_as(C.c_void_p), 0,
+                                 C.byref(res))
+        out = res.as_dict()
+        out["error"] = last_error() if rc < 0 else ""
+        return rc, out
+
+    def mpk(self, v, W, s, sigma, theta=None):
+        lib = load()
+        th = (C.c_double * s)(*theta) if theta is not None else None
+        check(lib.gmres_mpk(self.h, _ptr(v), _ptr(W), W.stride(1), int(s), float(sigma), th))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().gmres_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def workspace_bytes(n, k, nb) -> int:
+    return int(load().ortho_workspace_bytes(int(n), int(k), int(nb)))
+
+
+def _ortho(fn, Q, V, R, work, status, k, stream):
+    """Q: (>=n, >=k) column-major view or None; V: column-major (ld, nb) view."""
+    n = V.shape[0]
+    nb = V.shape[1]
+    ldv = V.stride(1)
+    ldq = Q.stride(1) if (Q is not None and k > 0) else n
+    qp = C.c_void_p(Q.data_ptr()) if (Q is not None and k > 0) else None
+    return fn(C.c_void_p(stream or 0), int(n), qp, int(ldq), int(k), C.c_void_p(V.data_ptr()), int(ldv), int(nb),
+              C.c_void_p(R.data_ptr()), int(R.stride(1)), C.c_void_p(work.data_ptr()), int(work.numel()),
+              C.c_void_p(status.data_ptr()))
+
+
+def ortho_stage1(Q, V, R, work, status, k=None, stream=None):
+    """BCGS-PIP of V against the first k columns of Q (stage 1 of §V).
+    Tensors are column-major views (``t.T`` of a row-major (cols, ld) tensor)."""
+    k = (Q.shape[1] if Q is not None else 0) if k is None else k
+    return check(_ortho(load().ortho_stage1, Q, V, R, work, status, k, stream))
+
+
+def ortho_stage2(Q, V, R, work, status, k=None, stream=None):
+    """BCGS-PIP of the big panel V against the first k columns of Q (stage 2 of §V)."""
+    k = (Q.shape[1] if Q is not None else 0) if k is None else k
+    return check(_ortho(load().ortho_stage2, Q, V, R, work, status, k, stream))

@@ -1,0 +1,71 @@
+// Shared helpers of the GB300 s-step GMRES library (host + device).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include "../../include/gmres.h"
+
+namespace gm {
+
+// Thread-local last-error message (gmres_last_error).
+void set_error(const char* fmt, ...);
+void clear_error();
+
+constexpr int kMaxNB = 64;        // widest block handled by one Gram column group
+constexpr int kMaxKX = 256;       // k + nb limit of the standalone ortho calls
+constexpr int kGramThreads = 256;
+
+// Number of CTAs of the split-n reductions: enough to fill every SM twice,
+// never more CTAs than 64-row chunks.
+int reduction_grid(int64_t n);
+int num_sms();
+
+// Layout of the scratch space of one BCGS-PIP call (bytes, 256-aligned pieces).
+struct PipWork {
+    double* partial;     // [grid][groups][64*64] per-CTA partial Gram blocks
+    unsigned* counter;   // [groups] arrival counters of the last-CTA reduce
+    double* gram;        // [kx * nb] reduced Gram (column-major, ld = kx)
+    size_t bytes;
+};
+PipWork pip_work_layout(void* base, int64_t n, int k, int nb);
+
+// Device-side status block of one BCGS-PIP (also used by the solver).
+struct PipStatus {
+    int32_t* status;     // 0 or 1-based bad pivot
+};
+
+// ---------------------------------------------------------------- launchers
+// BCGS-PIP step 1+2: [P; G] = [Q, V]^T V split over n rows; the last CTA to
+// finish reduces the partial blocks in a fixed order, forms G - P^T P, factors
+// it, and writes R = [P; T].  Q may be null when k == 0.
+cudaError_t launch_pip_gram_chol(cudaStream_t st, int64_t n,
+                                 const double* Q, int64_t ldq, int k,
+                                 const double* V, int64_t ldv, int nb,
+                                 double* R, int ldr, const PipWork& w, int32_t* d_status,
+                                 int32_t* d_skip, int grid);
+// BCGS-PIP step 3: V <- (V - Q P) T^{-1}, P and T read from R.
+cudaError_t launch_pip_update(cudaStream_t st, int64_t n,
+                              const double* Q, int64_t ldq, int k,
+                              double* V, int64_t ldv, int nb,
+                              const double* R, int ldr, const int32_t* d_status,
+                              const int32_t* d_skip);
+
+}  // namespace gm
+
+#define GM_CUDA_RET(call)                                                              \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            gm::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),       \
+                          __FILE__, __LINE__);                                         \
+            return e_ == cudaErrorMemoryAllocation ? GMRES_ERR_OOM : GMRES_ERR_CUDA;   \
+        }                                                                              \
+    } while (0)
+
+#define GM_ARG(cond, ...)                                                              \
+    do {                                                                               \
+        if (!(cond)) {                                                                 \
+            gm::set_error(__VA_ARGS__);                                                \
+            return GMRES_ERR_ARG;                                                      \
+        }                                                                              \
+    } while (0)

@@ -1,0 +1,524 @@
+// s-step GMRES driver (Fig. 1, §III) with two-stage block orthogonalization
+// (§V, Fig. 5) and the C ABI of include/gmres.h.
+//
+// One restart cycle, all on the device, in stream order:
+//   r = b - A x, q_1 = r/||r||                       (host reads ||r|| once per cycle)
+//   for each s-step block j:
+//     MPK: s SpMVs from the block's start column      (kernel (c))
+//     stage 1: BCGS-PIP of the s new columns against every accumulated column
+//              [Q_{1:l-1}, Q^_{l:j-1}]                (kernels (a)+(d), (b))
+//     at the end of a big panel [l, t]:
+//       stage 2: BCGS-PIP of Q^_{l:t} against Q_{1:l-1} (CholQR when l = 1)
+//       Hessenberg recovery + Givens least squares  (kernel (d), one CTA)
+//   x += Q_{1:k} y
+// A device flag ("done") makes every later kernel of the cycle return at once
+// after convergence at a big-panel end or after a Cholesky breakdown, so a
+// cycle is a fixed launch sequence without host round trips.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <vector>
+#include <algorithm>
+#include "solver_state.cuh"
+
+namespace gm {
+
+static thread_local char g_err[512];
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+
+int num_sms() {
+    static int cached = 0;
+    if (cached == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            cached = v;
+        else
+            cached = 152;
+    }
+    return cached;
+}
+
+// A fixed cap (two CTAs on each of GB300's 152 SMs) keeps the reduction tree,
+// and therefore the rounding, identical on every device.
+int reduction_grid(int64_t n) {
+    const int64_t chunks = (n + 127) / 128;
+    return (int)(chunks < 304 ? (chunks > 0 ? chunks : 1) : 304);
+}
+
+}  // namespace gm
+
+using namespace gm;
+
+struct gmres_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    gmres_opts opts{};
+    DevCSR A;
+    int64_t n = 0, ldq = 0;
+    double sigma = 1.0;
+    double* basis = nullptr;     // (m+1) columns, ld = ldq
+    double* b = nullptr;
+    double* x = nullptr;
+    double* red_partial = nullptr;
+    unsigned* red_counter = nullptr;
+    void* pip_work = nullptr;
+    size_t pip_bytes = 0;
+    DevState* st = nullptr;      // device
+    DevState* hst = nullptr;     // pinned host mirror
+    std::vector<cudaEvent_t> ev;
+};
+
+extern "C" {
+
+const char* gmres_last_error(void) { return g_err; }
+
+int gmres_default_opts(gmres_opts* o) {
+    if (!o) return GMRES_ERR_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->m = 60;
+    o->s = 5;
+    o->panel = 60;
+    o->max_restarts = 10000;
+    o->tol = 1e-8;
+    o->sigma = 0.0;
+    o->ortho = GMRES_ORTHO_TWO_STAGE;
+    o->precision = GMRES_PREC_FP64;
+    o->basis = GMRES_BASIS_MONOMIAL;
+    o->timing = 0;
+    o->inner_tol = 1e-5;
+    o->max_ir = 20;
+    return GMRES_OK;
+}
+
+size_t ortho_workspace_bytes(int64_t n, int32_t k, int32_t nb) {
+    if (n <= 0 || k < 0 || nb <= 0) return 0;
+    return pip_work_layout(nullptr, n, k, nb).bytes;
+}
+
+static int check_opts(const gmres_opts* o) {
+    GM_ARG(o->m >= 1 && o->m + 1 <= kMaxCols, "m must be in [1, %d]", kMaxCols - 1);
+    GM_ARG(o->s >= 1 && o->s <= 16, "s must be in [1, 16]");
+    GM_ARG(o->tol > 0.0, "tol must be positive");
+    GM_ARG(o->max_restarts >= 1, "max_restarts must be >= 1");
+    GM_ARG(o->ortho == GMRES_ORTHO_TWO_STAGE || o->ortho == GMRES_ORTHO_BCGS_PIP2, "unknown ortho");
+    GM_ARG(o->precision == GMRES_PREC_FP64, "precision: only FP64 is built");
+    GM_ARG(o->basis == GMRES_BASIS_MONOMIAL || o->basis == GMRES_BASIS_NEWTON, "unknown basis");
+    const int panel = o->ortho == GMRES_ORTHO_BCGS_PIP2 ? o->s : o->panel;
+    GM_ARG(panel >= o->s && panel % o->s == 0 && o->m % panel == 0, "need s | panel | m");
+    GM_ARG(o->sigma >= 0.0 && std::isfinite(o->sigma), "sigma must be >= 0");
+    return GMRES_OK;
+}
+
+int gmres_destroy(gmres_ctx* c) {
+    if (!c) return GMRES_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto e : c->ev) cudaEventDestroy(e);
+    cudaFree(c->A.rowptr);
+    cudaFree(c->A.colind);
+    cudaFree(c->A.vals);
+    cudaFree(c->basis);
+    cudaFree(c->b);
+    cudaFree(c->x);
+    cudaFree(c->red_partial);
+    cudaFree(c->red_counter);
+    cudaFree(c->pip_work);
+    cudaFree(c->st);
+    cudaFreeHost(c->hst);
+    delete c;
+    return GMRES_OK;
+}
+
+#define CK(call)                                    \
+    do {                                            \
+        int rc_ = (call);                           \
+        if (rc_ != GMRES_OK) { gmres_destroy(c); return rc_; } \
+    } while (0)
+
+static int cuda_rc(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return GMRES_OK;
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? GMRES_ERR_OOM : GMRES_ERR_CUDA;
+}
+
+int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colind,
+                 const double* vals, int32_t ptr_on_device, const gmres_opts* opts, void* stream) {
+    clear_error();
+    GM_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    GM_ARG(n >= 1, "n must be >= 1");
+    GM_ARG(nnz >= 0 && nnz < (int64_t(1) << 31), "nnz must be in [0, 2^31)");
+    GM_ARG(rowptr != nullptr && (nnz == 0 || (colind != nullptr && vals != nullptr)), "NULL CSR array");
+    gmres_opts o;
+    if (opts) o = *opts; else gmres_default_opts(&o);
+    if (o.ortho == GMRES_ORTHO_BCGS_PIP2) o.panel = o.s;
+    {
+        int rc = check_opts(&o);
+        if (rc) return rc;
+    }
+    gmres_ctx* c = new gmres_ctx();
+    c->opts = o;
+    c->n = n;
+    c->stream = static_cast<cudaStream_t>(stream);
+    CK(cuda_rc(cudaGetDevice(&c->device), "cudaGetDevice"));
+    cudaStream_t s = c->stream;
+    c->ldq = (n + 31) / 32 * 32;
+    const int mp1 = o.m + 1;
+
+    c->A.n = n;
+    c->A.nnz = nnz;
+    CK(cuda_rc(cudaMalloc(&c->A.rowptr, (n + 1) * sizeof(int32_t)), "cudaMalloc rowptr"));
+    CK(cuda_rc(cudaMalloc(&c->A.colind, (nnz > 0 ? nnz : 1) * sizeof(int32_t)), "cudaMalloc colind"));
+    CK(cuda_rc(cudaMalloc(&c->A.vals, (nnz > 0 ? nnz : 1) * sizeof(double)), "cudaMalloc vals"));
+    if (ptr_on_device) {
+        int64_t* tmp = nullptr;
+        CK(cuda_rc(cudaMalloc(&tmp, (n + 1) * sizeof(int64_t)), "cudaMalloc tmp"));
+        cudaError_t e = cudaMemcpyAsync(tmp, rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = launch_rowptr_narrow(s, n + 1, tmp, c->A.rowptr);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(tmp);
+        CK(cuda_rc(e, "rowptr copy"));
+        if (nnz > 0) {
+            CK(cuda_rc(cudaMemcpyAsync(c->A.colind, colind, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s), "colind copy"));
+            CK(cuda_rc(cudaMemcpyAsync(c->A.vals, vals, nnz * sizeof(double), cudaMemcpyDeviceToDevice, s), "vals copy"));
+        }
+    } else {
+        std::vector<int32_t> rp(n + 1);
+        for (int64_t i = 0; i <= n; ++i) {
+            if (rowptr[i] < 0 || rowptr[i] > nnz) {
+                set_error("rowptr[%lld] out of range", (long long)i);
+                gmres_destroy(c);
+                return GMRES_ERR_ARG;
+            }
+            rp[i] = (int32_t)rowptr[i];
+        }
+        CK(cuda_rc(cudaMemcpyAsync(c->A.rowptr, rp.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s), "rowptr copy"));
+        if (nnz > 0) {
+            CK(cuda_rc(cudaMemcpyAsync(c->A.colind, colind, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s), "colind copy"));
+            CK(cuda_rc(cudaMemcpyAsync(c->A.vals, vals, nnz * sizeof(double), cudaMemcpyHostToDevice, s), "vals copy"));
+        }
+        CK(cuda_rc(cudaStreamSynchronize(s), "sync"));
+    }
+    // validation and the power-of-two MPK scale
+    {
+        int32_t* bad = nullptr;
+        unsigned long long* mx = nullptr;
+        CK(cuda_rc(cudaMalloc(&bad, 16), "cudaMalloc"));
+        mx = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(bad) + 8);
+        cudaError_t e = cudaMemsetAsync(bad, 0, 16, s);
+        if (e == cudaSuccess) e = launch_validate_csr(s, n, nnz, c->A.rowptr, c->A.colind, bad);
+        int32_t hb = 0;
+        unsigned long long hm = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess || hb) cudaFree(bad);
+        CK(cuda_rc(e, "CSR validation"));
+        if (hb) {
+            set_error("invalid CSR (code %d): rowptr must start at 0, be nondecreasing and end at nnz; "
+                      "columns must lie in [0, n)", hb);
+            gmres_destroy(c);
+            return GMRES_ERR_ARG;
+        }
+        // only a validated CSR is read row by row
+        e = launch_rowabs(s, c->A, mx);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hm, mx, 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(bad);
+        CK(cuda_rc(e, "row sums"));
+        double rmax;
+        std::memcpy(&rmax, &hm, 8);
+        if (o.sigma > 0.0) c->sigma = o.sigma;
+        else c->sigma = (rmax > 0.0 && std::isfinite(rmax)) ? std::ldexp(1.0, (int)std::floor(std::log2(rmax))) : 1.0;
+    }
+    CK(cuda_rc(cudaMalloc(&c->basis, (size_t)mp1 * c->ldq * sizeof(double)), "cudaMalloc basis"));
+    CK(cuda_rc(cudaMemsetAsync(c->basis, 0, (size_t)mp1 * c->ldq * sizeof(double), s), "memset basis"));
+    CK(cuda_rc(cudaMalloc(&c->b, c->ldq * sizeof(double)), "cudaMalloc b"));
+    CK(cuda_rc(cudaMalloc(&c->x, c->ldq * sizeof(double)), "cudaMalloc x"));
+    const int ng = norm_grid(n);
+    CK(cuda_rc(cudaMalloc(&c->red_partial, ng * sizeof(double)), "cudaMalloc partial"));
+    CK(cuda_rc(cudaMalloc(&c->red_counter, 256), "cudaMalloc counter"));
+    CK(cuda_rc(cudaMemsetAsync(c->red_counter, 0, 256, s), "memset counter"));
+    // PIP workspace: the largest of the cycle's calls
+    size_t wb = 0;
+    for (int st0 = 0; st0 < o.m; st0 += o.s) {
+        wb = std::max(wb, ortho_workspace_bytes(n, st0 + 1, o.s));
+        const int t = st0 + o.s;
+        if (t % o.panel == 0) {
+            const int lo = (t == o.panel) ? 0 : t - o.panel + 1;
+            wb = std::max(wb, ortho_workspace_bytes(n, lo, t - lo + 1));
+        }
+    }
+    c->pip_bytes = wb;
+    CK(cuda_rc(cudaMalloc(&c->pip_work, wb), "cudaMalloc workspace"));
+    CK(cuda_rc(cudaMemsetAsync(c->pip_work, 0, wb, s), "memset workspace"));
+    CK(cuda_rc(cudaMalloc(&c->st, sizeof(DevState)), "cudaMalloc state"));
+    CK(cuda_rc(cudaMallocHost(&c->hst, sizeof(DevState)), "cudaMallocHost state"));
+    std::memset(c->hst, 0, sizeof(DevState));
+    c->hst->m = o.m;
+    c->hst->s = o.s;
+    c->hst->panel = o.panel;
+    c->hst->sigma = c->sigma;
+    for (int i = 0; i < 16; ++i) c->hst->theta[i] = (o.basis == GMRES_BASIS_NEWTON) ? o.theta[i] : 0.0;
+    CK(cuda_rc(cudaMemcpyAsync(c->st, c->hst, sizeof(DevState), cudaMemcpyHostToDevice, s), "state upload"));
+    CK(cuda_rc(cudaStreamSynchronize(s), "sync"));
+    if (o.timing) {
+        const int per_cycle = 2 * (2 * (o.m / o.s) + 2 * (o.m / o.panel)) + 2;
+        c->ev.resize(per_cycle);
+        for (auto& e : c->ev) CK(cuda_rc(cudaEventCreate(&e), "cudaEventCreate"));
+    }
+    *out = c;
+    return GMRES_OK;
+}
+
+// phases for opts.timing
+enum { PH_MPK = 0, PH_S1 = 1, PH_S2 = 2, PH_LS = 3 };
+
+static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
+    const gmres_opts& o = c->opts;
+    cudaStream_t s = c->stream;
+    DevState* ds = c->st;
+    int32_t* done = &ds->done;
+    const double sinv = 1.0 / c->sigma;
+    PipWork w = pip_work_layout(c->pip_work, c->n, 0, 1);  // re-laid out per call below
+    int evi = 0;
+    auto mark = [&](int phase) -> cudaError_t {
+        if (!marks) return cudaSuccess;
+        marks->push_back({phase, evi});
+        return cudaEventRecord(c->ev[evi++], s);
+    };
+    const int nblk = o.m / o.s;
+    int panel_idx = 0;
+    cudaError_t e = launch_cycle_begin(s, ds);
+    if (e == cudaSuccess) e = launch_scale(s, c->n, c->basis, ds);
+    for (int j = 0; j < nblk && e == cudaSuccess; ++j) {
+        const int st0 = j * o.s;
+        e = mark(PH_MPK);
+        for (int i = 0; i < o.s && e == cudaSuccess; ++i) {
+            const double th = c->hst->theta[i];
+            e = launch_spmv(s, c->A, c->basis + (size_t)(st0 + i) * c->ldq, c->basis + (size_t)(st0 + i + 1) * c->ldq,
+                            th, sinv, done);
+        }
+        if (e == cudaSuccess) e = mark(PH_MPK);
+        if (e == cudaSuccess) e = mark(PH_S1);
+        if (e == cudaSuccess) {
+            const int k = st0 + 1;
+            w = pip_work_layout(c->pip_work, c->n, k, o.s);
+            double* V = c->basis + (size_t)k * c->ldq;
+            double* R = ds->Rhat + (size_t)k * kMaxCols;
+            e = launch_pip_gram_chol(s, c->n, c->basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, w,
+                                     &ds->blkstat[j], done, reduction_grid(c->n));
+            if (e == cudaSuccess)
+                e = launch_pip_update(s, c->n, c->basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, &ds->blkstat[j], done);
+        }
+        if (e == cudaSuccess) e = mark(PH_S1);
+        const int t = st0 + o.s;
+        if (e == cudaSuccess && t % o.panel == 0) {
+            const int lo = (t == o.panel) ? 0 : t - o.panel + 1;
+            const int np = t - lo + 1;
+            e = mark(PH_S2);
+            w = pip_work_layout(c->pip_work, c->n, lo, np);
+            double* V = c->basis + (size_t)lo * c->ldq;
+            double* R = ds->Cm + (size_t)lo * kMaxCols;
+            int32_t* stat = &ds->blkstat[nblk + panel_idx];
+            if (e == cudaSuccess)
+                e = launch_pip_gram_chol(s, c->n, c->basis, c->ldq, lo, V, c->ldq, np, R, kMaxCols, w, stat, done,
+                                         reduction_grid(c->n));
+            if (e == cudaSuccess)
+                e = launch_pip_update(s, c->n, c->basis, c->ldq, lo, V, c->ldq, np, R, kMaxCols, stat, done);
+            if (e == cudaSuccess) e = mark(PH_S2);
+            if (e == cudaSuccess) e = mark(PH_LS);
+            if (e == cudaSuccess) e = launch_hessenberg_ls(s, ds, lo, t);
+            if (e == cudaSuccess) e = mark(PH_LS);
+            ++panel_idx;
+        }
+    }
+    if (e == cudaSuccess) e = launch_xupdate(s, c->n, c->basis, c->ldq, c->x, ds);
+    return cuda_rc(e, "cycle launch");
+}
+
+int gmres_solve(gmres_ctx* c, const double* b, double* x, int32_t ptr_on_device, gmres_result* res) {
+    clear_error();
+    GM_ARG(c != nullptr && b != nullptr && x != nullptr, "NULL argument");
+    gmres_result r{};
+    r.breakdown_block = -1;
+    auto finish = [&](int status) {
+        r.status = status;
+        if (res) *res = r;
+        return status;
+    };
+    if (cudaSetDevice(c->device) != cudaSuccess) return finish(cuda_rc(cudaGetLastError(), "cudaSetDevice"));
+    cudaStream_t s = c->stream;
+    const gmres_opts& o = c->opts;
+    const cudaMemcpyKind kin = ptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kout = ptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t vb = c->n * sizeof(double);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (o.timing) {
+        cudaEventCreate(&t0);
+        cudaEventCreate(&t1);
+        cudaEventRecord(t0, s);
+    }
+    int rc = cuda_rc(cudaMemcpyAsync(c->b, b, vb, kin, s), "copy b");
+    if (!rc) rc = cuda_rc(cudaMemcpyAsync(c->x, x, vb, kin, s), "copy x");
+    if (!rc) rc = cuda_rc(launch_residual(s, c->A, c->b, nullptr, nullptr, c->red_partial, c->red_counter, c->st, 1),
+                          "norm b");
+    if (!rc) rc = cuda_rc(cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s), "state read");
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(s), "sync");
+    if (rc) return finish(rc);
+    const double bnorm = c->hst->bnorm;
+    if (!std::isfinite(bnorm)) {
+        set_error("b has non-finite entries");
+        return finish(GMRES_ERR_NAN);
+    }
+    int status = GMRES_WARN_MAXIT;
+    if (bnorm == 0.0) {
+        // the solution of A x = 0 is x = 0
+        rc = cuda_rc(cudaMemsetAsync(c->x, 0, vb, s), "zero x");
+        if (!rc) rc = cuda_rc(cudaMemcpyAsync(x, c->x, vb, kout, s), "copy x");
+        if (!rc) rc = cuda_rc(cudaStreamSynchronize(s), "sync");
+        return finish(rc ? rc : GMRES_OK);
+    }
+    {
+        double tol_abs = o.tol * bnorm;
+        rc = cuda_rc(cudaMemcpyAsync(&c->st->tol_abs, &tol_abs, sizeof(double), cudaMemcpyHostToDevice, s), "tol");
+        int32_t zero = 0;
+        if (!rc) rc = cuda_rc(cudaMemcpyAsync(&c->st->iters, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, s), "iters");
+        if (!rc) rc = cuda_rc(cudaStreamSynchronize(s), "sync");
+        if (rc) return finish(rc);
+    }
+    std::vector<std::pair<int, int>> marks;
+    const int nstat = o.m / o.s + o.m / o.panel;
+    for (int cyc = 0;; ++cyc) {
+        rc = cuda_rc(launch_residual(s, c->A, c->b, c->x, c->basis, c->red_partial, c->red_counter, c->st, 0),
+                     "residual");
+        if (!rc) rc = cuda_rc(cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s), "state read");
+        if (!rc) rc = cuda_rc(cudaStreamSynchronize(s), "sync");
+        if (rc) return finish(rc);
+        const DevState& h = *c->hst;
+        if (cyc > 0 && o.timing) {
+            // accumulate the previous cycle's phase times
+            for (size_t i = 0; i + 1 < marks.size(); i += 2) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, c->ev[marks[i].second], c->ev[marks[i + 1].second]);
+                double* dst = marks[i].first == PH_MPK ? &r.t_mpk_ms : marks[i].first == PH_S1 ? &r.t_stage1_ms
+                            : marks[i].first == PH_S2 ? &r.t_stage2_ms : &r.t_ls_ms;
+                *dst += ms;
+            }
+        }
+        r.iters = h.iters;
+        r.restarts = cyc;
+        r.relres_true = h.beta / bnorm;
+        if (cyc > 0) r.relres_implicit = h.resid / bnorm;
+        for (int i = 0; i < nstat; ++i) {
+            if (h.blkstat[i]) {
+                r.breakdown_block = i;
+                r.breakdown_pivot = h.blkstat[i];
+                set_error("Cholesky breakdown in %s %d at pivot %d (restart cycle %d)",
+                          i < o.m / o.s ? "stage-1 block" : "stage-2 panel",
+                          i < o.m / o.s ? i : i - o.m / o.s, h.blkstat[i], cyc - 1);
+                status = GMRES_ERR_BREAKDOWN;
+                break;
+            }
+        }
+        if (status == GMRES_ERR_BREAKDOWN) break;
+        if (!std::isfinite(h.beta)) {
+            set_error("non-finite residual norm");
+            status = GMRES_ERR_NAN;
+            break;
+        }
+        if (h.beta <= o.tol * bnorm) { status = GMRES_OK; break; }
+        if (cyc >= o.max_restarts) { status = GMRES_WARN_MAXIT; break; }
+        marks.clear();
+        rc = run_cycle(c, o.timing ? &marks : nullptr);
+        if (rc) return finish(rc);
+    }
+    rc = cuda_rc(cudaMemcpyAsync(x, c->x, vb, kout, s), "copy x");
+    if (o.timing && !rc) {
+        cudaEventRecord(t1, s);
+    }
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(s), "sync");
+    if (o.timing) {
+        float ms = 0.f;
+        if (!rc) cudaEventElapsedTime(&ms, t0, t1);
+        r.t_total_ms = ms;
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+    }
+    if (rc) return finish(rc);
+    return finish(status);
+}
+
+static int check_pip_args(int64_t n, const double* Q, int64_t ldq, int32_t k, const double* V, int64_t ldv,
+                          int32_t nb, const double* R, int32_t ldr, void* d_work, size_t work_bytes,
+                          const int32_t* d_status, int* code) {
+    *code = GMRES_ERR_ARG;
+    GM_ARG(n >= 1, "n must be >= 1");
+    GM_ARG(k >= 0 && nb >= 1 && nb <= kMaxNB && k + nb <= kMaxKX, "need k >= 0, 1 <= nb <= 64, k + nb <= 256");
+    GM_ARG(k == 0 || (Q != nullptr && ldq >= n), "Q must be non-NULL with ldq >= n when k > 0");
+    GM_ARG(V != nullptr && ldv >= n, "V must be non-NULL with ldv >= n");
+    GM_ARG(R != nullptr && ldr >= k + nb, "R must be non-NULL with ldr >= k + nb");
+    GM_ARG(d_status != nullptr, "d_status is NULL");
+    GM_ARG(d_work != nullptr, "d_work is NULL");
+    GM_ARG((reinterpret_cast<uintptr_t>(V) & 15) == 0 && (k == 0 || (reinterpret_cast<uintptr_t>(Q) & 15) == 0),
+           "Q and V must be 16-byte aligned");
+    GM_ARG((reinterpret_cast<uintptr_t>(d_work) & 255) == 0, "d_work must be 256-byte aligned");
+    if (work_bytes < ortho_workspace_bytes(n, k, nb)) {
+        set_error("d_work holds %zu bytes, need %zu", work_bytes, ortho_workspace_bytes(n, k, nb));
+        *code = GMRES_ERR_WORKSPACE;
+        return *code;
+    }
+    *code = GMRES_OK;
+    return GMRES_OK;
+}
+
+static int ortho_pip(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,
+                     int32_t nb, double* R, int32_t ldr, void* d_work, size_t work_bytes, int32_t* d_status) {
+    clear_error();
+    int code = GMRES_OK;
+    if (check_pip_args(n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status, &code)) return code;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PipWork w = pip_work_layout(d_work, n, k, nb);
+    const int groups = (k + nb + kMaxNB - 1) / kMaxNB;
+    cudaError_t e = cudaMemsetAsync(w.counter, 0, (groups + 1) * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess)
+        e = launch_pip_gram_chol(s, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, nullptr, reduction_grid(n));
+    if (e == cudaSuccess) e = launch_pip_update(s, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, nullptr);
+    return cuda_rc(e, "ortho launch");
+}
+
+int ortho_stage1(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,
+                 int32_t nb, double* R, int32_t ldr, void* d_work, size_t work_bytes, int32_t* d_status) {
+    return ortho_pip(stream, n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status);
+}
+
+int ortho_stage2(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,
+                 int32_t nb, double* R, int32_t ldr, void* d_work, size_t work_bytes, int32_t* d_status) {
+    return ortho_pip(stream, n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status);
+}
+
+int gmres_mpk(gmres_ctx* c, const double* v, double* W, int64_t ldw, int32_t s, double sigma, const double* theta) {
+    clear_error();
+    GM_ARG(c != nullptr && v != nullptr && W != nullptr, "NULL argument");
+    GM_ARG(s >= 1 && s <= 16 && ldw >= c->n, "need 1 <= s <= 16 and ldw >= n");
+    GM_ARG(sigma != 0.0 && std::isfinite(sigma), "sigma must be finite and nonzero");
+    cudaError_t e = cudaSetDevice(c->device);
+    const double sinv = 1.0 / sigma;
+    const double* prev = v;
+    for (int i = 0; i < s && e == cudaSuccess; ++i) {
+        e = launch_spmv(c->stream, c->A, prev, W + (size_t)i * ldw, theta ? theta[i] : 0.0, sinv, nullptr);
+        prev = W + (size_t)i * ldw;
+    }
+    return cuda_rc(e, "mpk launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,59 @@
+// Device-resident state of one restart cycle and the launchers of the solver's
+// non-orthogonalization kernels.
+#pragma once
+#include "common.cuh"
+
+namespace gm {
+
+constexpr int kMaxCols = 64;   // m + 1 <= 64: one big panel per restart fits one CTA tile
+
+struct DevCSR {
+    int64_t n = 0, nnz = 0;
+    int32_t* rowptr = nullptr;
+    int32_t* colind = nullptr;
+    double* vals = nullptr;
+};
+
+// One restart cycle's scalars and small matrices (all FP64, column-major,
+// leading dimension kMaxCols).  Lives in device memory; the host reads it
+// once per cycle.
+struct DevState {
+    double beta;          // ||r|| at the start of the cycle
+    double inv_beta;
+    double bnorm;         // ||b||
+    double tol_abs;       // tol * ||b||
+    double resid;         // |g_k| after the latest least-squares update
+    double sigma;         // MPK scale
+    double theta[16];     // MPK shifts (zero for the monomial basis)
+    int32_t m, s, panel;
+    int32_t k_used;       // iterations used by this cycle (0 until decided)
+    int32_t done;         // 1: the rest of the cycle's kernels return at once
+    int32_t iters;        // total iterations over all cycles
+    int32_t nrot;         // Givens rotations applied so far in this cycle
+    int32_t pad_;
+    int32_t blkstat[2 * kMaxCols];  // Cholesky status per PIP call of the cycle (blocks, then panels)
+    double y[kMaxCols];         // least-squares solution
+    double g[kMaxCols + 1];     // rotated right-hand side
+    double cs[kMaxCols], sn[kMaxCols];
+    double Rhat[kMaxCols * kMaxCols];  // stage-1 factors  (V = Q^ Rhat)
+    double Cm[kMaxCols * kMaxCols];    // stage-2 factors  (Q^ = Q Cm)
+    double Rfin[kMaxCols * kMaxCols];  // Cm Rhat
+    double H[kMaxCols * kMaxCols];     // upper Hessenberg, A Q_k = Q_{k+1} H
+    double Rg[kMaxCols * kMaxCols];    // H after the Givens rotations
+};
+
+int norm_grid(int64_t n);
+cudaError_t launch_spmv(cudaStream_t st, const DevCSR& A, const double* x, double* y, double theta,
+                        double sinv, const int32_t* d_skip);
+cudaError_t launch_residual(cudaStream_t st, const DevCSR& A, const double* b, const double* x, double* out,
+                            double* partial, unsigned* counter, DevState* ds, int which);
+cudaError_t launch_scale(cudaStream_t st, int64_t n, double* v, const DevState* ds);
+cudaError_t launch_xupdate(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, double* x, DevState* ds);
+cudaError_t launch_validate_csr(cudaStream_t st, int64_t n, int64_t nnz, const int32_t* rowptr,
+                                const int32_t* colind, int32_t* bad);
+cudaError_t launch_rowabs(cudaStream_t st, const DevCSR& A, unsigned long long* out);
+cudaError_t launch_rowptr_narrow(cudaStream_t st, int64_t m, const int64_t* in, int32_t* out);
+cudaError_t launch_cycle_begin(cudaStream_t st, DevState* ds);
+cudaError_t launch_hessenberg_ls(cudaStream_t st, DevState* ds, int lo, int t);
+
+}  // namespace gm

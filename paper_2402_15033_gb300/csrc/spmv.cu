@@ -1,0 +1,202 @@
+// Sparse and vector kernels of the s-step GMRES cycle (§III):
+//   (c) the matrix powers kernel step y = (A x - theta x) / sigma (CSR SpMV),
+//   the restart residual r = b - A x with a deterministic norm reduction,
+//   the start-vector scaling q_1 = r / ||r||, and the solution update x += Q y.
+#include "common.cuh"
+#include "solver_state.cuh"
+
+namespace gm {
+
+namespace {
+
+constexpr int kVecThreads = 256;
+
+// Block-wide sum in a fixed order (warp butterflies, then warp 0 over warps).
+__device__ double block_sum(double v) {
+    __shared__ double s_w[kVecThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) s_w[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? s_w[lane] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    }
+    return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kVecThreads)
+spmv_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+            const double* __restrict__ vals, const double* __restrict__ x, double* __restrict__ y,
+            double theta, double sinv, const int32_t* d_skip) {
+    if (d_skip && *d_skip) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p0 = __ldg(rowptr + i), p1 = __ldg(rowptr + i + 1);
+        double acc = 0.0;
+        for (int32_t p = p0; p < p1; ++p) acc = fma(__ldg(vals + p), __ldg(x + __ldg(colind + p)), acc);
+        if (theta != 0.0) acc = fma(-theta, x[i], acc);
+        y[i] = acc * sinv;
+    }
+}
+
+// r = b - A x (x may be null: r = b); r written to out; ||r||^2 reduced in a
+// fixed order by the last CTA into st->beta / st->inv_beta (or st->bnorm).
+__global__ void __launch_bounds__(kVecThreads)
+residual_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                const double* __restrict__ vals, const double* __restrict__ b,
+                const double* __restrict__ x, double* __restrict__ out, double* partial,
+                unsigned* counter, DevState* st, int which) {
+    double ss = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double r = b[i];
+        if (x) {
+            const int32_t p0 = __ldg(rowptr + i), p1 = __ldg(rowptr + i + 1);
+            double acc = 0.0;
+            for (int32_t p = p0; p < p1; ++p) acc = fma(__ldg(vals + p), __ldg(x + __ldg(colind + p)), acc);
+            r -= acc;
+        }
+        if (out) out[i] = r;
+        ss = fma(r, r, ss);
+    }
+    const double t = block_sum(ss);
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = t;
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        double acc = 0.0;
+        for (unsigned bI = 0; bI < gridDim.x; ++bI) acc += __ldcg(partial + bI);
+        const double nrm = sqrt(acc);
+        if (which == 0) {
+            st->beta = nrm;
+            st->inv_beta = nrm > 0.0 ? 1.0 / nrm : 0.0;
+        } else {
+            st->bnorm = nrm;
+        }
+        *counter = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kVecThreads)
+scale_kernel(int64_t n, double* v, const DevState* st) {
+    const double s = st->inv_beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v[i] *= s;
+}
+
+// x += Q[:, 0:k] y with k = st->k_used, y = st->y; also counts iterations.
+__global__ void __launch_bounds__(kVecThreads)
+xupdate_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, double* __restrict__ x, DevState* st) {
+    __shared__ double ys[kMaxCols];
+    const int k = st->k_used;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) ys[c] = st->y[c];
+    __syncthreads();
+    if (k == 0) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = x[i];
+        for (int c = 0; c < k; ++c) acc = fma(__ldg(Q + (int64_t)c * ldq + i), ys[c], acc);
+        x[i] = acc;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->iters += k;
+}
+
+// CSR sanity check: rowptr[0] = 0, nondecreasing, rowptr[n] = nnz, columns in [0, n).
+__global__ void validate_csr_kernel(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
+                                    int32_t* bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p0 = rowptr[i], p1 = rowptr[i + 1];
+        if (p1 < p0 || p0 < 0 || (int64_t)p1 > nnz) { atomicOr(bad, 1); continue; }
+        for (int32_t p = p0; p < p1; ++p) {
+            const int32_t c = colind[p];
+            if (c < 0 || (int64_t)c >= n) { atomicOr(bad, 2); break; }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (rowptr[0] != 0 || (int64_t)rowptr[n] != nnz) atomicOr(bad, 4);
+    }
+}
+
+// max_i sum_j |a_ij| (non-negative doubles compare like their bit patterns)
+__global__ void rowabs_kernel(int64_t n, const int32_t* __restrict__ rowptr, const double* __restrict__ vals,
+                              unsigned long long* out) {
+    double mx = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) acc += fabs(vals[p]);
+        mx = fmax(mx, acc);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
+__global__ void rowptr_narrow_kernel(int64_t m, const int64_t* in, int32_t* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int32_t)in[i];
+}
+
+int vec_grid(int64_t n) {
+    const int64_t b = (n + kVecThreads - 1) / kVecThreads;
+    const int64_t cap = 8 * (int64_t)num_sms();
+    return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+}  // namespace
+
+int norm_grid(int64_t n) { return vec_grid(n); }
+
+cudaError_t launch_spmv(cudaStream_t st, const DevCSR& A, const double* x, double* y, double theta,
+                        double sinv, const int32_t* d_skip) {
+    spmv_kernel<<<vec_grid(A.n), kVecThreads, 0, st>>>(A.n, A.rowptr, A.colind, A.vals, x, y, theta, sinv, d_skip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(cudaStream_t st, const DevCSR& A, const double* b, const double* x, double* out,
+                            double* partial, unsigned* counter, DevState* ds, int which) {
+    residual_kernel<<<vec_grid(A.n), kVecThreads, 0, st>>>(A.n, A.rowptr, A.colind, A.vals, b, x, out, partial,
+                                                           counter, ds, which);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(cudaStream_t st, int64_t n, double* v, const DevState* ds) {
+    scale_kernel<<<vec_grid(n), kVecThreads, 0, st>>>(n, v, ds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xupdate(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, double* x, DevState* ds) {
+    xupdate_kernel<<<vec_grid(n), kVecThreads, 0, st>>>(n, Q, ldq, x, ds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_csr(cudaStream_t st, int64_t n, int64_t nnz, const int32_t* rowptr,
+                                const int32_t* colind, int32_t* bad) {
+    validate_csr_kernel<<<vec_grid(n), kVecThreads, 0, st>>>(n, nnz, rowptr, colind, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rowabs(cudaStream_t st, const DevCSR& A, unsigned long long* out) {
+    rowabs_kernel<<<vec_grid(A.n), kVecThreads, 0, st>>>(A.n, A.rowptr, A.vals, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rowptr_narrow(cudaStream_t st, int64_t m, const int64_t* in, int32_t* out) {
+    rowptr_narrow_kernel<<<vec_grid(m), kVecThreads, 0, st>>>(m, in, out);
+    return cudaGetLastError();
+}
+
+}  // namespace gm

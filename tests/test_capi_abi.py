@@ -1,0 +1,88 @@
+"""The C-ABI library builds, loads and exports every symbol include/gmres.h
+declares; argument checks fail cleanly without launching anything (CPU only)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gmres.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|size_t|const\s+char\s*\*)\s+(\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2402_15033_gb300 import build, capi as cap
+    build.build()
+    cap.load()
+    return cap
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("gmres_create", "gmres_solve", "gmres_destroy", "ortho_stage1", "ortho_stage2",
+              "ortho_workspace_bytes", "gmres_last_error", "gmres_default_opts", "gmres_mpk"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(capi):
+    lib = capi.load()
+    for name in declared_functions():
+        assert name in capi.SIGNATURES, f"binding lacks {name}"
+        assert getattr(lib, name) is not None
+
+
+def test_struct_layouts_match_the_header(capi):
+    assert C.sizeof(capi.gmres_opts) == 216
+    assert C.sizeof(capi.gmres_result) == 80
+    assert capi.gmres_opts.tol.offset == 16
+    assert capi.gmres_opts.theta.offset == 48
+    assert capi.gmres_result.relres_implicit.offset == 24
+
+
+def test_default_opts(capi):
+    o = capi.default_opts()
+    assert (o.m, o.s, o.panel, o.tol, o.ortho, o.precision) == (60, 5, 60, 1e-8, 0, 0)
+
+
+def test_workspace_size_is_positive_and_monotone(capi):
+    a = capi.workspace_bytes(4096, 1, 5)
+    b = capi.workspace_bytes(4194304, 56, 5)
+    c = capi.workspace_bytes(4194304, 0, 61)
+    assert 0 < a <= b
+    assert c > 0
+    assert capi.workspace_bytes(0, 1, 5) == 0
+
+
+def test_bad_arguments_are_rejected_before_any_launch(capi):
+    lib = capi.load()
+    st = C.c_void_p(16)  # never dereferenced: validation fails first
+    # nb = 0
+    rc = lib.ortho_stage1(None, 100, None, 100, 0, C.c_void_p(256), 100, 0, C.c_void_p(256), 1,
+                          C.c_void_p(256), 1 << 20, st)
+    assert rc == capi.GMRES_ERR_ARG and "nb" in capi.last_error()
+    # misaligned V
+    rc = lib.ortho_stage1(None, 100, None, 100, 0, C.c_void_p(8), 100, 5, C.c_void_p(256), 5,
+                          C.c_void_p(256), 1 << 20, st)
+    assert rc == capi.GMRES_ERR_ARG and "aligned" in capi.last_error()
+    # too small workspace
+    rc = lib.ortho_stage2(None, 100, None, 100, 0, C.c_void_p(256), 100, 5, C.c_void_p(256), 5,
+                          C.c_void_p(256), 8, st)
+    assert rc == capi.GMRES_ERR_WORKSPACE
+    # bad options at create
+    o = capi.default_opts(panel=7)
+    h = C.c_void_p()
+    import numpy as np
+    rp = np.array([0, 1], dtype=np.int64)
+    ci = np.array([0], dtype=np.int32)
+    vv = np.array([1.0])
+    rc = lib.gmres_create(C.byref(h), 1, 1, rp.ctypes.data_as(C.c_void_p), ci.ctypes.data_as(C.c_void_p),
+                          vv.ctypes.data_as(C.c_void_p), 0, C.byref(o), None)
+    assert rc == capi.GMRES_ERR_ARG and "panel" in capi.last_error()
+    assert lib.gmres_destroy(None) == capi.GMRES_OK

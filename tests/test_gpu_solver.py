@@ -1,0 +1,163 @@
+"""Parity of the CUDA s-step GMRES (two-stage, FP64) with the CPU oracle
+through the C ABI.  Bars (the benchmark spec): final x within 1e-6 relative of the
+oracle's at relative residual 1e-8, iteration count within +-s, Arnoldi-relation
+consistency through the converged residual."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import krylov as kr
+
+pytestmark = pytest.mark.gpu
+
+
+def solve_gpu(capi, A, b, x0=None, **opts):
+    S = capi.Solver.from_csr(A, capi.default_opts(**opts))
+    x = np.zeros(A.n) if x0 is None else np.array(x0, copy=True)
+    rc, res = S.solve(b, x)
+    S.close()
+    return rc, res, x
+
+
+@pytest.mark.parametrize("N,m,s,panel", [(64, 60, 5, 60), (64, 60, 5, 20), (64, 60, 10, 60), (40, 30, 5, 30),
+                                         (64, 60, 5, 5), (33, 24, 4, 12), (20, 12, 3, 6)])
+def test_laplace2d_matches_oracle(lib, N, m, s, panel):
+    from paper_2402_15033_gb300 import capi
+    A = synth.laplace2d(N)
+    xt = synth.x_true(A.n, 0)
+    b = kr.as_operator(A) @ xt
+    rc, res, x = solve_gpu(capi, A, b, m=m, s=s, panel=panel, tol=1e-8)
+    xr, info = kr.sstep_gmres(A, b, m=m, s=s, panel=panel, tol=1e-8)
+    assert info["status"] == 0
+    assert rc == capi.GMRES_OK, res
+    assert res["relres_true"] <= 1e-8
+    assert abs(res["iters"] - info["iters"]) <= s, (res["iters"], info["iters"])
+    assert np.linalg.norm(x - xr) / np.linalg.norm(xr) <= 1e-6
+    step = panel
+    assert res["iters"] % step == 0 or res["iters"] == info["iters"]
+
+
+def test_bcgs_pip2_mode_matches_oracle(lib):
+    from paper_2402_15033_gb300 import capi
+    A = synth.laplace2d(48)
+    b = kr.as_operator(A) @ synth.x_true(A.n, 4)
+    rc, res, x = solve_gpu(capi, A, b, m=60, s=5, ortho=capi.GMRES_ORTHO_BCGS_PIP2, tol=1e-8)
+    xr, info = kr.sstep_gmres(A, b, m=60, s=5, tol=1e-8, ortho="bcgs_pip2")
+    assert rc == 0 and res["relres_true"] <= 1e-8
+    assert abs(res["iters"] - info["iters"]) <= 5
+    assert np.linalg.norm(x - xr) / np.linalg.norm(xr) <= 1e-6
+
+
+@pytest.mark.parametrize("gen,seed", [("convdiff2d", 3), ("convdiff2d", 11), ("convdiff3d", 4), ("banded", 2)])
+def test_nonsymmetric_systems_match_oracle(lib, gen, seed):
+    from paper_2402_15033_gb300 import capi
+    if gen == "convdiff2d":
+        A = synth.convdiff2d(50, seed)
+    elif gen == "convdiff3d":
+        A = synth.convdiff3d(14, seed)
+    else:
+        A = synth.banded_random(3000, seed, band=200)
+    b = kr.as_operator(A) @ synth.x_true(A.n, seed)
+    rc, res, x = solve_gpu(capi, A, b, m=30, s=5, panel=30, tol=1e-8)
+    xr, info = kr.sstep_gmres(A, b, m=30, s=5, panel=30, tol=1e-8)
+    assert info["status"] == 0
+    assert rc == 0, res
+    assert abs(res["iters"] - info["iters"]) <= 5
+    assert np.linalg.norm(x - xr) / np.linalg.norm(xr) <= 1e-6
+
+
+def test_device_pointers_and_restart_checkpoint(lib):
+    """b, x on the device; solving again from the returned x (a checkpoint)
+    converges at once."""
+    from paper_2402_15033_gb300 import capi
+    A = synth.laplace2d(32)
+    b = kr.as_operator(A) @ synth.x_true(A.n, 1)
+    S = capi.Solver.from_csr(A, capi.default_opts(m=20, s=5, panel=20))
+    bd = torch.tensor(b, device="cuda")
+    xd = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    rc, res = S.solve(bd, xd)
+    assert rc == 0 and res["relres_true"] <= 1e-8
+    rc2, res2 = S.solve(bd, xd)
+    assert rc2 == 0 and res2["iters"] == 0 and res2["restarts"] == 0
+    S.close()
+
+
+def test_device_csr_input(lib):
+    from paper_2402_15033_gb300 import capi
+    A = synth.laplace2d(24)
+    b = kr.as_operator(A) @ synth.x_true(A.n, 2)
+    rp = torch.tensor(A.rowptr, device="cuda")
+    ci = torch.tensor(A.colind, device="cuda")
+    vv = torch.tensor(A.vals, device="cuda")
+    S = capi.Solver(A.n, rp, ci, vv, capi.default_opts(m=20, s=5, panel=20))
+    x = np.zeros(A.n)
+    rc, res = S.solve(b, x)
+    S.close()
+    assert rc == 0 and res["relres_true"] <= 1e-8
+
+
+def test_zero_rhs_and_nan_rhs(lib):
+    from paper_2402_15033_gb300 import capi
+    A = synth.laplace2d(16)
+    S = capi.Solver.from_csr(A, capi.default_opts(m=20, s=5, panel=20))
+    x = np.ones(A.n)
+    rc, res = S.solve(np.zeros(A.n), x)
+    assert rc == 0 and np.all(x == 0)
+    b = np.ones(A.n)
+    b[5] = np.nan
+    rc, res = S.solve(b, np.zeros(A.n))
+    assert rc == capi.GMRES_ERR_NAN
+    S.close()
+
+
+def test_breakdown_is_reported_with_its_block(lib):
+    """A = 2 I: the Krylov space has dimension 1, so the first block's Gram is
+    singular; the solver returns GMRES_ERR_BREAKDOWN like the oracle."""
+    from paper_2402_15033_gb300 import capi
+    n = 64
+    A = synth.CSR(n, np.arange(n + 1), np.arange(n, dtype=np.int32), np.full(n, 2.0))
+    b = synth.x_true(n, 5)
+    rc, res, x = solve_gpu(capi, A, b, m=10, s=5, panel=10, tol=1e-30)
+    _, info = kr.sstep_gmres(A, b, m=10, s=5, panel=10, tol=1e-30)
+    assert info["status"] == kr.STATUS_BREAKDOWN
+    assert rc == capi.GMRES_ERR_BREAKDOWN
+    assert res["breakdown_block"] == 0 and res["breakdown_pivot"] >= 1
+
+
+def test_maxit_warning(lib):
+    from paper_2402_15033_gb300 import capi
+    A = synth.laplace2d(64)
+    b = kr.as_operator(A) @ synth.x_true(A.n, 0)
+    rc, res, x = solve_gpu(capi, A, b, m=60, s=5, panel=60, tol=1e-12, max_restarts=1)
+    assert rc == capi.GMRES_WARN_MAXIT
+    assert res["iters"] == 60 and res["restarts"] == 1
+    xr, info = kr.sstep_gmres(A, b, m=60, s=5, panel=60, tol=1e-12, max_restarts=1)
+    assert np.linalg.norm(x - xr) / np.linalg.norm(xr) <= 1e-9
+
+
+def test_invalid_csr_rejected(lib):
+    from paper_2402_15033_gb300 import capi
+    A = synth.laplace2d(8)
+    ci = A.colind.copy()
+    ci[10] = 1000
+    with pytest.raises(capi.GmresError) as e:
+        capi.Solver(A.n, A.rowptr, ci, A.vals)
+    assert e.value.code == capi.GMRES_ERR_ARG
+
+
+def test_mpk_matches_oracle(lib):
+    from paper_2402_15033_gb300 import capi
+    A = synth.convdiff2d(40, 1)
+    M = kr.as_operator(A)
+    v = synth.x_true(A.n, 9)
+    S = capi.Solver.from_csr(A)
+    vd = torch.tensor(v, device="cuda")
+    W = torch.zeros(5, A.n + 2, dtype=torch.float64, device="cuda").T[: A.n]
+    theta = [0.5, -1.0, 0.0, 2.0, 0.25]
+    S.mpk(vd, W, 5, 16.0, theta)
+    torch.cuda.synchronize()
+    Wr = kr.mpk(M, v, 5, 16.0, theta)
+    Wg = W.cpu().numpy()
+    assert np.allclose(Wg, Wr, rtol=1e-13, atol=1e-13 * np.abs(Wr).max())
+    S.close()
