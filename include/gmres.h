@@ -145,6 +145,22 @@ int ortho_stage2(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t 
                  double* V, int64_t ldv, int32_t nb, double* R, int32_t ldr,
                  void* d_work, size_t work_bytes, int32_t* d_status);
 
+/* The two halves of one BCGS-PIP, for callers that schedule or time them
+ * separately; ortho_stage1/ortho_stage2 are exactly ortho_gram_chol followed
+ * by ortho_update on the same stream with the same arguments.
+ *   ortho_gram_chol: [P; G] = [Q, V]^T V and T = Chol(G - P^T P) into R, the
+ *                    status into d_status (V is only read).
+ *   ortho_update:    V <- (V - Q P) T^{-1} with P, T read from R; does nothing
+ *                    when *d_status != 0.  d_work is not used.
+ * Arguments, limits and errors as for ortho_stage1. */
+int ortho_gram_chol(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
+                    const double* V, int64_t ldv, int32_t nb, double* R, int32_t ldr,
+                    void* d_work, size_t work_bytes, int32_t* d_status);
+
+int ortho_update(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
+                 double* V, int64_t ldv, int32_t nb, const double* R, int32_t ldr,
+                 const int32_t* d_status);
+
 /* ------------------------------------------------ matrix powers kernel
  * MPK of §III (standard, not communication-avoiding): s products in sequence,
  * W[:,0] = (A v - theta_0 v) / sigma, W[:,i] = (A W[:,i-1] - theta_i W[:,i-1]) / sigma,

@@ -202,7 +202,9 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
     ``panel`` is the second step size s^ of the two-stage scheme (§V); it must
     satisfy s | s^ | m.  ``ortho`` in {"two_stage", "bcgs_pip2", "bcgs2_cholqr2"}.
     Returns (x, info dict) with status, iteration count (SpMVs inside restart
-    cycles), restarts, the explicit relative residual and, when
+    cycles), restarts, the explicit relative residual, the breakdown location
+    (``breakdown_block``: s-step block j, or m/s + p for the stage 2 of big
+    panel p; ``breakdown_pivot``: 1-based), and, when
     ``return_basis``, the last cycle's Q, H and g0 (for Arnoldi-relation tests)."""
     M = as_operator(A)
     n = b.shape[0]
@@ -221,6 +223,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
     status = STATUS_MAXIT
     last = {}
     err_where = None
+    breakdown = (-1, 0)
     for cyc in range(max_restarts):
         r = b - M @ x
         beta = np.linalg.norm(r)
@@ -250,8 +253,10 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
         gv = None
         k_used = 0
         done = False
+        where_blk = 0
         try:
             for j in range(m // s):
+                where_blk = j
                 st = s * j
                 start_final[st] = final[st]
                 W = mpk(M, Q[:, st], s, sig, theta)
@@ -264,6 +269,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
                     t = st + s
                     if t < hi:
                         continue
+                    where_blk = m // s + (t // panel) - 1
                     Qn, P2, T2 = bo.stage2(Q[:, :lo], Q[:, lo:t + 1], f"cycle{cyc}/stage2@{t}")
                     Q[:, lo:t + 1] = Qn
                     C[:lo, lo:t + 1] = P2
@@ -296,6 +302,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
         except bo.Breakdown as e:
             status = STATUS_BREAKDOWN
             err_where = str(e)
+            breakdown = (where_blk, e.pivot)
             break
         y = gv.solve()
         x = x + Q[:, :k_used] @ y
@@ -305,7 +312,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
         r = b - M @ x
         hist.append(np.linalg.norm(r) / bnorm)
     info = dict(status=status, iters=iters, restarts=restarts, relres=hist[-1], history=hist,
-                sigma=sig, where=err_where)
+                sigma=sig, where=err_where, breakdown_block=breakdown[0], breakdown_pivot=breakdown[1])
     if return_basis:
         info.update(last)
     return x, info

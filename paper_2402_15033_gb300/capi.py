@@ -64,6 +64,8 @@ SIGNATURES = {
     "ortho_stage1": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "ortho_stage2": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "gmres_mpk": (_i32, [_vp, _vp, _vp, _i64, _i32, _dbl, C.POINTER(_dbl)]),
+    "ortho_gram_chol": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
+    "ortho_update": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp]),
 }
 
 _lib = None
@@ -189,6 +191,23 @@ def _ortho(fn, Q, V, R, work, status, k, stream):
     return fn(C.c_void_p(stream or 0), int(n), qp, int(ldq), int(k), C.c_void_p(V.data_ptr()), int(ldv), int(nb),
               C.c_void_p(R.data_ptr()), int(R.stride(1)), C.c_void_p(work.data_ptr()), int(work.numel()),
               C.c_void_p(status.data_ptr()))
+
+
+def ortho_gram_chol(Q, V, R, work, status, k=None, stream=None):
+    """First half of BCGS-PIP: [P; G] = [Q, V]^T V and T = Chol(G - P^T P) into R."""
+    k = (Q.shape[1] if Q is not None else 0) if k is None else k
+    return check(_ortho(load().ortho_gram_chol, Q, V, R, work, status, k, stream))
+
+
+def ortho_update(Q, V, R, status, k=None, stream=None):
+    """Second half of BCGS-PIP: V <- (V - Q P) T^{-1}."""
+    k = (Q.shape[1] if Q is not None else 0) if k is None else k
+    n, nb = V.shape
+    ldq = Q.stride(1) if (Q is not None and k > 0) else n
+    qp = C.c_void_p(Q.data_ptr()) if (Q is not None and k > 0) else None
+    return check(load().ortho_update(C.c_void_p(stream or 0), int(n), qp, int(ldq), int(k),
+                                     C.c_void_p(V.data_ptr()), int(V.stride(1)), int(nb),
+                                     C.c_void_p(R.data_ptr()), int(R.stride(1)), C.c_void_p(status.data_ptr())))
 
 
 def ortho_stage1(Q, V, R, work, status, k=None, stream=None):

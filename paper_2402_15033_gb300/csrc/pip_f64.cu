@@ -446,19 +446,22 @@ cudaError_t launch_pip_update(cudaStream_t st, int64_t n, const double* Q, int64
 }
 
 PipWork pip_work_layout(void* base, int64_t n, int k, int nb) {
+    // The arrival counters sit at a fixed offset so that calls of different
+    // shapes sharing one workspace never overwrite each other's counters; the
+    // Gram and partial regions are rewritten in full by every call.
     PipWork w{};
     const int grid = reduction_grid(n);
     const int kx = k + nb;
     const int groups = (kx + kMaxNB - 1) / kMaxNB;
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    const size_t b_partial = up((size_t)grid * groups * kMaxNB * nb * sizeof(double));
-    const size_t b_counter = up((size_t)(groups + 1) * sizeof(unsigned));
+    const size_t b_counter = 256;
     const size_t b_gram = up((size_t)kx * nb * sizeof(double));
+    const size_t b_partial = up((size_t)grid * groups * kMaxNB * nb * sizeof(double));
     char* p = static_cast<char*>(base);
-    w.partial = reinterpret_cast<double*>(p);
-    w.counter = reinterpret_cast<unsigned*>(p + b_partial);
-    w.gram = reinterpret_cast<double*>(p + b_partial + b_counter);
-    w.bytes = b_partial + b_counter + b_gram;
+    w.counter = reinterpret_cast<unsigned*>(p);
+    w.gram = reinterpret_cast<double*>(p + b_counter);
+    w.partial = reinterpret_cast<double*>(p + b_counter + b_gram);
+    w.bytes = b_counter + b_gram + b_partial;
     return w;
 }
 

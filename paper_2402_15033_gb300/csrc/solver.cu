@@ -487,13 +487,44 @@ static int ortho_pip(void* stream, int64_t n, const double* Q, int64_t ldq, int3
     if (check_pip_args(n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status, &code)) return code;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PipWork w = pip_work_layout(d_work, n, k, nb);
-    const int groups = (k + nb + kMaxNB - 1) / kMaxNB;
-    cudaError_t e = cudaMemsetAsync(w.counter, 0, (groups + 1) * sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(w.counter, 0, 256, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(int32_t), s);
     if (e == cudaSuccess)
         e = launch_pip_gram_chol(s, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, nullptr, reduction_grid(n));
     if (e == cudaSuccess) e = launch_pip_update(s, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, nullptr);
     return cuda_rc(e, "ortho launch");
+}
+
+int ortho_gram_chol(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, const double* V,
+                    int64_t ldv, int32_t nb, double* R, int32_t ldr, void* d_work, size_t work_bytes,
+                    int32_t* d_status) {
+    clear_error();
+    int code = GMRES_OK;
+    if (check_pip_args(n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status, &code)) return code;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PipWork w = pip_work_layout(d_work, n, k, nb);
+    cudaError_t e = cudaMemsetAsync(w.counter, 0, 256, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess)
+        e = launch_pip_gram_chol(s, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, nullptr, reduction_grid(n));
+    return cuda_rc(e, "gram launch");
+}
+
+int ortho_update(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,
+                 int32_t nb, const double* R, int32_t ldr, const int32_t* d_status) {
+    clear_error();
+    int code = GMRES_OK;
+    // workspace is not used by the update: pass a dummy that satisfies the checks
+    GM_ARG(n >= 1, "n must be >= 1");
+    GM_ARG(k >= 0 && nb >= 1 && nb <= kMaxNB && k + nb <= kMaxKX, "need k >= 0, 1 <= nb <= 64, k + nb <= 256");
+    GM_ARG(k == 0 || (Q != nullptr && ldq >= n), "Q must be non-NULL with ldq >= n when k > 0");
+    GM_ARG(V != nullptr && ldv >= n, "V must be non-NULL with ldv >= n");
+    GM_ARG(R != nullptr && ldr >= k + nb, "R must be non-NULL with ldr >= k + nb");
+    GM_ARG(d_status != nullptr, "d_status is NULL");
+    (void)code;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_pip_update(s, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, nullptr);
+    return cuda_rc(e, "update launch");
 }
 
 int ortho_stage1(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,

@@ -113,13 +113,13 @@ def test_two_stage_sequence_matches_oracle_on_ill_conditioned_panels(lib):
 
 
 def test_breakdown_status_and_v_untouched(lib):
-    """A block with a repeated column has a singular Gram (violates Eq. (1)):
+    """A block with a zero column has a singular Gram (violates Eq. (1)):
     d_status reports the 1-based pivot and V is left unchanged."""
     from paper_2402_15033_gb300 import capi
     g = synth.rng(7)
     n = 500
     V = g.standard_normal((n, 5))
-    V[:, 3] = V[:, 1]
+    V[:, 3] = 0.0
     Vg, Rg, st = run_pip(capi, None, V, stage=1)
     assert st == 4
     assert np.array_equal(Vg, V)
