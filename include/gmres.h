@@ -145,6 +145,25 @@ int ortho_stage2(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t 
                  double* V, int64_t ldv, int32_t nb, double* R, int32_t ldr,
                  void* d_work, size_t work_bytes, int32_t* d_status);
 
+/* Stage 1 for callers that cannot allocate device memory.  No counterpart in
+ * the paper: it is ortho_stage1 without the d_work argument, for code that
+ * runs inside another framework's memory arena (which owns all device memory
+ * and forbids cudaMalloc), plug-ins whose host program exposes no allocator,
+ * and latency-critical loops that cannot pay the device-wide synchronization
+ * of cudaMalloc/cudaFree.  Its scratch is a 2.5 MiB array that the library
+ * owns in device memory; every GPU that loads the library keeps it until the
+ * process exits.  Limits: nb <= 16 and k + nb <= 64 (any n); larger blocks
+ * get GMRES_ERR_ARG with a message.  It calls no allocator: no cudaMalloc,
+ * cudaFree or allocating library routine.
+ * Set-up: the first call on a device (with that device current) looks up the
+ * array's device address once; make that first call before any stream
+ * capture.  Every call shares the one array: calls that may overlap on the
+ * GPU (different streams, or different host threads) race and must be
+ * serialized by the caller.  Arguments otherwise as for ortho_stage1. */
+int ortho_stage1_noalloc(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
+                         double* V, int64_t ldv, int32_t nb, double* R, int32_t ldr,
+                         int32_t* d_status);
+
 /* The two halves of one BCGS-PIP, for callers that schedule or time them
  * separately; ortho_stage1/ortho_stage2 are exactly ortho_gram_chol followed
  * by ortho_update on the same stream with the same arguments.

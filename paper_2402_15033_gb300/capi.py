@@ -66,6 +66,7 @@ SIGNATURES = {
     "gmres_mpk": (_i32, [_vp, _vp, _vp, _i64, _i32, _dbl, C.POINTER(_dbl)]),
     "ortho_gram_chol": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "ortho_update": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp]),
+    "ortho_stage1_noalloc": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp]),
 }
 
 _lib = None
@@ -208,6 +209,20 @@ def ortho_update(Q, V, R, status, k=None, stream=None):
     return check(load().ortho_update(C.c_void_p(stream or 0), int(n), qp, int(ldq), int(k),
                                      C.c_void_p(V.data_ptr()), int(V.stride(1)), int(nb),
                                      C.c_void_p(R.data_ptr()), int(R.stride(1)), C.c_void_p(status.data_ptr())))
+
+
+def ortho_stage1_noalloc(Q, V, R, status, k=None, stream=None):
+    """Stage 1 without a caller workspace, for callers that cannot allocate
+    device memory: the scratch is a fixed array inside the library (nb <= 16,
+    k + nb <= 64).  Calls that overlap on the GPU share that array and race."""
+    k = (Q.shape[1] if Q is not None else 0) if k is None else k
+    n, nb = V.shape
+    ldq = Q.stride(1) if (Q is not None and k > 0) else n
+    qp = C.c_void_p(Q.data_ptr()) if (Q is not None and k > 0) else None
+    return check(load().ortho_stage1_noalloc(C.c_void_p(stream or 0), int(n), qp, int(ldq), int(k),
+                                             C.c_void_p(V.data_ptr()), int(V.stride(1)), int(nb),
+                                             C.c_void_p(R.data_ptr()), int(R.stride(1)),
+                                             C.c_void_p(status.data_ptr())))
 
 
 def ortho_stage1(Q, V, R, work, status, k=None, stream=None):
