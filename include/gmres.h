@@ -69,7 +69,9 @@ typedef struct gmres_result {
     int32_t status;            /* same value gmres_solve returned                          */
     int32_t iters;             /* Krylov iterations (SpMVs inside restart cycles)          */
     int32_t restarts;          /* restart cycles run                                       */
-    int32_t ir_steps;          /* FP64 refinement steps (mixed precision), else 0          */
+    int32_t ir_steps;          /* mixed precision: FP64 refinement steps (one per restart  */
+                               /* cycle: r = b - A x in FP64, A d = r solved with the FP32 */
+                               /* basis, x += d in FP64), else 0                           */
     int32_t breakdown_block;   /* s-step block index of a GMRES_ERR_BREAKDOWN, else -1     */
     int32_t breakdown_pivot;   /* 1-based Cholesky pivot of that breakdown, else 0         */
     double  relres_implicit;   /* |g_{k+1}| / ||b|| of the last least-squares solve        */
@@ -145,6 +147,19 @@ int ortho_stage2(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t 
                  double* V, int64_t ldv, int32_t nb, double* R, int32_t ldr,
                  void* d_work, size_t work_bytes, int32_t* d_status);
 
+/* FP32-basis variants (the mixed-precision pattern): Q and V are FP32, every
+ * product and sum is formed in FP64 (FP32 inputs widen exactly), R and the
+ * Cholesky factor are FP64, and the updated block is rounded to FP32.  Same
+ * arguments, limits and errors as ortho_stage1/ortho_stage2 otherwise (ld a
+ * multiple of 4). */
+int ortho_stage1_f32(void* stream, int64_t n, const float* Q, int64_t ldq, int32_t k,
+                     float* V, int64_t ldv, int32_t nb, double* R, int32_t ldr,
+                     void* d_work, size_t work_bytes, int32_t* d_status);
+
+int ortho_stage2_f32(void* stream, int64_t n, const float* Q, int64_t ldq, int32_t k,
+                     float* V, int64_t ldv, int32_t nb, double* R, int32_t ldr,
+                     void* d_work, size_t work_bytes, int32_t* d_status);
+
 /* Stage 1 for callers that cannot allocate device memory.  No counterpart in
  * the paper: it is ortho_stage1 without the d_work argument, for code that
  * runs inside another framework's memory arena (which owns all device memory
@@ -185,7 +200,8 @@ int ortho_update(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t 
  * W[:,0] = (A v - theta_0 v) / sigma, W[:,i] = (A W[:,i-1] - theta_i W[:,i-1]) / sigma,
  * with the context's matrix.  v[n] and W (n x s, ldw >= n) are device FP64;
  * theta is a HOST array of s shifts, or NULL for the monomial basis; sigma is
- * finite and nonzero.  Asynchronous on the context's stream. */
+ * finite and nonzero; the context must be FP64 (GMRES_ERR_ARG otherwise).
+ * Asynchronous on the context's stream. */
 int gmres_mpk(gmres_ctx* c, const double* v, double* W, int64_t ldw, int32_t s,
               double sigma, const double* theta);
 

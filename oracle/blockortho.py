@@ -123,6 +123,27 @@ def stage1(Qacc: np.ndarray, V: np.ndarray, where: str = "stage1"):
     return bcgs_pip(Qacc, V, where)
 
 
+def stage1_lowp(Qacc: np.ndarray, V: np.ndarray, where: str = "stage1", store=np.float32):
+    """First stage for a basis stored in lower precision (the mixed-precision
+    pattern).  The block Pythagorean identity G - P^T P of BCGS-PIP assumes the
+    stored basis is orthonormal; an FP32-stored basis is orthonormal only to
+    about eps32, so the identity cancels to a non-positive pivot as soon as a
+    new MPK vector's component outside the basis falls below ~sqrt(eps32) of
+    its norm.  Here the projected block's Gram is formed explicitly instead:
+    P = Q^T V (FP64 products of the stored values); W = V - Q P rounded to the
+    storage precision; T = Chol(W^T W) in FP64 (the higher-precision Gram of
+    the mixed-precision CholQR of §II); Q^ = W T^{-1} rounded to storage.
+    Inputs are the stored (FP32) values widened to FP64.  Returns
+    (Q^ in FP64 holding storage-precision values, P, T)."""
+    P = Qacc.T @ V
+    W = (V - Qacc @ P).astype(store).astype(np.float64)
+    G = W.T @ W
+    T, info = chol_upper(G)
+    if info:
+        raise Breakdown(info, where)
+    return right_trsm_upper(W, T).astype(store).astype(np.float64), P, T
+
+
 def stage2(Qfin: np.ndarray, Qhat: np.ndarray, where: str = "stage2"):
     """Second stage (§V, Fig. 5): BCGS-PIP of the pre-processed big panel
     Q^_{l:t} against the finished basis Q_{1:l-1}.  With l = 1 (big panel equal

@@ -59,13 +59,14 @@ def mpk(M, v: np.ndarray, s: int, sigma: float, theta=None) -> np.ndarray:
     s sparse matrix-vector products in sequence, w_1 = (A v - theta_0 v)/sigma,
     w_i = (A w_{i-1} - theta_{i-1} w_{i-1})/sigma.  Returns the n x s block."""
     n = v.shape[0]
-    W = np.zeros((n, s))
+    dt = v.dtype
+    W = np.zeros((n, s), dtype=dt)
     prev = v
     for i in range(s):
         y = M @ prev
         if theta is not None and theta[i] != 0.0:
-            y = y - theta[i] * prev
-        W[:, i] = y / sigma
+            y = y - dt.type(theta[i]) * prev
+        W[:, i] = y / dt.type(sigma)
         prev = W[:, i]
     return W
 
@@ -196,11 +197,21 @@ def hessenberg_columns(Rfin, C, start_final, s, sigma, theta, c_lo, c_hi, H):
 
 
 def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=1000,
-                ortho="two_stage", sigma=None, theta=None, return_basis=False):
+                ortho="two_stage", sigma=None, theta=None, return_basis=False, basis_dtype=np.float64):
     """s-step GMRES (Fig. 1, §III) with the chosen block orthogonalization.
 
     ``panel`` is the second step size s^ of the two-stage scheme (§V); it must
     satisfy s | s^ | m.  ``ortho`` in {"two_stage", "bcgs_pip2", "bcgs2_cholqr2"}.
+    ``basis_dtype=np.float32`` is the mixed-precision pattern: the basis is
+    stored in FP32 and the MPK runs in FP32 on an FP32 copy of A, while every
+    Gram product and sum, the Cholesky factors, the Hessenberg/Givens work, x
+    and the restart residual stay FP64 (higher-precision Gram accumulation, as
+    in the mixed-precision CholQR of §II).  Stage 1 then forms the projected
+    block's Gram explicitly (``blockortho.stage1_lowp``) because the
+    Pythagorean identity assumes an orthonormal stored basis.  Each restart
+    cycle is one FP64 iterative-refinement step: r = b - A x in FP64, A d = r
+    solved with the FP32 basis, x += d.
+
     Returns (x, info dict) with status, iteration count (SpMVs inside restart
     cycles), restarts, the explicit relative residual, the breakdown location
     (``breakdown_block``: s-step block j, or m/s + p for the stage 2 of big
@@ -208,6 +219,9 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
     ``return_basis``, the last cycle's Q, H and g0 (for Arnoldi-relation tests)."""
     M = as_operator(A)
     n = b.shape[0]
+    lowp = np.dtype(basis_dtype) == np.float32
+    Mb = M.astype(np.float32) if lowp else M
+    f64 = np.float64
     if panel is None:
         panel = m
     if ortho != "two_stage":
@@ -235,7 +249,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
             status = STATUS_OK
             break
         restarts += 1
-        Q = np.zeros((n, m + 1))
+        Q = np.zeros((n, m + 1), dtype=basis_dtype)
         Q[:, 0] = r / beta
         Rhat = np.zeros((m + 1, m + 1))
         Rhat[0, 0] = 1.0
@@ -259,10 +273,11 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
                 where_blk = j
                 st = s * j
                 start_final[st] = final[st]
-                W = mpk(M, Q[:, st], s, sig, theta)
+                W = mpk(Mb, Q[:, st], s, sig, theta)
                 cols = slice(st + 1, st + s + 1)
                 if ortho == "two_stage":
-                    Qh, P, T = bo.stage1(Q[:, : st + 1], W, f"cycle{cyc}/block{j}")
+                    st1 = bo.stage1_lowp if lowp else bo.stage1
+                    Qh, P, T = st1(Q[:, : st + 1].astype(f64), W.astype(f64), f"cycle{cyc}/block{j}")
                     Q[:, cols] = Qh
                     Rhat[: st + 1, cols] = P
                     Rhat[cols, cols] = T
@@ -270,7 +285,8 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
                     if t < hi:
                         continue
                     where_blk = m // s + (t // panel) - 1
-                    Qn, P2, T2 = bo.stage2(Q[:, :lo], Q[:, lo:t + 1], f"cycle{cyc}/stage2@{t}")
+                    Qn, P2, T2 = bo.stage2(Q[:, :lo].astype(f64), Q[:, lo:t + 1].astype(f64),
+                                           f"cycle{cyc}/stage2@{t}")
                     Q[:, lo:t + 1] = Qn
                     C[:lo, lo:t + 1] = P2
                     C[lo:t + 1, lo:t + 1] = T2
@@ -282,7 +298,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
                     lo, hi = t + 1, t + panel
                 else:
                     fn = bo.bcgs_pip2 if ortho == "bcgs_pip2" else bo.bcgs2_cholqr2
-                    Qj, P, T = fn(Q[:, : st + 1], W, f"cycle{cyc}/block{j}")
+                    Qj, P, T = fn(Q[:, : st + 1].astype(f64), W.astype(f64), f"cycle{cyc}/block{j}")
                     Q[:, cols] = Qj
                     Rfin[: st + 1, cols] = P
                     Rfin[cols, cols] = T
@@ -305,7 +321,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
             breakdown = (where_blk, e.pivot)
             break
         y = gv.solve()
-        x = x + Q[:, :k_used] @ y
+        x = x + Q[:, :k_used].astype(f64) @ y
         iters += k_used
         last = dict(Q=Q, H=H, g0=beta * C[0, 0], k=k_used, Rfin=Rfin, C=C)
     else:

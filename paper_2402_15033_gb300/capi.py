@@ -66,6 +66,8 @@ SIGNATURES = {
     "gmres_mpk": (_i32, [_vp, _vp, _vp, _i64, _i32, _dbl, C.POINTER(_dbl)]),
     "ortho_gram_chol": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "ortho_update": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp]),
+    "ortho_stage1_f32": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
+    "ortho_stage2_f32": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "ortho_stage1_noalloc": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp]),
 }
 
@@ -230,6 +232,18 @@ def ortho_stage1(Q, V, R, work, status, k=None, stream=None):
     Tensors are column-major views (``t.T`` of a row-major (cols, ld) tensor)."""
     k = (Q.shape[1] if Q is not None else 0) if k is None else k
     return check(_ortho(load().ortho_stage1, Q, V, R, work, status, k, stream))
+
+
+def ortho_stage1_f32(Q, V, R, work, status, k=None, stream=None):
+    """Stage 1 on an FP32 basis (FP64 products and sums, FP64 R, FP32 result)."""
+    k = (Q.shape[1] if Q is not None else 0) if k is None else k
+    return check(_ortho(load().ortho_stage1_f32, Q, V, R, work, status, k, stream))
+
+
+def ortho_stage2_f32(Q, V, R, work, status, k=None, stream=None):
+    """Stage 2 on an FP32 basis (FP64 products and sums, FP64 R, FP32 result)."""
+    k = (Q.shape[1] if Q is not None else 0) if k is None else k
+    return check(_ortho(load().ortho_stage2_f32, Q, V, R, work, status, k, stream))
 
 
 def ortho_stage2(Q, V, R, work, status, k=None, stream=None):

@@ -34,6 +34,10 @@ struct PipStatus {
     int32_t* status;     // 0 or 1-based bad pivot
 };
 
+// Mode bits of the BCGS-PIP launchers.
+constexpr int kPipGramOnly = 1;   // Gram kernel: write [P; G] (upper G), no Cholesky, status 0
+constexpr int kPipNoTrsm = 2;     // update kernel: V <- V - Q P only (T taken as the identity)
+
 // ---------------------------------------------------------------- launchers
 // BCGS-PIP step 1+2: [P; G] = [Q, V]^T V split over n rows; the last CTA to
 // finish reduces the partial blocks in a fixed order, forms G - P^T P, factors
@@ -42,13 +46,23 @@ cudaError_t launch_pip_gram_chol(cudaStream_t st, int64_t n,
                                  const double* Q, int64_t ldq, int k,
                                  const double* V, int64_t ldv, int nb,
                                  double* R, int ldr, const PipWork& w, int32_t* d_status,
-                                 int32_t* d_skip, int grid);
+                                 int32_t* d_skip, int grid, int mode = 0);
+cudaError_t launch_pip_gram_chol(cudaStream_t st, int64_t n,
+                                 const float* Q, int64_t ldq, int k,
+                                 const float* V, int64_t ldv, int nb,
+                                 double* R, int ldr, const PipWork& w, int32_t* d_status,
+                                 int32_t* d_skip, int grid, int mode = 0);
 // BCGS-PIP step 3: V <- (V - Q P) T^{-1}, P and T read from R.
 cudaError_t launch_pip_update(cudaStream_t st, int64_t n,
                               const double* Q, int64_t ldq, int k,
                               double* V, int64_t ldv, int nb,
                               const double* R, int ldr, const int32_t* d_status,
-                              const int32_t* d_skip);
+                              const int32_t* d_skip, int mode = 0);
+cudaError_t launch_pip_update(cudaStream_t st, int64_t n,
+                              const float* Q, int64_t ldq, int k,
+                              float* V, int64_t ldv, int nb,
+                              const double* R, int ldr, const int32_t* d_status,
+                              const int32_t* d_skip, int mode = 0);
 
 }  // namespace gm
 

@@ -13,6 +13,10 @@
 // G - P^T P in shared memory (kernel (d)) and writes R = [P; T].
 // Kernel (b) applies V <- (V - Q P) T^{-1} row by row.
 //
+// The basis element type T is double (FP64 path) or float (the mixed-precision
+// path: FP32 basis, every product and sum in FP64, the FP32 inputs widened
+// exactly on load and the updated block rounded to FP32 on store).
+//
 // These kernels run on the FP64 pipe, which on GB300 issues about 2 FMA per
 // SM per clock (1.19 TFLOP/s measured): the Gram and the update are bound by
 // FP64 arithmetic, not by HBM, at the paper's block sizes.
@@ -28,10 +32,13 @@ constexpr int kSkinnyRows = 128;   // rows per chunk, skinny path (nb <= 16)
 constexpr int kWideRows = 32;      // rows per chunk, wide path
 constexpr int kSLd = kMaxNB + 1;   // leading dimension of the factor in shared memory
 
-__device__ __forceinline__ const double* col_ptr(const double* Q, int64_t ldq, int k,
-                                                 const double* V, int64_t ldv, int c) {
+template <typename T>
+__device__ __forceinline__ const T* col_ptr(const T* Q, int64_t ldq, int k, const T* V, int64_t ldv, int c) {
     return c < k ? Q + (int64_t)c * ldq : V + (int64_t)(c - k) * ldv;
 }
+
+__device__ __forceinline__ double ld_d(const double* p) { return __ldg(p); }
+__device__ __forceinline__ double ld_d(const float* p) { return (double)__ldg(p); }
 
 // Entry (c, j) of the (k+nb) x nb block [P; G] is needed unless it lies strictly
 // below the diagonal of the symmetric G block.
@@ -41,7 +48,7 @@ __device__ __forceinline__ bool needed(int c, int j, int k) { return c < k || (c
 // column group g in CTA order; the last group to finish factors the Gram.
 __device__ void pip_epilogue(int64_t n, int k, int nb, int kx, double* R, int ldr,
                              double* partial, unsigned* counter, double* gram,
-                             int32_t* d_status, int32_t* d_skip, double* smem) {
+                             int32_t* d_status, int32_t* d_skip, double* smem, int mode) {
     __shared__ unsigned s_ticket;
     __shared__ int s_info;
     __shared__ double s_inv;
@@ -80,6 +87,16 @@ __device__ void pip_epilogue(int64_t n, int k, int nb, int kx, double* R, int ld
     if (s_ticket != 0u) return;   // another group's last CTA factors the Gram
     __threadfence();
     if (tid == 0 && groups > 1) counter[groups] = 0u;
+
+    if (mode & kPipGramOnly) {
+        // [P; G] as reduced (upper triangle of G), no factorization
+        for (int e = tid; e < (k + nb) * nb; e += blockDim.x) {
+            const int c = e % (k + nb), j = e / (k + nb);
+            R[c + (size_t)j * ldr] = needed(c, j, k) ? __ldcg(gram + c + (size_t)j * kx) : 0.0;
+        }
+        if (tid == 0) *d_status = 0;
+        return;
+    }
 
     // S = G - P^T P (upper triangle), Pythagorean update of the Gram (Fig. 4a)
     double* S = smem;  // nb x nb, column-major, ld kSLd
@@ -140,12 +157,12 @@ __device__ void pip_epilogue(int64_t n, int k, int nb, int kx, double* R, int ld
 
 // Skinny Gram: nb <= 12.  Warp w owns the group columns w, w+8, ...; lane l owns
 // rows l, l+32, ... of each chunk; the V chunk is staged in shared memory.
-template <int NB>
+template <typename T, int NB>
 __global__ void __launch_bounds__(kGramThreads)
-gram_skinny_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
-                   const double* __restrict__ V, int64_t ldv, double* __restrict__ R, int ldr,
+gram_skinny_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, int k,
+                   const T* __restrict__ V, int64_t ldv, double* __restrict__ R, int ldr,
                    double* partial, unsigned* counter, double* gram, int32_t* d_status,
-                   int32_t* d_skip) {
+                   int32_t* d_skip, int mode) {
     extern __shared__ double smem[];
     if (d_skip && *d_skip) return;
     const int kx = k + NB;
@@ -154,7 +171,7 @@ gram_skinny_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int CPW = kMaxNB / 8;
 
-    const double* xp[CPW];
+    const T* xp[CPW];
 #pragma unroll
     for (int i = 0; i < CPW; ++i) {
         const int cl = warp + 8 * i;
@@ -174,7 +191,7 @@ gram_skinny_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
         for (int e = threadIdx.x; e < NB * kSkinnyRows; e += blockDim.x) {
             const int j = e / kSkinnyRows, r = e % kSkinnyRows;
             const int64_t row = row0 + r;
-            Ys[e] = row < n ? __ldg(V + (int64_t)j * ldv + row) : 0.0;
+            Ys[e] = row < n ? ld_d(V + (int64_t)j * ldv + row) : 0.0;
         }
         __syncthreads();
 #pragma unroll 1
@@ -188,7 +205,7 @@ gram_skinny_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
 #pragma unroll
             for (int i = 0; i < CPW; ++i) {
                 if (xp[i] != nullptr) {
-                    const double x = in ? __ldg(xp[i] + row) : 0.0;
+                    const double x = in ? ld_d(xp[i] + row) : 0.0;
 #pragma unroll
                     for (int j = 0; j < NB; ++j) acc[i][j] = fma(x, v[j], acc[i][j]);
                 }
@@ -209,17 +226,18 @@ gram_skinny_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
             if (lane == 0) slot[(warp + 8 * i) * NB + j] = a;
         }
     }
-    pip_epilogue(n, k, NB, kx, R, ldr, partial, counter, gram, d_status, d_skip, smem);
+    pip_epilogue(n, k, NB, kx, R, ldr, partial, counter, gram, d_status, d_skip, smem, mode);
 }
 
 // Wide Gram: nb up to 64.  Each thread owns a 4 x 4 tile of the group's
 // (<= 64) x nb block; tiles strictly below the diagonal of the symmetric G
 // block are skipped and the remaining tiles are packed onto the first threads.
+template <typename T>
 __global__ void __launch_bounds__(kGramThreads)
-gram_wide_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
-                 const double* __restrict__ V, int64_t ldv, int nb, double* __restrict__ R, int ldr,
+gram_wide_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, int k,
+                 const T* __restrict__ V, int64_t ldv, int nb, double* __restrict__ R, int ldr,
                  double* partial, unsigned* counter, double* gram, int32_t* d_status,
-                 int32_t* d_skip) {
+                 int32_t* d_skip, int mode) {
     extern __shared__ double smem[];
     if (d_skip && *d_skip) return;
     const int kx = k + nb;
@@ -258,9 +276,9 @@ gram_wide_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
             const int64_t row = row0 + r;
             double v = 0.0;
             if (row < n) {
-                const double* p = c < ccount ? col_ptr(Q, ldq, k, V, ldv, cg0 + c)
-                                             : V + (int64_t)(c - ccount) * ldv;
-                v = __ldg(p + row);
+                const T* p = c < ccount ? col_ptr(Q, ldq, k, V, ldv, cg0 + c)
+                                        : V + (int64_t)(c - ccount) * ldv;
+                v = ld_d(p + row);
             }
             if (c < ccount) Xs[c * LD + r] = v; else Ys[(c - ccount) * LD + r] = v;
         }
@@ -292,15 +310,15 @@ gram_wide_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
                 if (cl < ccount && j < nb) slot[cl * nb + j] = acc[s][t];
             }
     }
-    pip_epilogue(n, k, nb, kx, R, ldr, partial, counter, gram, d_status, d_skip, smem);
+    pip_epilogue(n, k, nb, kx, R, ldr, partial, counter, gram, d_status, d_skip, smem, mode);
 }
 
 // Update, nb <= 16: one thread per row, P and T staged in shared memory.
-template <int NB>
+template <typename T, int NB>
 __global__ void __launch_bounds__(256)
-update_skinny_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
-                     double* __restrict__ V, int64_t ldv, const double* __restrict__ R, int ldr,
-                     const int32_t* d_status, const int32_t* d_skip) {
+update_skinny_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, int k,
+                     T* __restrict__ V, int64_t ldv, const double* __restrict__ R, int ldr,
+                     const int32_t* d_status, const int32_t* d_skip, int mode) {
     extern __shared__ double smem[];
     if ((d_skip && *d_skip) || *d_status) return;
     double* Ps = smem;                 // [k][NB]
@@ -312,7 +330,7 @@ update_skinny_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k
     }
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
         const int i = e / NB, j = e % NB;
-        Ts[e] = R[(k + i) + (size_t)j * ldr];
+        Ts[e] = (mode & kPipNoTrsm) ? (i == j ? 1.0 : 0.0) : R[(k + i) + (size_t)j * ldr];
     }
     __syncthreads();
     if (threadIdx.x < NB) Dinv[threadIdx.x] = 1.0 / Ts[threadIdx.x * NB + threadIdx.x];
@@ -321,9 +339,9 @@ update_skinny_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k
          row += (int64_t)gridDim.x * blockDim.x) {
         double w[NB];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) w[j] = V[(int64_t)j * ldv + row];
+        for (int j = 0; j < NB; ++j) w[j] = (double)V[(int64_t)j * ldv + row];
         for (int c = 0; c < k; ++c) {
-            const double q = __ldg(Q + (int64_t)c * ldq + row);
+            const double q = ld_d(Q + (int64_t)c * ldq + row);
 #pragma unroll
             for (int j = 0; j < NB; ++j) w[j] = fma(-q, Ps[c * NB + j], w[j]);
         }
@@ -335,22 +353,24 @@ update_skinny_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k
             w[j] = s * Dinv[j];
         }
 #pragma unroll
-        for (int j = 0; j < NB; ++j) V[(int64_t)j * ldv + row] = w[j];
+        for (int j = 0; j < NB; ++j) V[(int64_t)j * ldv + row] = (T)w[j];
     }
 }
 
 // Update, 16 < nb <= 64: one thread per row, the row of V in registers, T in
 // shared memory, P read through the read-only cache (uniform across a warp).
+template <typename T>
 __global__ void __launch_bounds__(128)
-update_wide_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
-                   double* __restrict__ V, int64_t ldv, int nb, const double* __restrict__ R, int ldr,
-                   const int32_t* d_status, const int32_t* d_skip) {
+update_wide_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, int k,
+                   T* __restrict__ V, int64_t ldv, int nb, const double* __restrict__ R, int ldr,
+                   const int32_t* d_status, const int32_t* d_skip, int mode) {
     __shared__ double Ts[kMaxNB * kMaxNB];
     __shared__ double Dinv[kMaxNB];
     if ((d_skip && *d_skip) || *d_status) return;
     for (int e = threadIdx.x; e < kMaxNB * kMaxNB; e += blockDim.x) {
         const int i = e / kMaxNB, j = e % kMaxNB;
-        Ts[e] = (i < nb && j < nb) ? R[(k + i) + (size_t)j * ldr] : 0.0;
+        Ts[e] = (i < nb && j < nb) ? ((mode & kPipNoTrsm) ? (i == j ? 1.0 : 0.0) : R[(k + i) + (size_t)j * ldr])
+                                   : 0.0;
     }
     __syncthreads();
     if (threadIdx.x < kMaxNB) Dinv[threadIdx.x] = threadIdx.x < nb ? 1.0 / Ts[threadIdx.x * (kMaxNB + 1)] : 0.0;
@@ -359,9 +379,9 @@ update_wide_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
          row += (int64_t)gridDim.x * blockDim.x) {
         double w[kMaxNB];
 #pragma unroll
-        for (int j = 0; j < kMaxNB; ++j) w[j] = j < nb ? V[(int64_t)j * ldv + row] : 0.0;
+        for (int j = 0; j < kMaxNB; ++j) w[j] = j < nb ? (double)V[(int64_t)j * ldv + row] : 0.0;
         for (int c = 0; c < k; ++c) {
-            const double q = __ldg(Q + (int64_t)c * ldq + row);
+            const double q = ld_d(Q + (int64_t)c * ldq + row);
             const double* pr = R + c;
 #pragma unroll
             for (int j = 0; j < kMaxNB; ++j)
@@ -378,30 +398,30 @@ update_wide_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
         }
 #pragma unroll
         for (int j = 0; j < kMaxNB; ++j)
-            if (j < nb) V[(int64_t)j * ldv + row] = w[j];
+            if (j < nb) V[(int64_t)j * ldv + row] = (T)w[j];
     }
 }
 
-template <int NB>
-cudaError_t launch_skinny(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k,
-                          const double* V, int64_t ldv, double* R, int ldr, const PipWork& w,
-                          int32_t* d_status, int32_t* d_skip, int grid) {
+template <typename T, int NB>
+cudaError_t launch_skinny(cudaStream_t st, int64_t n, const T* Q, int64_t ldq, int k,
+                          const T* V, int64_t ldv, double* R, int ldr, const PipWork& w,
+                          int32_t* d_status, int32_t* d_skip, int grid, int mode) {
     const int kx = k + NB;
     const dim3 g(grid, (kx + kMaxNB - 1) / kMaxNB);
     const size_t sm = (size_t)kMaxNB * kSLd * sizeof(double);  // >= NB * kSkinnyRows doubles
-    gram_skinny_kernel<NB><<<g, kGramThreads, sm, st>>>(n, Q, ldq, k, V, ldv, R, ldr, w.partial,
-                                                        w.counter, w.gram, d_status, d_skip);
+    gram_skinny_kernel<T, NB><<<g, kGramThreads, sm, st>>>(n, Q, ldq, k, V, ldv, R, ldr, w.partial,
+                                                        w.counter, w.gram, d_status, d_skip, mode);
     return cudaGetLastError();
 }
 
-template <int NB>
-cudaError_t launch_update_skinny(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k,
-                                 double* V, int64_t ldv, const double* R, int ldr,
-                                 const int32_t* d_status, const int32_t* d_skip) {
+template <typename T, int NB>
+cudaError_t launch_update_skinny(cudaStream_t st, int64_t n, const T* Q, int64_t ldq, int k,
+                                 T* V, int64_t ldv, const double* R, int ldr,
+                                 const int32_t* d_status, const int32_t* d_skip, int mode) {
     const size_t sm = ((size_t)k * NB + NB * NB + NB) * sizeof(double);
     const int64_t blocks = (n + 255) / 256;
     const int grid = (int)(blocks < 8 * (int64_t)num_sms() ? blocks : 8 * (int64_t)num_sms());
-    update_skinny_kernel<NB><<<grid, 256, sm, st>>>(n, Q, ldq, k, V, ldv, R, ldr, d_status, d_skip);
+    update_skinny_kernel<T, NB><<<grid, 256, sm, st>>>(n, Q, ldq, k, V, ldv, R, ldr, d_status, d_skip, mode);
     return cudaGetLastError();
 }
 
@@ -411,11 +431,12 @@ static_assert(kMaxNB * kSLd >= 12 * kSkinnyRows, "skinny staging fits the epilog
 constexpr size_t kWideSmem = (2 * kMaxNB * (kWideRows + 1) > kMaxNB * kSLd ? 2 * kMaxNB * (kWideRows + 1)
                                                                             : kMaxNB * kSLd) * sizeof(double);
 
-cudaError_t launch_pip_gram_chol(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k,
-                                 const double* V, int64_t ldv, int nb, double* R, int ldr,
-                                 const PipWork& w, int32_t* d_status, int32_t* d_skip, int grid) {
+template <typename T>
+cudaError_t pip_gram_chol_t(cudaStream_t st, int64_t n, const T* Q, int64_t ldq, int k,
+                            const T* V, int64_t ldv, int nb, double* R, int ldr,
+                            const PipWork& w, int32_t* d_status, int32_t* d_skip, int grid, int mode) {
     switch (nb) {
-#define GM_CASE(NBV) case NBV: return launch_skinny<NBV>(st, n, Q, ldq, k, V, ldv, R, ldr, w, d_status, d_skip, grid);
+#define GM_CASE(NBV) case NBV: return launch_skinny<T, NBV>(st, n, Q, ldq, k, V, ldv, R, ldr, w, d_status, d_skip, grid, mode);
         GM_CASE(1) GM_CASE(2) GM_CASE(3) GM_CASE(4) GM_CASE(5) GM_CASE(6) GM_CASE(7) GM_CASE(8)
         GM_CASE(9) GM_CASE(10) GM_CASE(11) GM_CASE(12)
 #undef GM_CASE
@@ -424,16 +445,17 @@ cudaError_t launch_pip_gram_chol(cudaStream_t st, int64_t n, const double* Q, in
     const int kx = k + nb;
     const dim3 g(grid, (kx + kMaxNB - 1) / kMaxNB);
     const size_t sm = kWideSmem;
-    gram_wide_kernel<<<g, kGramThreads, sm, st>>>(n, Q, ldq, k, V, ldv, nb, R, ldr, w.partial,
-                                                  w.counter, w.gram, d_status, d_skip);
+    gram_wide_kernel<T><<<g, kGramThreads, sm, st>>>(n, Q, ldq, k, V, ldv, nb, R, ldr, w.partial,
+                                                  w.counter, w.gram, d_status, d_skip, mode);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pip_update(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k,
-                              double* V, int64_t ldv, int nb, const double* R, int ldr,
-                              const int32_t* d_status, const int32_t* d_skip) {
+template <typename T>
+cudaError_t pip_update_t(cudaStream_t st, int64_t n, const T* Q, int64_t ldq, int k,
+                         T* V, int64_t ldv, int nb, const double* R, int ldr,
+                         const int32_t* d_status, const int32_t* d_skip, int mode) {
     switch (nb) {
-#define GM_CASE(NBV) case NBV: return launch_update_skinny<NBV>(st, n, Q, ldq, k, V, ldv, R, ldr, d_status, d_skip);
+#define GM_CASE(NBV) case NBV: return launch_update_skinny<T, NBV>(st, n, Q, ldq, k, V, ldv, R, ldr, d_status, d_skip, mode);
         GM_CASE(1) GM_CASE(2) GM_CASE(3) GM_CASE(4) GM_CASE(5) GM_CASE(6) GM_CASE(7) GM_CASE(8)
         GM_CASE(9) GM_CASE(10) GM_CASE(11) GM_CASE(12) GM_CASE(13) GM_CASE(14) GM_CASE(15) GM_CASE(16)
 #undef GM_CASE
@@ -441,8 +463,29 @@ cudaError_t launch_pip_update(cudaStream_t st, int64_t n, const double* Q, int64
     }
     const int64_t blocks = (n + 127) / 128;
     const int grid = (int)(blocks < 16 * (int64_t)num_sms() ? blocks : 16 * (int64_t)num_sms());
-    update_wide_kernel<<<grid, 128, 0, st>>>(n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, d_skip);
+    update_wide_kernel<T><<<grid, 128, 0, st>>>(n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, d_skip, mode);
     return cudaGetLastError();
+}
+
+cudaError_t launch_pip_gram_chol(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k,
+                                 const double* V, int64_t ldv, int nb, double* R, int ldr,
+                                 const PipWork& w, int32_t* d_status, int32_t* d_skip, int grid, int mode) {
+    return pip_gram_chol_t<double>(st, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode);
+}
+cudaError_t launch_pip_gram_chol(cudaStream_t st, int64_t n, const float* Q, int64_t ldq, int k,
+                                 const float* V, int64_t ldv, int nb, double* R, int ldr,
+                                 const PipWork& w, int32_t* d_status, int32_t* d_skip, int grid, int mode) {
+    return pip_gram_chol_t<float>(st, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode);
+}
+cudaError_t launch_pip_update(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k,
+                              double* V, int64_t ldv, int nb, const double* R, int ldr,
+                              const int32_t* d_status, const int32_t* d_skip, int mode) {
+    return pip_update_t<double>(st, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, d_skip, mode);
+}
+cudaError_t launch_pip_update(cudaStream_t st, int64_t n, const float* Q, int64_t ldq, int k,
+                              float* V, int64_t ldv, int nb, const double* R, int ldr,
+                              const int32_t* d_status, const int32_t* d_skip, int mode) {
+    return pip_update_t<float>(st, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, d_skip, mode);
 }
 
 PipWork pip_work_layout(void* base, int64_t n, int k, int nb) {

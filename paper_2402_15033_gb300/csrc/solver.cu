@@ -14,6 +14,12 @@
 // A device flag ("done") makes every later kernel of the cycle return at once
 // after convergence at a big-panel end or after a Cholesky breakdown, so a
 // cycle is a fixed launch sequence without host round trips.
+//
+// Mixed precision (GMRES_PREC_MIXED): the basis and the MPK are FP32 (an FP32
+// copy of A's values), the Gram products and sums, the Cholesky factors, the
+// Hessenberg/Givens work and x stay FP64.  Every restart cycle starts from the
+// FP64 residual r = b - A x and ends with x += d, d = Q y: one step of FP64
+// iterative refinement whose correction is solved with the FP32 basis.
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -65,7 +71,8 @@ struct gmres_ctx {
     DevCSR A;
     int64_t n = 0, ldq = 0;
     double sigma = 1.0;
-    double* basis = nullptr;     // (m+1) columns, ld = ldq
+    void* basis = nullptr;       // (m+1) columns, ld = ldq, FP64 or FP32 (opts.precision)
+    double* r = nullptr;         // FP64 residual (mixed precision only)
     double* b = nullptr;
     double* x = nullptr;
     double* red_partial = nullptr;
@@ -110,7 +117,7 @@ static int check_opts(const gmres_opts* o) {
     GM_ARG(o->tol > 0.0, "tol must be positive");
     GM_ARG(o->max_restarts >= 1, "max_restarts must be >= 1");
     GM_ARG(o->ortho == GMRES_ORTHO_TWO_STAGE || o->ortho == GMRES_ORTHO_BCGS_PIP2, "unknown ortho");
-    GM_ARG(o->precision == GMRES_PREC_FP64, "precision: only FP64 is built");
+    GM_ARG(o->precision == GMRES_PREC_FP64 || o->precision == GMRES_PREC_MIXED, "unknown precision");
     GM_ARG(o->basis == GMRES_BASIS_MONOMIAL || o->basis == GMRES_BASIS_NEWTON, "unknown basis");
     const int panel = o->ortho == GMRES_ORTHO_BCGS_PIP2 ? o->s : o->panel;
     GM_ARG(panel >= o->s && panel % o->s == 0 && o->m % panel == 0, "need s | panel | m");
@@ -126,6 +133,8 @@ int gmres_destroy(gmres_ctx* c) {
     cudaFree(c->A.rowptr);
     cudaFree(c->A.colind);
     cudaFree(c->A.vals);
+    cudaFree(c->A.vals32);
+    cudaFree(c->r);
     cudaFree(c->basis);
     cudaFree(c->b);
     cudaFree(c->x);
@@ -239,8 +248,14 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
         if (o.sigma > 0.0) c->sigma = o.sigma;
         else c->sigma = (rmax > 0.0 && std::isfinite(rmax)) ? std::ldexp(1.0, (int)std::floor(std::log2(rmax))) : 1.0;
     }
-    CK(cuda_rc(cudaMalloc(&c->basis, (size_t)mp1 * c->ldq * sizeof(double)), "cudaMalloc basis"));
-    CK(cuda_rc(cudaMemsetAsync(c->basis, 0, (size_t)mp1 * c->ldq * sizeof(double), s), "memset basis"));
+    const size_t esz = o.precision == GMRES_PREC_MIXED ? sizeof(float) : sizeof(double);
+    CK(cuda_rc(cudaMalloc(&c->basis, (size_t)mp1 * c->ldq * esz), "cudaMalloc basis"));
+    CK(cuda_rc(cudaMemsetAsync(c->basis, 0, (size_t)mp1 * c->ldq * esz, s), "memset basis"));
+    if (o.precision == GMRES_PREC_MIXED) {
+        CK(cuda_rc(cudaMalloc(&c->A.vals32, (nnz > 0 ? nnz : 1) * sizeof(float)), "cudaMalloc vals32"));
+        if (nnz > 0) CK(cuda_rc(launch_narrow_vals(s, nnz, c->A.vals, c->A.vals32), "narrow vals"));
+        CK(cuda_rc(cudaMalloc(&c->r, c->ldq * sizeof(double)), "cudaMalloc r"));
+    }
     CK(cuda_rc(cudaMalloc(&c->b, c->ldq * sizeof(double)), "cudaMalloc b"));
     CK(cuda_rc(cudaMalloc(&c->x, c->ldq * sizeof(double)), "cudaMalloc x"));
     const int ng = norm_grid(n);
@@ -282,13 +297,17 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
 // phases for opts.timing
 enum { PH_MPK = 0, PH_S1 = 1, PH_S2 = 2, PH_LS = 3 };
 
+}  // extern "C"
+
+template <typename T>
 static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
     const gmres_opts& o = c->opts;
     cudaStream_t s = c->stream;
     DevState* ds = c->st;
     int32_t* done = &ds->done;
+    T* basis = static_cast<T*>(c->basis);
     const double sinv = 1.0 / c->sigma;
-    PipWork w = pip_work_layout(c->pip_work, c->n, 0, 1);  // re-laid out per call below
+    PipWork w{};
     int evi = 0;
     auto mark = [&](int phase) -> cudaError_t {
         if (!marks) return cudaSuccess;
@@ -298,13 +317,13 @@ static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
     const int nblk = o.m / o.s;
     int panel_idx = 0;
     cudaError_t e = launch_cycle_begin(s, ds);
-    if (e == cudaSuccess) e = launch_scale(s, c->n, c->basis, ds);
+    if (e == cudaSuccess) e = launch_scale(s, c->n, c->r ? c->r : static_cast<double*>(c->basis), basis, ds);
     for (int j = 0; j < nblk && e == cudaSuccess; ++j) {
         const int st0 = j * o.s;
         e = mark(PH_MPK);
         for (int i = 0; i < o.s && e == cudaSuccess; ++i) {
             const double th = c->hst->theta[i];
-            e = launch_spmv(s, c->A, c->basis + (size_t)(st0 + i) * c->ldq, c->basis + (size_t)(st0 + i + 1) * c->ldq,
+            e = launch_spmv(s, c->A, basis + (size_t)(st0 + i) * c->ldq, basis + (size_t)(st0 + i + 1) * c->ldq,
                             th, sinv, done);
         }
         if (e == cudaSuccess) e = mark(PH_MPK);
@@ -312,12 +331,32 @@ static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
         if (e == cudaSuccess) {
             const int k = st0 + 1;
             w = pip_work_layout(c->pip_work, c->n, k, o.s);
-            double* V = c->basis + (size_t)k * c->ldq;
+            T* V = basis + (size_t)k * c->ldq;
             double* R = ds->Rhat + (size_t)k * kMaxCols;
-            e = launch_pip_gram_chol(s, c->n, c->basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, w,
-                                     &ds->blkstat[j], done, reduction_grid(c->n));
-            if (e == cudaSuccess)
-                e = launch_pip_update(s, c->n, c->basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, &ds->blkstat[j], done);
+            int32_t* stat = &ds->blkstat[j];
+            if (sizeof(T) == sizeof(double)) {
+                // BCGS-PIP (Fig. 4a): one reduction, Pythagorean Gram
+                e = launch_pip_gram_chol(s, c->n, basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, w, stat, done,
+                                         reduction_grid(c->n));
+                if (e == cudaSuccess)
+                    e = launch_pip_update(s, c->n, basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, stat, done);
+            } else {
+                // FP32 basis: project, then CholQR of the projected block with an
+                // explicit FP64 Gram (the Pythagorean identity needs an
+                // orthonormal stored basis, which FP32 storage is only to ~1e-7)
+                e = launch_pip_gram_chol(s, c->n, basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, w, stat, done,
+                                         reduction_grid(c->n), kPipGramOnly);
+                if (e == cudaSuccess)
+                    e = launch_pip_update(s, c->n, basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, stat, done,
+                                          kPipNoTrsm);
+                if (e == cudaSuccess) {
+                    PipWork w0 = pip_work_layout(c->pip_work, c->n, 0, o.s);
+                    e = launch_pip_gram_chol(s, c->n, basis, c->ldq, 0, V, c->ldq, o.s, R + k, kMaxCols, w0, stat,
+                                             done, reduction_grid(c->n));
+                }
+                if (e == cudaSuccess)
+                    e = launch_pip_update(s, c->n, basis, c->ldq, 0, V, c->ldq, o.s, R + k, kMaxCols, stat, done);
+            }
         }
         if (e == cudaSuccess) e = mark(PH_S1);
         const int t = st0 + o.s;
@@ -326,14 +365,14 @@ static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
             const int np = t - lo + 1;
             e = mark(PH_S2);
             w = pip_work_layout(c->pip_work, c->n, lo, np);
-            double* V = c->basis + (size_t)lo * c->ldq;
+            T* V = basis + (size_t)lo * c->ldq;
             double* R = ds->Cm + (size_t)lo * kMaxCols;
             int32_t* stat = &ds->blkstat[nblk + panel_idx];
             if (e == cudaSuccess)
-                e = launch_pip_gram_chol(s, c->n, c->basis, c->ldq, lo, V, c->ldq, np, R, kMaxCols, w, stat, done,
+                e = launch_pip_gram_chol(s, c->n, basis, c->ldq, lo, V, c->ldq, np, R, kMaxCols, w, stat, done,
                                          reduction_grid(c->n));
             if (e == cudaSuccess)
-                e = launch_pip_update(s, c->n, c->basis, c->ldq, lo, V, c->ldq, np, R, kMaxCols, stat, done);
+                e = launch_pip_update(s, c->n, basis, c->ldq, lo, V, c->ldq, np, R, kMaxCols, stat, done);
             if (e == cudaSuccess) e = mark(PH_S2);
             if (e == cudaSuccess) e = mark(PH_LS);
             if (e == cudaSuccess) e = launch_hessenberg_ls(s, ds, lo, t);
@@ -341,9 +380,11 @@ static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
             ++panel_idx;
         }
     }
-    if (e == cudaSuccess) e = launch_xupdate(s, c->n, c->basis, c->ldq, c->x, ds);
+    if (e == cudaSuccess) e = launch_xupdate(s, c->n, basis, c->ldq, c->x, ds);
     return cuda_rc(e, "cycle launch");
 }
+
+extern "C" {
 
 int gmres_solve(gmres_ctx* c, const double* b, double* x, int32_t ptr_on_device, gmres_result* res) {
     clear_error();
@@ -398,7 +439,8 @@ int gmres_solve(gmres_ctx* c, const double* b, double* x, int32_t ptr_on_device,
     std::vector<std::pair<int, int>> marks;
     const int nstat = o.m / o.s + o.m / o.panel;
     for (int cyc = 0;; ++cyc) {
-        rc = cuda_rc(launch_residual(s, c->A, c->b, c->x, c->basis, c->red_partial, c->red_counter, c->st, 0),
+        double* rout = c->r ? c->r : static_cast<double*>(c->basis);
+        rc = cuda_rc(launch_residual(s, c->A, c->b, c->x, rout, c->red_partial, c->red_counter, c->st, 0),
                      "residual");
         if (!rc) rc = cuda_rc(cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s), "state read");
         if (!rc) rc = cuda_rc(cudaStreamSynchronize(s), "sync");
@@ -438,7 +480,9 @@ int gmres_solve(gmres_ctx* c, const double* b, double* x, int32_t ptr_on_device,
         if (h.beta <= o.tol * bnorm) { status = GMRES_OK; break; }
         if (cyc >= o.max_restarts) { status = GMRES_WARN_MAXIT; break; }
         marks.clear();
-        rc = run_cycle(c, o.timing ? &marks : nullptr);
+        rc = o.precision == GMRES_PREC_MIXED ? run_cycle<float>(c, o.timing ? &marks : nullptr)
+                                             : run_cycle<double>(c, o.timing ? &marks : nullptr);
+        if (o.precision == GMRES_PREC_MIXED) ++r.ir_steps;
         if (rc) return finish(rc);
     }
     rc = cuda_rc(cudaMemcpyAsync(x, c->x, vb, kout, s), "copy x");
@@ -457,7 +501,7 @@ int gmres_solve(gmres_ctx* c, const double* b, double* x, int32_t ptr_on_device,
     return finish(status);
 }
 
-static int check_pip_args(int64_t n, const double* Q, int64_t ldq, int32_t k, const double* V, int64_t ldv,
+static int check_pip_args(int64_t n, const void* Q, int64_t ldq, int32_t k, const void* V, int64_t ldv,
                           int32_t nb, const double* R, int32_t ldr, void* d_work, size_t work_bytes,
                           const int32_t* d_status, int* code) {
     *code = GMRES_ERR_ARG;
@@ -480,7 +524,10 @@ static int check_pip_args(int64_t n, const double* Q, int64_t ldq, int32_t k, co
     return GMRES_OK;
 }
 
-static int ortho_pip(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,
+}  // extern "C"
+
+template <typename T>
+static int ortho_pip(void* stream, int64_t n, const T* Q, int64_t ldq, int32_t k, T* V, int64_t ldv,
                      int32_t nb, double* R, int32_t ldr, void* d_work, size_t work_bytes, int32_t* d_status) {
     clear_error();
     int code = GMRES_OK;
@@ -494,6 +541,8 @@ static int ortho_pip(void* stream, int64_t n, const double* Q, int64_t ldq, int3
     if (e == cudaSuccess) e = launch_pip_update(s, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, nullptr);
     return cuda_rc(e, "ortho launch");
 }
+
+extern "C" {
 
 int ortho_gram_chol(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, const double* V,
                     int64_t ldv, int32_t nb, double* R, int32_t ldr, void* d_work, size_t work_bytes,
@@ -537,11 +586,22 @@ int ortho_stage2(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t 
     return ortho_pip(stream, n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status);
 }
 
+int ortho_stage1_f32(void* stream, int64_t n, const float* Q, int64_t ldq, int32_t k, float* V, int64_t ldv,
+                     int32_t nb, double* R, int32_t ldr, void* d_work, size_t work_bytes, int32_t* d_status) {
+    return ortho_pip(stream, n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status);
+}
+
+int ortho_stage2_f32(void* stream, int64_t n, const float* Q, int64_t ldq, int32_t k, float* V, int64_t ldv,
+                     int32_t nb, double* R, int32_t ldr, void* d_work, size_t work_bytes, int32_t* d_status) {
+    return ortho_pip(stream, n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status);
+}
+
 int gmres_mpk(gmres_ctx* c, const double* v, double* W, int64_t ldw, int32_t s, double sigma, const double* theta) {
     clear_error();
     GM_ARG(c != nullptr && v != nullptr && W != nullptr, "NULL argument");
     GM_ARG(s >= 1 && s <= 16 && ldw >= c->n, "need 1 <= s <= 16 and ldw >= n");
     GM_ARG(sigma != 0.0 && std::isfinite(sigma), "sigma must be finite and nonzero");
+    GM_ARG(c->opts.precision == GMRES_PREC_FP64, "gmres_mpk works on FP64 vectors: create the context with FP64");
     cudaError_t e = cudaSetDevice(c->device);
     const double sinv = 1.0 / sigma;
     const double* prev = v;

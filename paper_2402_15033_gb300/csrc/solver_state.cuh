@@ -12,6 +12,7 @@ struct DevCSR {
     int32_t* rowptr = nullptr;
     int32_t* colind = nullptr;
     double* vals = nullptr;
+    float* vals32 = nullptr;   // FP32 copy for the mixed-precision MPK (else null)
 };
 
 // One restart cycle's scalars and small matrices (all FP64, column-major,
@@ -45,10 +46,15 @@ struct DevState {
 int norm_grid(int64_t n);
 cudaError_t launch_spmv(cudaStream_t st, const DevCSR& A, const double* x, double* y, double theta,
                         double sinv, const int32_t* d_skip);
+cudaError_t launch_spmv(cudaStream_t st, const DevCSR& A, const float* x, float* y, double theta,
+                        double sinv, const int32_t* d_skip);
 cudaError_t launch_residual(cudaStream_t st, const DevCSR& A, const double* b, const double* x, double* out,
                             double* partial, unsigned* counter, DevState* ds, int which);
-cudaError_t launch_scale(cudaStream_t st, int64_t n, double* v, const DevState* ds);
+cudaError_t launch_scale(cudaStream_t st, int64_t n, const double* v, double* out, const DevState* ds);
+cudaError_t launch_scale(cudaStream_t st, int64_t n, const double* v, float* out, const DevState* ds);
 cudaError_t launch_xupdate(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, double* x, DevState* ds);
+cudaError_t launch_xupdate(cudaStream_t st, int64_t n, const float* Q, int64_t ldq, double* x, DevState* ds);
+cudaError_t launch_narrow_vals(cudaStream_t st, int64_t m, const double* in, float* out);
 cudaError_t launch_validate_csr(cudaStream_t st, int64_t n, int64_t nnz, const int32_t* rowptr,
                                 const int32_t* colind, int32_t* bad);
 cudaError_t launch_rowabs(cudaStream_t st, const DevCSR& A, unsigned long long* out);

@@ -28,17 +28,20 @@ __device__ double block_sum(double v) {
     return t;  // valid in thread 0
 }
 
+// y = (A x - theta x) * sinv in the basis precision T (FP64, or FP32 for the
+// mixed-precision MPK with an FP32 copy of the values).
+template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
 spmv_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-            const double* __restrict__ vals, const double* __restrict__ x, double* __restrict__ y,
-            double theta, double sinv, const int32_t* d_skip) {
+            const T* __restrict__ vals, const T* __restrict__ x, T* __restrict__ y,
+            T theta, T sinv, const int32_t* d_skip) {
     if (d_skip && *d_skip) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t p0 = __ldg(rowptr + i), p1 = __ldg(rowptr + i + 1);
-        double acc = 0.0;
+        T acc = T(0);
         for (int32_t p = p0; p < p1; ++p) acc = fma(__ldg(vals + p), __ldg(x + __ldg(colind + p)), acc);
-        if (theta != 0.0) acc = fma(-theta, x[i], acc);
+        if (theta != T(0)) acc = fma(-theta, x[i], acc);
         y[i] = acc * sinv;
     }
 }
@@ -87,17 +90,21 @@ residual_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __
     }
 }
 
+// out = (T)(v * (1/||r||)): the start vector q_1 of a cycle in the basis precision.
+template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
-scale_kernel(int64_t n, double* v, const DevState* st) {
+scale_kernel(int64_t n, const double* v, T* out, const DevState* st) {
     const double s = st->inv_beta;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        v[i] *= s;
+        out[i] = (T)(v[i] * s);
 }
 
-// x += Q[:, 0:k] y with k = st->k_used, y = st->y; also counts iterations.
+// x += Q[:, 0:k] y with k = st->k_used, y = st->y (FP64 accumulation); also
+// counts iterations.
+template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
-xupdate_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, double* __restrict__ x, DevState* st) {
+xupdate_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, double* __restrict__ x, DevState* st) {
     __shared__ double ys[kMaxCols];
     const int k = st->k_used;
     for (int c = threadIdx.x; c < k; c += blockDim.x) ys[c] = st->y[c];
@@ -106,10 +113,16 @@ xupdate_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, double* __r
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         double acc = x[i];
-        for (int c = 0; c < k; ++c) acc = fma(__ldg(Q + (int64_t)c * ldq + i), ys[c], acc);
+        for (int c = 0; c < k; ++c) acc = fma((double)__ldg(Q + (int64_t)c * ldq + i), ys[c], acc);
         x[i] = acc;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) st->iters += k;
+}
+
+__global__ void narrow_vals_kernel(int64_t m, const double* in, float* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
 }
 
 // CSR sanity check: rowptr[0] = 0, nondecreasing, rowptr[n] = nnz, columns in [0, n).
@@ -162,7 +175,15 @@ int norm_grid(int64_t n) { return vec_grid(n); }
 
 cudaError_t launch_spmv(cudaStream_t st, const DevCSR& A, const double* x, double* y, double theta,
                         double sinv, const int32_t* d_skip) {
-    spmv_kernel<<<vec_grid(A.n), kVecThreads, 0, st>>>(A.n, A.rowptr, A.colind, A.vals, x, y, theta, sinv, d_skip);
+    spmv_kernel<double><<<vec_grid(A.n), kVecThreads, 0, st>>>(A.n, A.rowptr, A.colind, A.vals, x, y, theta, sinv,
+                                                               d_skip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv(cudaStream_t st, const DevCSR& A, const float* x, float* y, double theta,
+                        double sinv, const int32_t* d_skip) {
+    spmv_kernel<float><<<vec_grid(A.n), kVecThreads, 0, st>>>(A.n, A.rowptr, A.colind, A.vals32, x, y, (float)theta,
+                                                              (float)sinv, d_skip);
     return cudaGetLastError();
 }
 
@@ -173,13 +194,28 @@ cudaError_t launch_residual(cudaStream_t st, const DevCSR& A, const double* b, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_scale(cudaStream_t st, int64_t n, double* v, const DevState* ds) {
-    scale_kernel<<<vec_grid(n), kVecThreads, 0, st>>>(n, v, ds);
+cudaError_t launch_scale(cudaStream_t st, int64_t n, const double* v, double* out, const DevState* ds) {
+    scale_kernel<double><<<vec_grid(n), kVecThreads, 0, st>>>(n, v, out, ds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(cudaStream_t st, int64_t n, const double* v, float* out, const DevState* ds) {
+    scale_kernel<float><<<vec_grid(n), kVecThreads, 0, st>>>(n, v, out, ds);
     return cudaGetLastError();
 }
 
 cudaError_t launch_xupdate(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, double* x, DevState* ds) {
-    xupdate_kernel<<<vec_grid(n), kVecThreads, 0, st>>>(n, Q, ldq, x, ds);
+    xupdate_kernel<double><<<vec_grid(n), kVecThreads, 0, st>>>(n, Q, ldq, x, ds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xupdate(cudaStream_t st, int64_t n, const float* Q, int64_t ldq, double* x, DevState* ds) {
+    xupdate_kernel<float><<<vec_grid(n), kVecThreads, 0, st>>>(n, Q, ldq, x, ds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_narrow_vals(cudaStream_t st, int64_t m, const double* in, float* out) {
+    narrow_vals_kernel<<<vec_grid(m), kVecThreads, 0, st>>>(m, in, out);
     return cudaGetLastError();
 }
 

@@ -321,3 +321,45 @@ def test_monomial_scale_is_a_power_of_two():
     assert kr.mpk_sigma(synth.laplace3d(5)) == 8.0
     s = kr.mpk_sigma(synth.convdiff2d(10, 1))
     assert s == 2.0 ** math.floor(math.log2(s))
+
+
+# ---------------------------------------------------------------- mixed-precision pattern
+def test_fp32_mpk_is_the_fp64_mpk_to_fp32_precision():
+    A = synth.laplace2d(40)
+    M = kr.as_operator(A)
+    v = synth.x_true(A.n, 3)
+    W64 = kr.mpk(M, v, 5, 8.0)
+    W32 = kr.mpk(M.astype(np.float32), v.astype(np.float32), 5, 8.0)
+    assert W32.dtype == np.float32
+    rel = np.linalg.norm(W32 - W64, axis=0) / np.linalg.norm(W64, axis=0)
+    assert np.all(rel < 5e-6)
+
+
+@pytest.mark.parametrize("N", [32, 64])
+def test_mixed_precision_refinement_reaches_fp64_accuracy(N):
+    """FP32 basis with FP64 Gram/Cholesky/Hessenberg and FP64 restart
+    residuals (iterative refinement) still reaches ||b - A x|| / ||b|| <= 1e-8,
+    and its x agrees with the FP64 solve to the forward-error bound
+    kappa(A) * tol (closed-form Laplace eigenvalues)."""
+    A = synth.laplace2d(N)
+    M = kr.as_operator(A)
+    b = M @ synth.x_true(A.n, 0)
+    x32, i32 = kr.sstep_gmres(A, b, m=60, s=5, tol=1e-8, basis_dtype=np.float32)
+    x64, i64 = kr.sstep_gmres(A, b, m=60, s=5, tol=1e-8)
+    assert i32["status"] == 0 and i64["status"] == 0
+    assert np.linalg.norm(b - M @ x32) / np.linalg.norm(b) <= 1e-8
+    lo, hi = checks.laplace2d_extreme_eigs(N)
+    assert np.linalg.norm(x32 - x64) / np.linalg.norm(x64) <= 2 * (hi / lo) * 1e-8
+    assert i32["iters"] % 60 == 0
+
+
+def test_mixed_basis_keeps_fp32_orthogonality_after_stage2():
+    """Stage 2 on an FP32-stored pre-processed panel: the FP64-computed Q has
+    O(eps64) orthogonality before rounding and O(eps32) after (Theorem 3 with
+    the basis precision)."""
+    n, s, nb = 20000, 5, 4
+    V = synth.glued(n, s, nb, 1e3, seed=4).astype(np.float32)
+    blocks = [V[:, i * s:(i + 1) * s].astype(np.float64) for i in range(nb)]
+    Q, _, _, _ = bo.two_stage_panel(np.zeros((n, 0)), blocks)
+    assert checks.orth_error(Q)[0] < 100 * EPS
+    assert checks.orth_error(Q.astype(np.float32).astype(np.float64))[0] < 50 * np.finfo(np.float32).eps
