@@ -195,6 +195,36 @@ int ortho_update(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t 
                  double* V, int64_t ldv, int32_t nb, const double* R, int32_t ldr,
                  const int32_t* d_status);
 
+/* ------------------------------------------------ batched solver (many uneven systems)
+ * nsys independent systems of different sizes and matrices share one set of
+ * options (m, s, panel, tol, precision) and advance together: one restart
+ * cycle of every active system is one CUDA-graph launch of persistent kernels
+ * over all systems' work (rows are concatenated, A is block diagonal).  A
+ * system's reductions use the same split and order whatever the batch holds,
+ * so its result does not depend on the other systems.  CSR arrays (rowptr
+ * int64, colind int32, vals FP64) and b, x are per-system HOST arrays; x holds
+ * x0 on entry.  res (may be NULL) receives nsys results.  A NULL stream makes
+ * the batch create its own non-blocking stream (graph capture cannot use the
+ * legacy default stream).  gmres_batch_solve returns GMRES_OK when every
+ * system converged, else the most severe per-system status. */
+typedef struct gmres_batch gmres_batch;
+
+/* Device bytes a batch of these sizes would allocate (for admission control). */
+size_t gmres_batch_footprint(int32_t nsys, const int64_t* n, const int64_t* nnz, const gmres_opts* opts);
+
+int gmres_batch_create(gmres_batch** out, int32_t nsys, const int64_t* n, const int64_t* const* rowptr,
+                       const int32_t* const* colind, const double* const* vals, const gmres_opts* opts,
+                       void* stream);
+
+int gmres_batch_solve(gmres_batch* b, const double* const* rhs, double* const* x, gmres_result* res);
+
+/* Time candidate persistent-grid sizes of the batched Gram and row kernels on
+ * this batch's shapes and keep the fastest (res_ms[4] = best Gram ms, best
+ * update ms, Gram grid, row grid; may be NULL).  Changes speed, never results. */
+int gmres_batch_autotune(gmres_batch* b, double* res_ms);
+
+int gmres_batch_destroy(gmres_batch* b);   /* NULL-safe */
+
 /* ------------------------------------------------ matrix powers kernel
  * MPK of §III (standard, not communication-avoiding): s products in sequence,
  * W[:,0] = (A v - theta_0 v) / sigma, W[:,i] = (A W[:,i-1] - theta_i W[:,i-1]) / sigma,

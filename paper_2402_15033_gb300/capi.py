@@ -68,6 +68,11 @@ SIGNATURES = {
     "ortho_update": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp]),
     "ortho_stage1_f32": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "ortho_stage2_f32": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
+    "gmres_batch_footprint": (_sz, [_i32, _vp, _vp, C.POINTER(gmres_opts)]),
+    "gmres_batch_create": (_i32, [C.POINTER(_vp), _i32, _vp, _vp, _vp, _vp, C.POINTER(gmres_opts), _vp]),
+    "gmres_batch_solve": (_i32, [_vp, _vp, _vp, _vp]),
+    "gmres_batch_autotune": (_i32, [_vp, C.POINTER(_dbl)]),
+    "gmres_batch_destroy": (_i32, [_vp]),
     "ortho_stage1_noalloc": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp]),
 }
 
@@ -171,6 +176,63 @@ class Solver:
     def close(self):
         if getattr(self, "h", None):
             load().gmres_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr_array(arrs):
+    return (C.c_void_p * len(arrs))(*[a.ctypes.data_as(C.c_void_p) for a in arrs])
+
+
+class Batch:
+    """gmres_batch_create / _solve / _autotune / _destroy over a list of CSR
+    matrices (objects with n, rowptr, colind, vals as numpy arrays)."""
+
+    def __init__(self, mats, opts: gmres_opts | None = None, stream=None):
+        lib = load()
+        self.mats = list(mats)
+        self.n = [int(A.n) for A in self.mats]
+        ns = len(self.mats)
+        nn = (C.c_int64 * ns)(*self.n)
+        o = opts if opts is not None else default_opts()
+        h = C.c_void_p()
+        check(lib.gmres_batch_create(C.byref(h), ns, nn, _ptr_array([A.rowptr for A in self.mats]),
+                                     _ptr_array([A.colind for A in self.mats]), _ptr_array([A.vals for A in self.mats]),
+                                     C.byref(o), C.c_void_p(stream or 0)))
+        self.h = h
+        self.opts = o
+
+    @staticmethod
+    def footprint(mats, opts=None) -> int:
+        ns = len(mats)
+        nn = (C.c_int64 * ns)(*[int(A.n) for A in mats])
+        nz = (C.c_int64 * ns)(*[int(A.rowptr[-1]) for A in mats])
+        o = opts if opts is not None else default_opts()
+        return int(load().gmres_batch_footprint(ns, nn, nz, C.byref(o)))
+
+    def solve(self, bs, xs):
+        """bs, xs: lists of float64 numpy arrays (x holds x0, receives x).
+        Returns (worst status, list of result dicts)."""
+        ns = len(self.mats)
+        res = (gmres_result * ns)()
+        rc = load().gmres_batch_solve(self.h, _ptr_array(bs), _ptr_array(xs), res)
+        if rc in (GMRES_ERR_ARG, GMRES_ERR_CUDA, GMRES_ERR_OOM):
+            raise GmresError(rc, last_error())
+        return rc, [r.as_dict() for r in res]
+
+    def autotune(self):
+        out = (C.c_double * 4)()
+        check(load().gmres_batch_autotune(self.h, out))
+        return {"gram_ms": out[0], "update_ms": out[1], "gram_grid": int(out[2]), "row_grid": int(out[3])}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().gmres_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
