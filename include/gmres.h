@@ -225,6 +225,50 @@ int gmres_batch_autotune(gmres_batch* b, double* res_ms);
 
 int gmres_batch_destroy(gmres_batch* b);   /* NULL-safe */
 
+/* Device bytes gmres_create would allocate for an n x n matrix with nnz
+ * nonzeros under these options (0 for invalid arguments). */
+size_t gmres_footprint(int64_t n, int64_t nnz, const gmres_opts* opts);
+
+/* ------------------------------------------------ serving loop (continuous batching)
+ * A worker thread serves independent solves of different sizes, matrices and
+ * options.  Requests are admitted in arrival order whenever a slot is free
+ * and their device footprint (gmres_footprint) fits the unused part of the
+ * memory budget; admitted solves run concurrently on streams of their own,
+ * one restart cycle at a time, each keeping its Krylov basis and Hessenberg
+ * state resident on the device until it finishes.  A request that arrives
+ * while others are running joins them at the next cycle boundary.  Results do
+ * not depend on what else is being served.  Latency is submit-to-completion
+ * on the host clock. */
+typedef struct gmres_server gmres_server;
+
+typedef struct gmres_server_stats {
+    int64_t submitted, admitted, completed, rejected, failed, active, pending;
+    double  p50_ms, p99_ms, mean_ms;    /* latency of completed requests            */
+    double  solves_per_s, busy_s;       /* completed / (last completion - first submit) */
+    size_t  mem_budget, mem_in_use;     /* bytes                                     */
+} gmres_server_stats;
+
+/* mem_budget = 0: 90% of the device memory free at start.  max_active >= 1. */
+int gmres_server_start(gmres_server** out, size_t mem_budget, int32_t max_active);
+
+/* Copies the host CSR (rowptr int64, colind int32, vals FP64), b and x0 (may
+ * be NULL: zero) and queues the request; *id identifies it.  A request whose
+ * footprint exceeds the whole budget finishes at once with GMRES_ERR_OOM. */
+int gmres_server_submit(gmres_server* s, int64_t n, const int64_t* rowptr, const int32_t* colind,
+                        const double* vals, const double* b, const double* x0, const gmres_opts* opts,
+                        int64_t* id);
+
+/* 1 = finished (x[n] and *res filled, the request released), 0 = not yet
+ * (timeout_s < 0 waits forever; poll = wait with timeout 0). */
+int gmres_server_wait(gmres_server* s, int64_t id, double* x, gmres_result* res, double timeout_s);
+int gmres_server_poll(gmres_server* s, int64_t id, double* x, gmres_result* res);
+
+int gmres_server_get_stats(gmres_server* s, gmres_server_stats* st);
+
+/* Serves every queued and running request to completion, then joins the
+ * worker and frees the server (results not collected are dropped). */
+int gmres_server_stop(gmres_server* s);
+
 /* ------------------------------------------------ matrix powers kernel
  * MPK of §III (standard, not communication-avoiding): s products in sequence,
  * W[:,0] = (A v - theta_0 v) / sigma, W[:,i] = (A W[:,i-1] - theta_i W[:,i-1]) / sigma,

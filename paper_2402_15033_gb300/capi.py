@@ -40,6 +40,17 @@ class gmres_opts(C.Structure):
                 ("reserved", C.c_int32 * 7)]
 
 
+class gmres_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("rejected", C.c_int64), ("failed", C.c_int64), ("active", C.c_int64), ("pending", C.c_int64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
+                ("solves_per_s", C.c_double), ("busy_s", C.c_double),
+                ("mem_budget", C.c_size_t), ("mem_in_use", C.c_size_t)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class gmres_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("restarts", C.c_int32), ("ir_steps", C.c_int32),
                 ("breakdown_block", C.c_int32), ("breakdown_pivot", C.c_int32),
@@ -73,6 +84,13 @@ SIGNATURES = {
     "gmres_batch_solve": (_i32, [_vp, _vp, _vp, _vp]),
     "gmres_batch_autotune": (_i32, [_vp, C.POINTER(_dbl)]),
     "gmres_batch_destroy": (_i32, [_vp]),
+    "gmres_footprint": (_sz, [_i64, _i64, C.POINTER(gmres_opts)]),
+    "gmres_server_start": (_i32, [C.POINTER(_vp), _sz, _i32]),
+    "gmres_server_submit": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, C.POINTER(gmres_opts), C.POINTER(_i64)]),
+    "gmres_server_wait": (_i32, [_vp, _i64, _vp, C.POINTER(gmres_result), _dbl]),
+    "gmres_server_poll": (_i32, [_vp, _i64, _vp, C.POINTER(gmres_result)]),
+    "gmres_server_get_stats": (_i32, [_vp, C.POINTER(gmres_server_stats)]),
+    "gmres_server_stop": (_i32, [_vp]),
     "ortho_stage1_noalloc": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp]),
 }
 
@@ -238,6 +256,61 @@ class Batch:
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+def footprint(n, nnz, opts=None) -> int:
+    o = opts if opts is not None else default_opts()
+    return int(load().gmres_footprint(int(n), int(nnz), C.byref(o)))
+
+
+class Server:
+    """gmres_server_start / submit / wait / stats / stop."""
+
+    def __init__(self, mem_budget=0, max_active=16):
+        h = C.c_void_p()
+        check(load().gmres_server_start(C.byref(h), int(mem_budget), int(max_active)))
+        self.h = h
+        self._n = {}
+
+    def submit(self, A, b, x0=None, opts=None):
+        rid = C.c_int64()
+        o = opts if opts is not None else default_opts()
+        check(load().gmres_server_submit(self.h, int(A.n), A.rowptr.ctypes.data_as(C.c_void_p),
+                                         A.colind.ctypes.data_as(C.c_void_p), A.vals.ctypes.data_as(C.c_void_p),
+                                         b.ctypes.data_as(C.c_void_p),
+                                         None if x0 is None else x0.ctypes.data_as(C.c_void_p), C.byref(o),
+                                         C.byref(rid)))
+        self._n[rid.value] = int(A.n)
+        return rid.value
+
+    def wait(self, rid, timeout=-1.0):
+        """Returns (x, result dict) once finished, or None on timeout."""
+        n = self._n[rid]
+        x = __import__("numpy").zeros(n)
+        res = gmres_result()
+        got = load().gmres_server_wait(self.h, int(rid), x.ctypes.data_as(C.c_void_p), C.byref(res), float(timeout))
+        if got < 0:
+            raise GmresError(got, last_error())
+        if got == 0:
+            return None
+        del self._n[rid]
+        return x, res.as_dict()
+
+    def stats(self):
+        st = gmres_server_stats()
+        check(load().gmres_server_get_stats(self.h, C.byref(st)))
+        return st.as_dict()
+
+    def stop(self):
+        if getattr(self, "h", None):
+            load().gmres_server_stop(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.stop()
         except Exception:
             pass
 

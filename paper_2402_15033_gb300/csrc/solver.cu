@@ -26,7 +26,7 @@
 #include <cmath>
 #include <vector>
 #include <algorithm>
-#include "solver_state.cuh"
+#include "solver_run.cuh"
 
 namespace gm {
 
@@ -84,6 +84,15 @@ struct gmres_ctx {
     std::vector<cudaEvent_t> ev;
 };
 
+namespace gm {
+
+enum { PH_MPK = 0, PH_S1 = 1, PH_S2 = 2, PH_LS = 3 };
+
+size_t pip_bytes_for(int64_t n, const gmres_opts& o);
+size_t ctx_bytes(int64_t n, int64_t nnz, const gmres_opts& o);
+
+}  // namespace gm
+
 extern "C" {
 
 const char* gmres_last_error(void) { return g_err; }
@@ -111,6 +120,41 @@ size_t ortho_workspace_bytes(int64_t n, int32_t k, int32_t nb) {
     return pip_work_layout(nullptr, n, k, nb).bytes;
 }
 
+}  // extern "C"
+
+namespace gm {
+
+size_t pip_bytes_for(int64_t n, const gmres_opts& o) {
+    size_t wb = 0;
+    for (int st0 = 0; st0 < o.m; st0 += o.s) {
+        wb = std::max(wb, ortho_workspace_bytes(n, st0 + 1, o.s));
+        const int t = st0 + o.s;
+        if (t % o.panel == 0) {
+            const int lo = (t == o.panel) ? 0 : t - o.panel + 1;
+            wb = std::max(wb, ortho_workspace_bytes(n, lo, t - lo + 1));
+        }
+    }
+    return wb;
+}
+
+// Device bytes gmres_create allocates for a host-CSR context (each piece
+// rounded up to the 256-byte allocation granule).
+size_t ctx_bytes(int64_t n, int64_t nnz, const gmres_opts& o) {
+    auto up = [](size_t b) { return (b + 511) & ~(size_t)511; };
+    const int64_t ldq = (n + 31) / 32 * 32;
+    const bool mixed = o.precision == GMRES_PREC_MIXED;
+    const size_t esz = mixed ? 4 : 8;
+    const size_t nz = (size_t)(nnz > 0 ? nnz : 1);
+    size_t b = up((n + 1) * 4) + up(nz * 4) + up(nz * 8);
+    if (mixed) b += up(nz * 4) + up(ldq * 8);
+    b += up((size_t)(o.m + 1) * ldq * esz) + 2 * up(ldq * 8);
+    b += up(norm_grid(n) * 8) + up(256) + up(pip_bytes_for(n, o)) + up(sizeof(DevState)) + up(16);
+    return b;
+}
+
+}  // namespace gm
+
+extern "C" {
 static int check_opts(const gmres_opts* o) {
     GM_ARG(o->m >= 1 && o->m + 1 <= kMaxCols, "m must be in [1, %d]", kMaxCols - 1);
     GM_ARG(o->s >= 1 && o->s <= 16, "s must be in [1, 16]");
@@ -263,15 +307,7 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
     CK(cuda_rc(cudaMalloc(&c->red_counter, 256), "cudaMalloc counter"));
     CK(cuda_rc(cudaMemsetAsync(c->red_counter, 0, 256, s), "memset counter"));
     // PIP workspace: the largest of the cycle's calls
-    size_t wb = 0;
-    for (int st0 = 0; st0 < o.m; st0 += o.s) {
-        wb = std::max(wb, ortho_workspace_bytes(n, st0 + 1, o.s));
-        const int t = st0 + o.s;
-        if (t % o.panel == 0) {
-            const int lo = (t == o.panel) ? 0 : t - o.panel + 1;
-            wb = std::max(wb, ortho_workspace_bytes(n, lo, t - lo + 1));
-        }
-    }
+    const size_t wb = pip_bytes_for(n, o);
     c->pip_bytes = wb;
     CK(cuda_rc(cudaMalloc(&c->pip_work, wb), "cudaMalloc workspace"));
     CK(cuda_rc(cudaMemsetAsync(c->pip_work, 0, wb, s), "memset workspace"));
@@ -294,8 +330,6 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
     return GMRES_OK;
 }
 
-// phases for opts.timing
-enum { PH_MPK = 0, PH_S1 = 1, PH_S2 = 2, PH_LS = 3 };
 
 }  // extern "C"
 
@@ -386,27 +420,32 @@ static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
 
 extern "C" {
 
-int gmres_solve(gmres_ctx* c, const double* b, double* x, int32_t ptr_on_device, gmres_result* res) {
-    clear_error();
-    GM_ARG(c != nullptr && b != nullptr && x != nullptr, "NULL argument");
-    gmres_result r{};
-    r.breakdown_block = -1;
-    auto finish = [&](int status) {
-        r.status = status;
-        if (res) *res = r;
-        return status;
-    };
-    if (cudaSetDevice(c->device) != cudaSuccess) return finish(cuda_rc(cudaGetLastError(), "cudaSetDevice"));
+}  // extern "C"
+
+namespace gm {
+
+// ---------------------------------------------------------------- step-wise solve
+// gmres_solve is begin, then {enqueue_check, synchronize, decide, enqueue_cycle}
+// until decide says stop, then finish.  The serving loop drives the same steps
+// for many contexts on their own streams.
+
+cudaStream_t run_stream(const SolveRun* R) { return R->c->stream; }
+
+int run_begin(gmres_ctx* c, SolveRun* R, const double* b, const double* x, int on_device) {
+    *R = SolveRun{};
+    R->c = c;
+    R->r.breakdown_block = -1;
+    R->status = GMRES_WARN_MAXIT;
+    R->on_device = on_device;
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_rc(cudaGetLastError(), "cudaSetDevice");
     cudaStream_t s = c->stream;
     const gmres_opts& o = c->opts;
-    const cudaMemcpyKind kin = ptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    const cudaMemcpyKind kout = ptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const size_t vb = c->n * sizeof(double);
-    cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (o.timing) {
-        cudaEventCreate(&t0);
-        cudaEventCreate(&t1);
-        cudaEventRecord(t0, s);
+        cudaEventCreate(&R->t0);
+        cudaEventCreate(&R->t1);
+        cudaEventRecord(R->t0, s);
     }
     int rc = cuda_rc(cudaMemcpyAsync(c->b, b, vb, kin, s), "copy b");
     if (!rc) rc = cuda_rc(cudaMemcpyAsync(c->x, x, vb, kin, s), "copy x");
@@ -414,91 +453,138 @@ int gmres_solve(gmres_ctx* c, const double* b, double* x, int32_t ptr_on_device,
                           "norm b");
     if (!rc) rc = cuda_rc(cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s), "state read");
     if (!rc) rc = cuda_rc(cudaStreamSynchronize(s), "sync");
-    if (rc) return finish(rc);
-    const double bnorm = c->hst->bnorm;
-    if (!std::isfinite(bnorm)) {
+    if (rc) return rc;
+    R->bnorm = c->hst->bnorm;
+    if (!std::isfinite(R->bnorm)) {
         set_error("b has non-finite entries");
-        return finish(GMRES_ERR_NAN);
+        R->status = GMRES_ERR_NAN;
+        R->finished = true;
+        return GMRES_OK;
     }
-    int status = GMRES_WARN_MAXIT;
-    if (bnorm == 0.0) {
+    if (R->bnorm == 0.0) {
         // the solution of A x = 0 is x = 0
         rc = cuda_rc(cudaMemsetAsync(c->x, 0, vb, s), "zero x");
-        if (!rc) rc = cuda_rc(cudaMemcpyAsync(x, c->x, vb, kout, s), "copy x");
-        if (!rc) rc = cuda_rc(cudaStreamSynchronize(s), "sync");
-        return finish(rc ? rc : GMRES_OK);
+        R->status = GMRES_OK;
+        R->finished = true;
+        return rc;
     }
-    {
-        double tol_abs = o.tol * bnorm;
-        rc = cuda_rc(cudaMemcpyAsync(&c->st->tol_abs, &tol_abs, sizeof(double), cudaMemcpyHostToDevice, s), "tol");
-        int32_t zero = 0;
-        if (!rc) rc = cuda_rc(cudaMemcpyAsync(&c->st->iters, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, s), "iters");
-        if (!rc) rc = cuda_rc(cudaStreamSynchronize(s), "sync");
-        if (rc) return finish(rc);
+    double tol_abs = o.tol * R->bnorm;
+    rc = cuda_rc(cudaMemcpyAsync(&c->st->tol_abs, &tol_abs, sizeof(double), cudaMemcpyHostToDevice, s), "tol");
+    int32_t zero = 0;
+    if (!rc) rc = cuda_rc(cudaMemcpyAsync(&c->st->iters, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, s), "iters");
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(s), "sync");   // tol_abs is a stack value
+    return rc;
+}
+
+int run_enqueue_check(SolveRun* R) {
+    gmres_ctx* c = R->c;
+    cudaStream_t s = c->stream;
+    double* rout = c->r ? c->r : static_cast<double*>(c->basis);
+    int rc = cuda_rc(launch_residual(s, c->A, c->b, c->x, rout, c->red_partial, c->red_counter, c->st, 0), "residual");
+    if (!rc) rc = cuda_rc(cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s), "state read");
+    return rc;
+}
+
+int run_decide(SolveRun* R) {
+    gmres_ctx* c = R->c;
+    const gmres_opts& o = c->opts;
+    const DevState& h = *c->hst;
+    gmres_result& r = R->r;
+    const int cyc = R->cyc;
+    if (cyc > 0 && o.timing) {
+        // accumulate the previous cycle's phase times
+        for (size_t i = 0; i + 1 < R->marks.size(); i += 2) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, c->ev[R->marks[i].second], c->ev[R->marks[i + 1].second]);
+            double* dst = R->marks[i].first == PH_MPK ? &r.t_mpk_ms : R->marks[i].first == PH_S1 ? &r.t_stage1_ms
+                        : R->marks[i].first == PH_S2 ? &r.t_stage2_ms : &r.t_ls_ms;
+            *dst += ms;
+        }
     }
-    std::vector<std::pair<int, int>> marks;
+    r.iters = h.iters;
+    r.restarts = cyc;
+    r.relres_true = h.beta / R->bnorm;
+    if (cyc > 0) r.relres_implicit = h.resid / R->bnorm;
     const int nstat = o.m / o.s + o.m / o.panel;
-    for (int cyc = 0;; ++cyc) {
-        double* rout = c->r ? c->r : static_cast<double*>(c->basis);
-        rc = cuda_rc(launch_residual(s, c->A, c->b, c->x, rout, c->red_partial, c->red_counter, c->st, 0),
-                     "residual");
-        if (!rc) rc = cuda_rc(cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s), "state read");
-        if (!rc) rc = cuda_rc(cudaStreamSynchronize(s), "sync");
-        if (rc) return finish(rc);
-        const DevState& h = *c->hst;
-        if (cyc > 0 && o.timing) {
-            // accumulate the previous cycle's phase times
-            for (size_t i = 0; i + 1 < marks.size(); i += 2) {
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, c->ev[marks[i].second], c->ev[marks[i + 1].second]);
-                double* dst = marks[i].first == PH_MPK ? &r.t_mpk_ms : marks[i].first == PH_S1 ? &r.t_stage1_ms
-                            : marks[i].first == PH_S2 ? &r.t_stage2_ms : &r.t_ls_ms;
-                *dst += ms;
-            }
+    for (int i = 0; i < nstat; ++i) {
+        if (h.blkstat[i]) {
+            r.breakdown_block = i;
+            r.breakdown_pivot = h.blkstat[i];
+            set_error("Cholesky breakdown in %s %d at pivot %d (restart cycle %d)",
+                      i < o.m / o.s ? "stage-1 block" : "stage-2 panel",
+                      i < o.m / o.s ? i : i - o.m / o.s, h.blkstat[i], cyc - 1);
+            R->status = GMRES_ERR_BREAKDOWN;
+            return (R->finished = true), 1;
         }
-        r.iters = h.iters;
-        r.restarts = cyc;
-        r.relres_true = h.beta / bnorm;
-        if (cyc > 0) r.relres_implicit = h.resid / bnorm;
-        for (int i = 0; i < nstat; ++i) {
-            if (h.blkstat[i]) {
-                r.breakdown_block = i;
-                r.breakdown_pivot = h.blkstat[i];
-                set_error("Cholesky breakdown in %s %d at pivot %d (restart cycle %d)",
-                          i < o.m / o.s ? "stage-1 block" : "stage-2 panel",
-                          i < o.m / o.s ? i : i - o.m / o.s, h.blkstat[i], cyc - 1);
-                status = GMRES_ERR_BREAKDOWN;
-                break;
-            }
-        }
-        if (status == GMRES_ERR_BREAKDOWN) break;
-        if (!std::isfinite(h.beta)) {
-            set_error("non-finite residual norm");
-            status = GMRES_ERR_NAN;
-            break;
-        }
-        if (h.beta <= o.tol * bnorm) { status = GMRES_OK; break; }
-        if (cyc >= o.max_restarts) { status = GMRES_WARN_MAXIT; break; }
-        marks.clear();
-        rc = o.precision == GMRES_PREC_MIXED ? run_cycle<float>(c, o.timing ? &marks : nullptr)
-                                             : run_cycle<double>(c, o.timing ? &marks : nullptr);
-        if (o.precision == GMRES_PREC_MIXED) ++r.ir_steps;
-        if (rc) return finish(rc);
     }
-    rc = cuda_rc(cudaMemcpyAsync(x, c->x, vb, kout, s), "copy x");
-    if (o.timing && !rc) {
-        cudaEventRecord(t1, s);
+    if (!std::isfinite(h.beta)) {
+        set_error("non-finite residual norm");
+        R->status = GMRES_ERR_NAN;
+        return (R->finished = true), 1;
     }
+    if (h.beta <= o.tol * R->bnorm) { R->status = GMRES_OK; return (R->finished = true), 1; }
+    if (cyc >= o.max_restarts) { R->status = GMRES_WARN_MAXIT; return (R->finished = true), 1; }
+    return 0;
+}
+
+int run_enqueue_cycle(SolveRun* R) {
+    gmres_ctx* c = R->c;
+    const gmres_opts& o = c->opts;
+    R->marks.clear();
+    const int rc = o.precision == GMRES_PREC_MIXED ? run_cycle<float>(c, o.timing ? &R->marks : nullptr)
+                                                   : run_cycle<double>(c, o.timing ? &R->marks : nullptr);
+    if (o.precision == GMRES_PREC_MIXED) ++R->r.ir_steps;
+    ++R->cyc;
+    return rc;
+}
+
+int run_finish(SolveRun* R, double* x) {
+    gmres_ctx* c = R->c;
+    cudaStream_t s = c->stream;
+    const cudaMemcpyKind kout = R->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    int rc = cuda_rc(cudaMemcpyAsync(x, c->x, c->n * sizeof(double), kout, s), "copy x");
+    if (c->opts.timing && !rc) cudaEventRecord(R->t1, s);
     if (!rc) rc = cuda_rc(cudaStreamSynchronize(s), "sync");
-    if (o.timing) {
+    if (c->opts.timing) {
         float ms = 0.f;
-        if (!rc) cudaEventElapsedTime(&ms, t0, t1);
-        r.t_total_ms = ms;
-        cudaEventDestroy(t0);
-        cudaEventDestroy(t1);
+        if (!rc) cudaEventElapsedTime(&ms, R->t0, R->t1);
+        R->r.t_total_ms = ms;
+        cudaEventDestroy(R->t0);
+        cudaEventDestroy(R->t1);
+        R->t0 = R->t1 = nullptr;
     }
-    if (rc) return finish(rc);
-    return finish(status);
+    R->r.status = rc ? rc : R->status;
+    return rc;
+}
+
+}  // namespace gm
+
+extern "C" {
+
+int gmres_solve(gmres_ctx* c, const double* b, double* x, int32_t ptr_on_device, gmres_result* res) {
+    clear_error();
+    GM_ARG(c != nullptr && b != nullptr && x != nullptr, "NULL argument");
+    SolveRun R;
+    int rc = run_begin(c, &R, b, x, ptr_on_device);
+    while (!rc && !R.finished) {
+        rc = run_enqueue_check(&R);
+        if (!rc) rc = cuda_rc(cudaStreamSynchronize(c->stream), "sync");
+        if (rc || run_decide(&R)) break;
+        rc = run_enqueue_cycle(&R);
+    }
+    if (!rc) rc = run_finish(&R, x);
+    R.r.status = rc ? rc : R.status;
+    if (res) *res = R.r;
+    return R.r.status;
+}
+
+size_t gmres_footprint(int64_t n, int64_t nnz, const gmres_opts* opts) {
+    if (n <= 0 || nnz < 0) return 0;
+    gmres_opts o;
+    if (opts) o = *opts; else gmres_default_opts(&o);
+    if (o.ortho == GMRES_ORTHO_BCGS_PIP2) o.panel = o.s;
+    if (check_opts(&o)) return 0;
+    return ctx_bytes(n, nnz, o);
 }
 
 static int check_pip_args(int64_t n, const void* Q, int64_t ldq, int32_t k, const void* V, int64_t ldv,

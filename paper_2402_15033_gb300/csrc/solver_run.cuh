@@ -1,0 +1,34 @@
+// Step-wise solve on a gmres_ctx (used by gmres_solve and by the serving loop).
+#pragma once
+#include <vector>
+#include <utility>
+#include "solver_state.cuh"
+
+namespace gm {
+
+struct SolveRun {
+    gmres_ctx* c = nullptr;
+    gmres_result r{};
+    double bnorm = 0.0;
+    int cyc = 0;
+    int status = GMRES_WARN_MAXIT;
+    int on_device = 0;
+    bool finished = false;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    std::vector<std::pair<int, int>> marks;
+};
+
+// Copy b and x0, compute ||b|| (synchronizes the context's stream).  Sets
+// R->finished for b = 0 (x = 0) or a non-finite b.
+int run_begin(gmres_ctx* c, SolveRun* R, const double* b, const double* x, int on_device);
+// Enqueue r = b - A x and the read-back of the cycle state (asynchronous).
+int run_enqueue_check(SolveRun* R);
+// Once the stream has passed the read-back: 1 = stop (R->status final), 0 = run another cycle.
+int run_decide(SolveRun* R);
+// Enqueue one restart cycle (asynchronous).
+int run_enqueue_cycle(SolveRun* R);
+// Copy x out and synchronize; R->r.status holds the final status.
+int run_finish(SolveRun* R, double* x);
+cudaStream_t run_stream(const SolveRun* R);
+
+}  // namespace gm
