@@ -322,6 +322,12 @@ def run_ours(args):
     if not args.no_solve and rank == 0:
         solve = solver_numbers(capi, dev, args)
 
+    # ---- the precision, batching and serving patterns
+    patterns = None
+    if not args.no_patterns and rank == 0:
+        patterns = {"mixed_precision": mixed_numbers(capi, dev), "batched": batched_numbers(capi, args),
+                    "serving": serving_numbers(capi, args)}
+
     # ---- CPU oracle on a bounded sample of the same workload
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -338,7 +344,8 @@ def run_ours(args):
                            "bytes_per_step": bytes_step, "l2": "basis 2 GB >> 129 MB L2, no flush needed",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "kernels": families, "e2e": e2e, "cpu_baseline": cpu,
-                "gpu_launches": (2 * NBLK + 2) * args.steps, "clocks": clk, "solver": solve}
+                "gpu_launches": (2 * NBLK + 2) * args.steps, "clocks": clk, "solver": solve,
+                "patterns": patterns}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -391,6 +398,171 @@ def solver_numbers(capi, dev, args):
     return out
 
 
+def mixed_numbers(capi, dev):
+    """Mixed-precision configuration: 3D Laplace 7-point on 160^3, FP32 basis and
+    MPK, FP64 Gram/Cholesky/Hessenberg and refinement, m=60, s=10, s^=60,
+    tol 1e-8.  Time to solution, and the error against x_true and against the
+    FP64 path on the same system."""
+    import numpy as np
+    import torch
+    import synth
+    from scipy.sparse import csr_matrix
+    A = synth.laplace3d(160)
+    xt = synth.x_true(A.n, 0)
+    M = csr_matrix((A.vals, A.colind, A.rowptr), shape=(A.n, A.n))
+    b = M @ xt
+    bd = torch.tensor(b, device=dev)
+    out = {"grid": "160^3", "n": A.n}
+    xs = {}
+    for name, prec in (("mixed", capi.GMRES_PREC_MIXED), ("fp64", capi.GMRES_PREC_FP64)):
+        S = capi.Solver.from_csr(A, capi.default_opts(m=60, s=10, panel=60, tol=1e-8, precision=prec,
+                                                      max_restarts=2000))
+        xd = torch.zeros(A.n, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, res = S.solve(bd, xd)
+        dt = time.perf_counter() - t0
+        S.close()
+        x = xd.cpu().numpy()
+        xs[name] = (rc, x)
+        out[name] = {"status": rc, "time_to_solution_s": round(dt, 3), "iters": res["iters"],
+                     "restarts": res["restarts"], "ir_steps": res["ir_steps"], "relres": res["relres_true"],
+                     "err_vs_x_true": float(np.linalg.norm(x - xt) / np.linalg.norm(xt)),
+                     "breakdown_block": res["breakdown_block"]}
+    if xs["mixed"][0] == 0 and xs["fp64"][0] == 0:
+        out["mixed"]["err_vs_fp64"] = float(np.linalg.norm(xs["mixed"][1] - xs["fp64"][1]) /
+                                            np.linalg.norm(xs["fp64"][1]))
+    return out
+
+
+def batched_systems(nsys, seed, nmin, nmax):
+    """Half 2D upwinded convection-diffusion (5-point, cell Peclet ~ U(0,10)),
+    half random banded (27 nnz/row, bandwidth 1000, N(0,1) off-diagonals,
+    diagonally dominant), n log-uniform in [nmin, nmax]."""
+    import numpy as np
+    import synth
+    g = synth.rng(seed)
+    mats = []
+    for i in range(nsys):
+        n = int(np.exp(g.uniform(np.log(nmin), np.log(nmax))))
+        if i % 2 == 0:
+            mats.append(synth.convdiff2d(int(np.ceil(np.sqrt(n))), seed * 100000 + i))
+        else:
+            mats.append(synth.banded_random(n, seed * 100000 + i))
+    return mats
+
+
+def batched_numbers(capi, args):
+    """Batched configuration: 256 nonsymmetric systems, n log-uniform in
+    [1e4, 5e5], FP32 basis / FP64 Gram, s=5, m=40, s^=40, tol 1e-8, one
+    persistent launch per step under captured CUDA graphs, autotuned grids;
+    against the plain FP64 single-solve path on the same systems."""
+    import numpy as np
+    import synth
+    from scipy.sparse import csr_matrix
+    t0 = time.perf_counter()
+    mats = batched_systems(args.batch_systems, 2, 1e4, args.batch_nmax)
+    bs = [csr_matrix((A.vals, A.colind, A.rowptr), shape=(A.n, A.n)) @ synth.x_true(A.n, i)
+          for i, A in enumerate(mats)]
+    gen_s = time.perf_counter() - t0
+    o = capi.default_opts(m=40, s=5, panel=40, tol=1e-8, precision=capi.GMRES_PREC_MIXED, max_restarts=500)
+    B = capi.Batch(mats, o)
+    tune = B.autotune()
+    xs = [np.zeros(A.n) for A in mats]
+    B.solve(bs, [np.zeros(A.n) for A in mats])   # warm-up (graph capture)
+    t0 = time.perf_counter()
+    rc, res = B.solve(bs, xs)
+    bt = time.perf_counter() - t0
+    B.close()
+    ok = sum(1 for r in res if r["status"] == 0)
+    relres = [r["relres_true"] for r in res if r["status"] == 0]
+    # plain FP64, one system at a time
+    o64 = capi.default_opts(m=40, s=5, panel=40, tol=1e-8, max_restarts=500)
+    t0 = time.perf_counter()
+    ok64 = 0
+    for A, b in zip(mats, bs):
+        S = capi.Solver.from_csr(A, o64)
+        x = np.zeros(A.n)
+        rc1, r1 = S.solve(b, x)
+        S.close()
+        ok64 += rc1 == 0
+    t64 = time.perf_counter() - t0
+    return {"systems": len(mats), "rows": int(sum(A.n for A in mats)), "nnz": int(sum(A.nnz for A in mats)),
+            "mixed_batched": {"solves_per_s": round(ok / bt, 3), "converged": ok, "wall_s": round(bt, 3),
+                              "max_relres": max(relres) if relres else None,
+                              "iters_median": int(np.median([r["iters"] for r in res]))},
+            "fp64_one_at_a_time": {"solves_per_s": round(ok64 / t64, 3), "converged": int(ok64),
+                                   "wall_s": round(t64, 3),
+                                   "note": "includes per-system create/destroy; FP64 BCGS-PIP breaks down on "
+                                           "systems whose monomial blocks violate Eq. (5)"},
+            "autotune": tune, "generate_s": round(gen_s, 1)}
+
+
+def serving_numbers(capi, args):
+    """Serving configuration: Poisson arrivals (rate swept) of solves drawn from
+    2D Laplace grids 128^2..1024^2 and 3D convection-diffusion grids
+    32^3..128^3, s in {5,10}, m in {30,60}, s^ = m, mixed precision served with
+    footprint admission; p50/p99 latency and solves/s, against the plain FP64
+    path solving the same requests one at a time."""
+    import numpy as np
+    import synth
+    from scipy.sparse import csr_matrix
+    g = synth.rng(3)
+    cache = {}
+
+    def mat(kind, N):
+        key = (kind, N)
+        if key not in cache:
+            cache[key] = synth.laplace2d(N) if kind == "lap2d" else synth.convdiff3d(N, 7000 + N)
+        return cache[key]
+
+    reqs = []
+    for i in range(args.serve_requests):
+        if g.random() < 0.5:
+            A = mat("lap2d", int(g.choice([128, 256, 512, 1024])))
+        else:
+            A = mat("cd3d", int(g.choice([32, 64, 96, 128])))
+        s = int(g.choice([5, 10]))
+        m = int(g.choice([30, 60]))
+        b = csr_matrix((A.vals, A.colind, A.rowptr), shape=(A.n, A.n)) @ synth.x_true(A.n, i)
+        reqs.append((A, b, s, m))
+    out = {"requests": len(reqs), "max_restarts": args.serve_restarts, "rates": []}
+    for rate in list(args.serve_rates) + [0.0]:
+        # rate 0: every request arrives at t = 0 (saturated server, peak solves/s)
+        arr = np.cumsum(g.exponential(1.0 / rate, size=len(reqs))) if rate > 0 else np.zeros(len(reqs))
+        srv = capi.Server(max_active=32)
+        ids = []
+        t0 = time.perf_counter()
+        for (A, b, s, m), ta in zip(reqs, arr):
+            while time.perf_counter() - t0 < ta:
+                time.sleep(0.001)
+            ids.append(srv.submit(A, b, opts=capi.default_opts(m=m, s=s, panel=m, tol=1e-8,
+                                                               precision=capi.GMRES_PREC_MIXED,
+                                                               max_restarts=args.serve_restarts)))
+        res = [srv.wait(i) for i in ids]
+        st = srv.stats()
+        srv.stop()
+        conv = sum(1 for _, r in res if r["status"] == 0)
+        out["rates"].append({"rate_per_s": rate if rate > 0 else "saturated", "p50_ms": round(st["p50_ms"], 2),
+                             "p99_ms": round(st["p99_ms"], 2), "solves_per_s": round(st["solves_per_s"], 3),
+                             "converged_per_s": round(conv / st["busy_s"], 3) if st["busy_s"] > 0 else None,
+                             "converged": conv,
+                             "statuses": sorted(set(r["status"] for _, r in res))})
+    t0 = time.perf_counter()
+    conv64 = 0
+    for A, b, s, m in reqs:
+        S = capi.Solver.from_csr(A, capi.default_opts(m=m, s=s, panel=m, tol=1e-8, max_restarts=args.serve_restarts))
+        x = np.zeros(A.n)
+        rc, r = S.solve(b, x)
+        S.close()
+        conv64 += rc == 0
+    t64 = time.perf_counter() - t0
+    out["fp64_one_at_a_time"] = {"solves_per_s": round(len(reqs) / t64, 3),
+                                 "converged_per_s": round(conv64 / t64, 3), "converged": int(conv64),
+                                 "wall_s": round(t64, 2)}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -402,6 +574,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-patterns", action="store_true", help="skip the mixed, batched and serving configurations")
+    ap.add_argument("--batch-systems", type=int, default=256)
+    ap.add_argument("--batch-nmax", type=float, default=5e5)
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-restarts", type=int, default=100)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[2.0, 8.0])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -143,68 +143,37 @@ def convdiff3d(N: int, seed: int) -> CSR:
 
 
 def banded_random(n: int, seed: int, band: int = 1000, offdiag: int = 26) -> CSR:
-    """Random banded CSR: ``offdiag`` distinct off-diagonal columns per row drawn
-    uniformly in [i-band, i+band] (clipped to the matrix, diagonal excluded),
-    N(0,1) values, diagonal equal to 1.1 * sum|off-diagonal| + 1 (strictly
-    diagonally dominant, nonsymmetric).  Rows whose clipped window holds fewer
-    than ``offdiag`` candidates take all of them."""
+    """Random banded CSR: ``offdiag`` distinct off-diagonal columns per row in
+    [i-band, i+band] (clipped to the matrix, diagonal excluded), N(0,1) values,
+    diagonal equal to 1.1 * sum|off-diagonal| + 1 (strictly diagonally
+    dominant, nonsymmetric).  The distinct columns come from sorted draws u_1 <=
+    ... <= u_k in [0, W-k] shifted by 0..k-1 (W = window size), a vectorized
+    sample of k distinct sorted positions; rows whose window holds fewer than
+    ``offdiag`` candidates take all of them."""
     g = rng(seed)
     i = np.arange(n, dtype=np.int64)
     lo = np.maximum(0, i - band)
     hi = np.minimum(n, i + band + 1)
-    cand = hi - lo - 1                          # window without the diagonal
-    draws = 2 * offdiag + 8
-    u = g.random((n, draws))
-    off = np.floor(u * cand[:, None]).astype(np.int64) + lo[:, None]
-    off = np.where(off >= i[:, None], off + 1, off)
-    off.sort(axis=1)
-    dup = np.zeros_like(off, dtype=bool)
-    dup[:, 1:] = off[:, 1:] == off[:, :-1]
-    key = np.where(dup, n + 1, off)              # duplicates sort to the end
-    order = np.argsort(key, axis=1, kind="stable")
-    uniq = np.take_along_axis(key, order, axis=1)
-    k = np.minimum(offdiag, cand)
-    cols, vals, rowptr = [], [], np.zeros(n + 1, dtype=np.int64)
-    ok = uniq[:, offdiag - 1] <= n if n > offdiag else np.zeros(n, bool)
-    # rows with enough distinct draws: vectorized; the rest: exact draw
-    v = g.standard_normal((n, offdiag))
-    counts = np.where(ok, offdiag, k) + 1
+    W = hi - lo - 1                                   # candidates without the diagonal
+    k = np.minimum(offdiag, W)
+    u = np.floor(g.random((n, offdiag)) * (np.maximum(W - k, 0) + 1)[:, None]).astype(np.int64)
+    u.sort(axis=1)
+    u += np.arange(offdiag)[None, :]
+    cols = lo[:, None] + u
+    cols = np.where(cols >= i[:, None], cols + 1, cols)   # skip the diagonal
+    valid = np.arange(offdiag)[None, :] < k[:, None]
+    v = g.standard_normal((n, offdiag)) * valid
+    diag = 1.1 * np.abs(v).sum(axis=1) + 1.0
+    allc = np.concatenate([np.where(valid, cols, n + 1), i[:, None]], axis=1)
+    allv = np.concatenate([v, diag[:, None]], axis=1)
+    o = np.argsort(allc, axis=1, kind="stable")
+    allc = np.take_along_axis(allc, o, axis=1)
+    allv = np.take_along_axis(allv, o, axis=1)
+    keep = allc <= n - 1
+    counts = keep.sum(axis=1)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
     rowptr[1:] = np.cumsum(counts)
-    nnz = int(rowptr[-1])
-    colind = np.empty(nnz, dtype=np.int64)
-    values = np.empty(nnz)
-    for r in np.nonzero(~ok)[0]:
-        pick = g.choice(int(cand[r]), size=int(k[r]), replace=False) + lo[r]
-        pick = np.where(pick >= r, pick + 1, pick)
-        uniq[r, : k[r]] = np.sort(pick)
-    for r_ok in (True, False):
-        rows = np.nonzero(ok == r_ok)[0]
-        if rows.size == 0:
-            continue
-        kk = offdiag if r_ok else None
-        for r in (rows if not r_ok else [None]):
-            if r_ok:
-                c = uniq[rows, :offdiag]
-                vv = v[rows]
-                d = 1.1 * np.abs(vv).sum(axis=1) + 1.0
-                allc = np.concatenate([c, rows[:, None]], axis=1)
-                allv = np.concatenate([vv, d[:, None]], axis=1)
-                o = np.argsort(allc, axis=1)
-                allc = np.take_along_axis(allc, o, axis=1)
-                allv = np.take_along_axis(allv, o, axis=1)
-                pos = rowptr[rows][:, None] + np.arange(offdiag + 1)[None, :]
-                colind[pos] = allc
-                values[pos] = allv
-            else:
-                kr_ = int(k[r])
-                c = uniq[r, :kr_]
-                vv = v[r, :kr_]
-                allc = np.concatenate([c, [r]])
-                allv = np.concatenate([vv, [1.1 * np.abs(vv).sum() + 1.0]])
-                o = np.argsort(allc)
-                colind[rowptr[r]:rowptr[r + 1]] = allc[o]
-                values[rowptr[r]:rowptr[r + 1]] = allv[o]
-    return CSR(n, rowptr, colind.astype(np.int32), values, f"banded_{n}_s{seed}")
+    return CSR(n, rowptr, allc[keep].astype(np.int32), allv[keep], f"banded_{n}_s{seed}")
 
 
 def x_true(n: int, seed: int = 0) -> np.ndarray:
