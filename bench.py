@@ -292,6 +292,36 @@ def run_ours(args):
                     "gbs": round(v["bytes"] / (v["ms_total"] * 1e-3) / 1e9, 1),
                     "tflops": round(v["flops"] / (v["ms_total"] * 1e-3) / 1e12, 4)} for k, v in fam.items()}
 
+    # ---- the same step with the opt-in double-float arithmetic (GMRES_ARITH_DD):
+    # 48-bit products and sums on the FP32 pipe; reported beside, not as, the
+    # FP64 headline
+    arith_dd = None
+    if not args.no_dd:
+        def step_dd():
+            for j, k in enumerate(K_BLOCKS):
+                Q = B[:, :k]
+                V = B[:, k:k + S]
+                Rb = Rh[:k + S, k:k + S]
+                capi.ortho_gram_chol_dd(Q, V, Rb, work, st[j:j + 1], k=k, stream=stream)
+                capi.ortho_update(Q, V, Rb, st[j:j + 1], k=k, stream=stream, dd=True)
+            capi.ortho_gram_chol_dd(None, B, R2, work, st[NBLK:], k=0, stream=stream)
+            capi.ortho_update(None, B, R2, st[NBLK:], k=0, stream=stream, dd=True)
+        R2_64 = R2.clone()
+        for _ in range(2):
+            step_dd()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            step_dd()
+        b.record()
+        torch.cuda.synchronize()
+        dms = a.elapsed_time(b) / args.steps
+        arith_dd = {"value": round(bytes_step / (dms * 1e-3) / 1e9, 3), "unit": "GB/s", "ms_per_step": round(dms, 3),
+                    "arithmetic": "double-float (hi+lo FP32), ~2^-48 relative, FP64 in/out",
+                    "max_abs_R_diff_vs_fp64": float((R2 - R2_64).abs().max().item())}
+
     # ---- end to end: pinned host basis in, Q and R out, every step
     e2e = None
     if not args.no_e2e:
@@ -343,7 +373,7 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "n": n, "cols": NCOL, "s": S, "panel": NCOL - 1,
                            "bytes_per_step": bytes_step, "l2": "basis 2 GB >> 129 MB L2, no flush needed",
                            "parallelism": "replicas" if world > 1 else "single"},
-                "roofline": roofline, "kernels": families, "e2e": e2e, "cpu_baseline": cpu,
+                "roofline": roofline, "kernels": families, "arith_dd": arith_dd, "e2e": e2e, "cpu_baseline": cpu,
                 "gpu_launches": (2 * NBLK + 2) * args.steps, "clocks": clk, "solver": solve,
                 "patterns": patterns}
         print(json.dumps(line))
@@ -575,6 +605,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-patterns", action="store_true", help="skip the mixed, batched and serving configurations")
+    ap.add_argument("--no-dd", action="store_true", help="skip the double-float measurement")
     ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--batch-nmax", type=float, default=5e5)
     ap.add_argument("--serve-requests", type=int, default=24)

@@ -47,6 +47,13 @@ extern "C" {
 #define GMRES_PREC_MIXED           1  /* FP32 basis + MPK, FP64 Gram/Cholesky/Hessenberg, FP64 IR */
 #define GMRES_BASIS_MONOMIAL       0  /* §VI: monomial basis (scaled by a power of two)           */
 #define GMRES_BASIS_NEWTON         1  /* shifted products (A - theta_i I) v, shifts in opts.theta  */
+#define GMRES_ARITH_FP64           0  /* native FP64 pipe (default)                                 */
+#define GMRES_ARITH_DD             1  /* opt-in: double-float (hi + lo FP32) on the FP32 pipe:      */
+                                      /* error-free products, renormalized sums, ~2^-48 relative;   */
+                                      /* FP64 in/out.  32x less precise than FP64, so the block      */
+                                      /* Pythagorean step (Eq. 5) breaks down sooner on marginal     */
+                                      /* blocks; values must keep |x y| and partial sums inside the  */
+                                      /* FP32 exponent range (|x| in [2^-50, 2^50] for unit-scale n) */
 
 typedef struct gmres_opts {
     int32_t m;             /* restart length: m+1 basis vectors per cycle (Table 1)            */
@@ -62,7 +69,8 @@ typedef struct gmres_opts {
     double  theta[16];     /* Newton shifts theta_0..theta_{s-1} (basis = NEWTON)              */
     double  inner_tol;     /* mixed precision: relative tolerance of each inner FP32 solve     */
     int32_t max_ir;        /* mixed precision: maximum FP64 refinement steps                   */
-    int32_t reserved[7];
+    int32_t arith;         /* GMRES_ARITH_*: arithmetic of the Gram and block-update kernels   */
+    int32_t reserved[6];
 } gmres_opts;
 
 typedef struct gmres_result {
@@ -134,6 +142,8 @@ const char* gmres_last_error(void);
  *   d_status device int32: set to 0, or to the 1-based index of the first bad
  *            Cholesky pivot (then V is left unchanged and R holds P and the
  *            partial factor)
+ * Arithmetic: FP64 (GMRES_ARITH_FP64).  ortho_gram_chol_dd/ortho_update_dd
+ * run the same two halves in double-float arithmetic (GMRES_ARITH_DD).
  * Limits: k + nb <= 256, nb <= 64.  Returns GMRES_ERR_ARG / _WORKSPACE /
  * _CUDA for bad calls (nothing launched); a breakdown is reported only through
  * d_status, because the call is asynchronous. */
@@ -194,6 +204,16 @@ int ortho_gram_chol(void* stream, int64_t n, const double* Q, int64_t ldq, int32
 int ortho_update(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
                  double* V, int64_t ldv, int32_t nb, const double* R, int32_t ldr,
                  const int32_t* d_status);
+
+/* The same two halves with double-float arithmetic (GMRES_ARITH_DD): faster on
+ * GB300, whose FP64 pipe is 1/64 of its FP32 pipe, at ~2^-48 relative accuracy. */
+int ortho_gram_chol_dd(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
+                       const double* V, int64_t ldv, int32_t nb, double* R, int32_t ldr,
+                       void* d_work, size_t work_bytes, int32_t* d_status);
+
+int ortho_update_dd(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
+                    double* V, int64_t ldv, int32_t nb, const double* R, int32_t ldr,
+                    const int32_t* d_status);
 
 /* ------------------------------------------------ batched solver (many uneven systems)
  * nsys independent systems of different sizes and matrices share one set of

@@ -30,6 +30,8 @@ GMRES_PREC_FP64 = 0
 GMRES_PREC_MIXED = 1
 GMRES_BASIS_MONOMIAL = 0
 GMRES_BASIS_NEWTON = 1
+GMRES_ARITH_FP64 = 0
+GMRES_ARITH_DD = 1
 
 
 class gmres_opts(C.Structure):
@@ -37,7 +39,7 @@ class gmres_opts(C.Structure):
                 ("tol", C.c_double), ("sigma", C.c_double),
                 ("ortho", C.c_int32), ("precision", C.c_int32), ("basis", C.c_int32), ("timing", C.c_int32),
                 ("theta", C.c_double * 16), ("inner_tol", C.c_double), ("max_ir", C.c_int32),
-                ("reserved", C.c_int32 * 7)]
+                ("arith", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class gmres_server_stats(C.Structure):
@@ -77,6 +79,8 @@ SIGNATURES = {
     "gmres_mpk": (_i32, [_vp, _vp, _vp, _i64, _i32, _dbl, C.POINTER(_dbl)]),
     "ortho_gram_chol": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "ortho_update": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp]),
+    "ortho_gram_chol_dd": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
+    "ortho_update_dd": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp]),
     "ortho_stage1_f32": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "ortho_stage2_f32": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "gmres_batch_footprint": (_sz, [_i32, _vp, _vp, C.POINTER(gmres_opts)]),
@@ -337,13 +341,20 @@ def ortho_gram_chol(Q, V, R, work, status, k=None, stream=None):
     return check(_ortho(load().ortho_gram_chol, Q, V, R, work, status, k, stream))
 
 
-def ortho_update(Q, V, R, status, k=None, stream=None):
-    """Second half of BCGS-PIP: V <- (V - Q P) T^{-1}."""
+def ortho_gram_chol_dd(Q, V, R, work, status, k=None, stream=None):
+    """ortho_gram_chol in double-float arithmetic (~2^-48 relative)."""
+    k = (Q.shape[1] if Q is not None else 0) if k is None else k
+    return check(_ortho(load().ortho_gram_chol_dd, Q, V, R, work, status, k, stream))
+
+
+def ortho_update(Q, V, R, status, k=None, stream=None, dd=False):
+    """Second half of BCGS-PIP: V <- (V - Q P) T^{-1} (dd: double-float arithmetic)."""
     k = (Q.shape[1] if Q is not None else 0) if k is None else k
     n, nb = V.shape
     ldq = Q.stride(1) if (Q is not None and k > 0) else n
     qp = C.c_void_p(Q.data_ptr()) if (Q is not None and k > 0) else None
-    return check(load().ortho_update(C.c_void_p(stream or 0), int(n), qp, int(ldq), int(k),
+    fn = load().ortho_update_dd if dd else load().ortho_update
+    return check(fn(C.c_void_p(stream or 0), int(n), qp, int(ldq), int(k),
                                      C.c_void_p(V.data_ptr()), int(V.stride(1)), int(nb),
                                      C.c_void_p(R.data_ptr()), int(R.stride(1)), C.c_void_p(status.data_ptr())))
 

@@ -77,7 +77,7 @@ __device__ inline double* r_block(DevState* st, int which, int k0) {
     return (which == 0 ? st->Rhat : st->Cm) + (size_t)k0 * kMaxCols;
 }
 
-template <typename T, int NB>
+template <typename T, int NB, bool DDA>
 __global__ void __launch_bounds__(kGramThreads)
 bgram_skinny_kernel(BatchDev B, T* basis, int k, int vcol, int which, int rrow, int statidx, int mode) {
     extern __shared__ double smem[];
@@ -91,14 +91,15 @@ bgram_skinny_kernel(BatchDev B, T* basis, int k, int vcol, int which, int rrow, 
         double* partial0 = B.partial + (size_t)S.v0 * ps;
         const T* Q = basis + S.row0;
         const T* V = basis + S.row0 + (int64_t)vcol * B.ld;
-        gram_skinny_part<T, NB>(S.n, Q, B.ld, k, V, B.ld, 0, b, S.G, partial0 + (size_t)b * ps, smem);
+        if (DDA) gram_skinny_part_df<T, NB>(S.n, Q, B.ld, k, V, B.ld, 0, b, S.G, partial0 + (size_t)b * ps, smem);
+        else gram_skinny_part<T, NB>(S.n, Q, B.ld, k, V, B.ld, 0, b, S.G, partial0 + (size_t)b * ps, smem);
         pip_finish(k, NB, 0, 1, S.G, r_block(st, which, vcol) + rrow, kMaxCols, partial0, ps,
                    B.counter + 8 * s, B.gram + (size_t)s * kMaxNB * kMaxNB, &st->blkstat[statidx], &st->done, smem,
                    mode);
     }
 }
 
-template <typename T>
+template <typename T, bool DDA>
 __global__ void __launch_bounds__(kGramThreads)
 bgram_wide_kernel(BatchDev B, T* basis, int k, int nb, int vcol, int which, int rrow, int statidx, int mode) {
     extern __shared__ double smem[];
@@ -112,16 +113,19 @@ bgram_wide_kernel(BatchDev B, T* basis, int k, int nb, int vcol, int which, int 
         double* partial0 = B.partial + (size_t)S.v0 * ps;
         const T* Q = basis + S.row0;
         const T* V = basis + S.row0 + (int64_t)vcol * B.ld;
-        gram_wide_part<T>(S.n, Q, B.ld, k, V, B.ld, nb, 0, b, S.G, partial0 + (size_t)b * ps, smem);
+        if (DDA) gram_wide_part_df<T>(S.n, Q, B.ld, k, V, B.ld, nb, 0, b, S.G, partial0 + (size_t)b * ps, smem);
+        else gram_wide_part<T>(S.n, Q, B.ld, k, V, B.ld, nb, 0, b, S.G, partial0 + (size_t)b * ps, smem);
         pip_finish(k, nb, 0, 1, S.G, r_block(st, which, vcol) + rrow, kMaxCols, partial0, ps,
                    B.counter + 8 * s, B.gram + (size_t)s * kMaxNB * kMaxNB, &st->blkstat[statidx], &st->done, smem,
                    mode);
     }
 }
 
-template <typename T, int NB>
+template <typename T, int NB, bool DDA>
 __global__ void __launch_bounds__(kTile)
 bupdate_skinny_kernel(BatchDev B, T* basis, int k, int vcol, int which, int rrow, int statidx, int mode) {
+    __shared__ double Tinv[16 * 16];
+    __shared__ float2 Ws[kMaxCols * 16];
     __shared__ double Ps[kMaxCols * 16];
     __shared__ double Ts[16 * 16];
     __shared__ double Dinv[16];
@@ -134,20 +138,29 @@ bupdate_skinny_kernel(BatchDev B, T* basis, int k, int vcol, int which, int rrow
         const double* R = r_block(st, which, vcol) + rrow;
         if (s != cur) {
             __syncthreads();
-            stage_pt<NB>(k, R, kMaxCols, mode, Ps, Ts, Dinv);
+            if (DDA) stage_w_df(k, NB, R, kMaxCols, mode, Ws, NB, 1, Tinv);
+            else stage_pt<NB>(k, R, kMaxCols, mode, Ps, Ts, Dinv);
             cur = s;
         }
         const int64_t row = (int64_t)(t - S.t0) * kTile + threadIdx.x;
-        if (row < S.n)
-            update_row<T, NB>(row, basis + S.row0, B.ld, k, basis + S.row0 + (int64_t)vcol * B.ld, B.ld, Ps, Ts, Dinv);
+        if (row < S.n) {
+            T* V = basis + S.row0 + (int64_t)vcol * B.ld;
+            if (DDA) update_row_df<T, NB>(row, basis + S.row0, B.ld, k, V, B.ld, Ws);
+            else update_row<T, NB>(row, basis + S.row0, B.ld, k, V, B.ld, Ps, Ts, Dinv);
+        }
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128)
+constexpr size_t kBWideSmem = (size_t)kMaxNB * kMaxNB * sizeof(float2) + (size_t)kDfWideRows * (kMaxNB + 1) * sizeof(float2);
+
+template <typename T, bool DDA>
+__global__ void __launch_bounds__(256)
 bupdate_wide_kernel(BatchDev B, T* basis, int k, int nb, int vcol, int which, int rrow, int statidx, int mode) {
-    __shared__ double Ts[kMaxNB * kMaxNB];
-    __shared__ double Dinv[kMaxNB];
+    extern __shared__ double smem[];
+    float2* Ws = reinterpret_cast<float2*>(smem);
+    float2* Xt = Ws + kMaxNB * kMaxNB;
+    double* Ts = smem;                       // FP64 path: T and 1/T_jj
+    double* Dinv = smem + kMaxNB * kMaxNB;
     int cur = -1;
     for (int t = blockIdx.x; t < B.ttot; t += gridDim.x) {
         const int s = B.tsys[t];
@@ -157,14 +170,19 @@ bupdate_wide_kernel(BatchDev B, T* basis, int k, int nb, int vcol, int which, in
         const double* R = r_block(st, which, vcol) + rrow;
         if (s != cur) {
             __syncthreads();
-            stage_t_wide(k, nb, R, kMaxCols, mode, Ts, Dinv);
+            if (DDA) stage_w_df(k, nb, R, kMaxCols, mode, Ws, kMaxNB, 4, reinterpret_cast<double*>(Xt));
+            else stage_t_wide(k, nb, R, kMaxCols, mode, Ts, Dinv);
             cur = s;
         }
-        for (int r = threadIdx.x; r < kTile; r += blockDim.x) {
-            const int64_t row = (int64_t)(t - S.t0) * kTile + r;
-            if (row < S.n)
-                update_row_wide<T>(row, basis + S.row0, B.ld, k, basis + S.row0 + (int64_t)vcol * B.ld, B.ld, nb, R,
-                                   kMaxCols, Ts, Dinv);
+        const int64_t r0 = (int64_t)(t - S.t0) * kTile;
+        T* V = basis + S.row0 + (int64_t)vcol * B.ld;
+        if (DDA) {
+            for (int q = 0; q < kTile / kDfWideRows; ++q)
+                update_tile_wide_df<T>(r0 + q * kDfWideRows, S.n, basis + S.row0, B.ld, k, V, B.ld, nb, Ws, Xt);
+        } else {
+            for (int r = threadIdx.x; r < kTile; r += blockDim.x)
+                if (r0 + r < S.n)
+                    update_row_wide<T>(r0 + r, basis + S.row0, B.ld, k, V, B.ld, nb, R, kMaxCols, Ts, Dinv);
         }
     }
 }
@@ -328,44 +346,90 @@ int cuda_rc_b(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? GMRES_ERR_OOM : GMRES_ERR_CUDA;
 }
 
-template <typename T>
-cudaError_t launch_bgram(gmres_batch* c, T* basis, int k, int nb, int vcol, int which, int rrow, int statidx,
-                         int mode) {
+template <typename T, bool DDA>
+cudaError_t launch_bgram_t(gmres_batch* c, T* basis, int k, int nb, int vcol, int which, int rrow, int statidx,
+                           int mode) {
     const BatchDev& B = c->B;
-    switch (nb) {
-#define GM_CASE(NBV)                                                                                         \
-    case NBV:                                                                                                \
-        bgram_skinny_kernel<T, NBV><<<c->grid_gram, kGramThreads, kGramSmem, c->stream>>>(B, basis, k, vcol, \
-                                                                                          which, rrow,      \
-                                                                                          statidx, mode);   \
+    if (!DDA || nb > kDfSkinnyMaxNB) {
+        if (nb <= kSkinnyMaxNB && !DDA) {
+            switch (nb) {
+#define GM_CASE(NBV)                                                                                       \
+    case NBV:                                                                                              \
+        bgram_skinny_kernel<T, NBV, false><<<c->grid_gram, kGramThreads, kGramSmem, c->stream>>>(          \
+            B, basis, k, vcol, which, rrow, statidx, mode);                                                \
         return cudaGetLastError();
+                GM_CASE(1) GM_CASE(2) GM_CASE(3) GM_CASE(4) GM_CASE(5) GM_CASE(6) GM_CASE(7) GM_CASE(8)
+                GM_CASE(9) GM_CASE(10) GM_CASE(11) GM_CASE(12)
+#undef GM_CASE
+                default: break;
+            }
+        }
+        bgram_wide_kernel<T, DDA><<<c->grid_gram, kGramThreads, kGramSmem, c->stream>>>(B, basis, k, nb, vcol, which,
+                                                                                         rrow, statidx, mode);
+        return cudaGetLastError();
+    }
+    switch (nb) {
+#define GM_CASE(NBV)                                                                                       \
+    case NBV: {                                                                                            \
+        static bool attr = false;                                                                          \
+        if (!attr) {                                                                                       \
+            cudaError_t e = cudaFuncSetAttribute(bgram_skinny_kernel<T, NBV, true>,                        \
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                                                 (int)gram_skinny_df_smem(kMaxNB + NBV));                  \
+            if (e != cudaSuccess) return e;                                                                \
+            attr = true;                                                                                   \
+        }                                                                                                  \
+        bgram_skinny_kernel<T, NBV, true><<<c->grid_gram, kGramThreads, gram_skinny_df_smem(k + NBV + NBV), \
+                                            c->stream>>>(B, basis, k, vcol, which, rrow, statidx, mode);   \
+        return cudaGetLastError();                                                                         \
+    }
         GM_CASE(1) GM_CASE(2) GM_CASE(3) GM_CASE(4) GM_CASE(5) GM_CASE(6) GM_CASE(7) GM_CASE(8)
-        GM_CASE(9) GM_CASE(10) GM_CASE(11) GM_CASE(12)
 #undef GM_CASE
         default: break;
     }
-    bgram_wide_kernel<T><<<c->grid_gram, kGramThreads, kGramSmem, c->stream>>>(B, basis, k, nb, vcol, which, rrow,
-                                                                                statidx, mode);
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>
-cudaError_t launch_bupdate(gmres_batch* c, T* basis, int k, int nb, int vcol, int which, int rrow, int statidx,
-                           int mode) {
+cudaError_t launch_bgram(gmres_batch* c, T* basis, int k, int nb, int vcol, int which, int rrow, int statidx,
+                         int mode) {
+    return c->opts.arith == GMRES_ARITH_DD ? launch_bgram_t<T, true>(c, basis, k, nb, vcol, which, rrow, statidx, mode)
+                                           : launch_bgram_t<T, false>(c, basis, k, nb, vcol, which, rrow, statidx, mode);
+}
+
+template <typename T, bool DDA>
+cudaError_t launch_bupdate_t(gmres_batch* c, T* basis, int k, int nb, int vcol, int which, int rrow, int statidx,
+                             int mode) {
     const BatchDev& B = c->B;
     switch (nb) {
-#define GM_CASE(NBV)                                                                                   \
-    case NBV:                                                                                          \
-        bupdate_skinny_kernel<T, NBV><<<c->grid_rows, kTile, 0, c->stream>>>(B, basis, k, vcol, which, \
-                                                                              rrow, statidx, mode);    \
+#define GM_CASE(NBV)                                                                                          \
+    case NBV:                                                                                                 \
+        bupdate_skinny_kernel<T, NBV, DDA><<<c->grid_rows, kTile, 0, c->stream>>>(B, basis, k, vcol, which,   \
+                                                                                   rrow, statidx, mode);      \
         return cudaGetLastError();
         GM_CASE(1) GM_CASE(2) GM_CASE(3) GM_CASE(4) GM_CASE(5) GM_CASE(6) GM_CASE(7) GM_CASE(8)
         GM_CASE(9) GM_CASE(10) GM_CASE(11) GM_CASE(12) GM_CASE(13) GM_CASE(14) GM_CASE(15) GM_CASE(16)
 #undef GM_CASE
         default: break;
     }
-    bupdate_wide_kernel<T><<<c->grid_rows, 128, 0, c->stream>>>(B, basis, k, nb, vcol, which, rrow, statidx, mode);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(bupdate_wide_kernel<T, DDA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kBWideSmem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    bupdate_wide_kernel<T, DDA><<<c->grid_rows, DDA ? 256 : 128, kBWideSmem, c->stream>>>(B, basis, k, nb, vcol, which,
+                                                                                        rrow, statidx, mode);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_bupdate(gmres_batch* c, T* basis, int k, int nb, int vcol, int which, int rrow, int statidx,
+                           int mode) {
+    return c->opts.arith == GMRES_ARITH_DD
+               ? launch_bupdate_t<T, true>(c, basis, k, nb, vcol, which, rrow, statidx, mode)
+               : launch_bupdate_t<T, false>(c, basis, k, nb, vcol, which, rrow, statidx, mode);
 }
 
 // One restart cycle for every active system (the sequence captured in the graph).
@@ -482,6 +546,7 @@ int gmres_batch_create(gmres_batch** out, int32_t nsys, const int64_t* n, const 
            "need s | panel | m, m + 1 <= 64, s <= 16");
     GM_ARG(o.precision == GMRES_PREC_FP64 || o.precision == GMRES_PREC_MIXED, "unknown precision");
     GM_ARG(o.tol > 0.0 && o.max_restarts >= 1, "bad tol / max_restarts");
+    GM_ARG(o.arith == GMRES_ARITH_FP64 || o.arith == GMRES_ARITH_DD, "unknown arith");
     gmres_batch* c = new gmres_batch();
     c->opts = o;
     c->nsys = nsys;

@@ -38,6 +38,10 @@ struct PipStatus {
 constexpr int kPipGramOnly = 1;   // Gram kernel: write [P; G] (upper G), no Cholesky, status 0
 constexpr int kPipNoTrsm = 2;     // update kernel: V <- V - Q P only (T taken as the identity)
 
+// Arithmetic of the Gram and update kernels (gmres_opts.arith).
+constexpr int kArithFP64 = 0;     // native FP64 pipe (default)
+constexpr int kArithDD = 1;       // double-float on the FP32 pipe (df.cuh), ~2^-48 relative
+
 // ---------------------------------------------------------------- launchers
 // BCGS-PIP step 1+2: [P; G] = [Q, V]^T V split over n rows; the last CTA to
 // finish reduces the partial blocks in a fixed order, forms G - P^T P, factors
@@ -46,23 +50,23 @@ cudaError_t launch_pip_gram_chol(cudaStream_t st, int64_t n,
                                  const double* Q, int64_t ldq, int k,
                                  const double* V, int64_t ldv, int nb,
                                  double* R, int ldr, const PipWork& w, int32_t* d_status,
-                                 int32_t* d_skip, int grid, int mode = 0);
+                                 int32_t* d_skip, int grid, int mode = 0, int arith = kArithFP64);
 cudaError_t launch_pip_gram_chol(cudaStream_t st, int64_t n,
                                  const float* Q, int64_t ldq, int k,
                                  const float* V, int64_t ldv, int nb,
                                  double* R, int ldr, const PipWork& w, int32_t* d_status,
-                                 int32_t* d_skip, int grid, int mode = 0);
+                                 int32_t* d_skip, int grid, int mode = 0, int arith = kArithFP64);
 // BCGS-PIP step 3: V <- (V - Q P) T^{-1}, P and T read from R.
 cudaError_t launch_pip_update(cudaStream_t st, int64_t n,
                               const double* Q, int64_t ldq, int k,
                               double* V, int64_t ldv, int nb,
                               const double* R, int ldr, const int32_t* d_status,
-                              const int32_t* d_skip, int mode = 0);
+                              const int32_t* d_skip, int mode = 0, int arith = kArithFP64);
 cudaError_t launch_pip_update(cudaStream_t st, int64_t n,
                               const float* Q, int64_t ldq, int k,
                               float* V, int64_t ldv, int nb,
                               const double* R, int ldr, const int32_t* d_status,
-                              const int32_t* d_skip, int mode = 0);
+                              const int32_t* d_skip, int mode = 0, int arith = kArithFP64);
 
 }  // namespace gm
 

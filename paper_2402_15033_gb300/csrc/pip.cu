@@ -20,6 +20,7 @@
 // These kernels run on the FP64 pipe, which on GB300 issues about 2 FMA per
 // SM per clock (1.19 TFLOP/s measured): the Gram and the update are bound by
 // FP64 arithmetic, not by HBM, at the paper's block sizes.
+#include <algorithm>
 #include "pip_body.cuh"
 
 namespace gm {
@@ -88,6 +89,72 @@ update_wide_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, int k,
         update_row_wide<T>(row, Q, ldq, k, V, ldv, nb, R, ldr, Ts, Dinv);
 }
 
+// ---------------------------------------------------------------- double-float kernels
+template <typename T, int NB>
+__global__ void __launch_bounds__(kGramThreads)
+gram_skinny_df_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, int k,
+                      const T* __restrict__ V, int64_t ldv, double* __restrict__ R, int ldr,
+                      double* partial, unsigned* counter, double* gram, int32_t* d_status,
+                      int32_t* d_skip, int mode) {
+    extern __shared__ double smem[];
+    if (d_skip && *d_skip) return;
+    const int g = blockIdx.y, G = gridDim.x;
+    const size_t ps = (size_t)kMaxNB * NB;
+    double* partial0 = partial + (size_t)g * G * ps;
+    gram_skinny_part_df<T, NB>(n, Q, ldq, k, V, ldv, g, blockIdx.x, G, partial0 + blockIdx.x * ps, smem);
+    pip_finish(k, NB, g, gridDim.y, G, R, ldr, partial0, ps, counter, gram, d_status, d_skip, smem, mode);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGramThreads)
+gram_wide_df_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, int k,
+                    const T* __restrict__ V, int64_t ldv, int nb, double* __restrict__ R, int ldr,
+                    double* partial, unsigned* counter, double* gram, int32_t* d_status,
+                    int32_t* d_skip, int mode) {
+    extern __shared__ double smem[];
+    if (d_skip && *d_skip) return;
+    const int g = blockIdx.y, G = gridDim.x;
+    const size_t ps = (size_t)kMaxNB * nb;
+    double* partial0 = partial + (size_t)g * G * ps;
+    gram_wide_part_df<T>(n, Q, ldq, k, V, ldv, nb, g, blockIdx.x, G, partial0 + blockIdx.x * ps, smem);
+    pip_finish(k, nb, g, gridDim.y, G, R, ldr, partial0, ps, counter, gram, d_status, d_skip, smem, mode);
+}
+
+// Double-float update, nb <= 16: W = [-P T^{-1}; T^{-1}] staged pre-split, one thread per row.
+template <typename T, int NB>
+__global__ void __launch_bounds__(256)
+update_skinny_df_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, int k,
+                        T* __restrict__ V, int64_t ldv, const double* __restrict__ R, int ldr,
+                        const int32_t* d_status, const int32_t* d_skip, int mode) {
+    extern __shared__ double smem[];
+    if ((d_skip && *d_skip) || *d_status) return;
+    double* Tinv = smem;                                          // [NB][NB]
+    float2* Ws = reinterpret_cast<float2*>(smem + NB * NB);       // [(k+NB)][NB]
+    stage_w_df(k, NB, R, ldr, mode, Ws, NB, 1, Tinv);
+    for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n;
+         row += (int64_t)gridDim.x * blockDim.x)
+        update_row_df<T, NB>(row, Q, ldq, k, V, ldv, Ws);
+}
+
+constexpr size_t kWideDfSmem = (size_t)kMaxNB * kMaxNB * sizeof(float2) +            // W
+                               (size_t)kDfWideRows * (kMaxNB + 1) * sizeof(float2);  // row tile (and T^{-1})
+
+// Double-float update, 16 < nb and k + nb <= 64: 64-row tiles, 4 output groups.
+template <typename T>
+__global__ void __launch_bounds__(256)
+update_wide_df_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, int k,
+                      T* __restrict__ V, int64_t ldv, int nb, const double* __restrict__ R, int ldr,
+                      const int32_t* d_status, const int32_t* d_skip, int mode) {
+    extern __shared__ double smem[];
+    if ((d_skip && *d_skip) || *d_status) return;
+    float2* Ws = reinterpret_cast<float2*>(smem);
+    float2* Xt = Ws + kMaxNB * kMaxNB;
+    stage_w_df(k, nb, R, ldr, mode, Ws, kMaxNB, 4, reinterpret_cast<double*>(Xt));
+    const int64_t ntiles = (n + kDfWideRows - 1) / kDfWideRows;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
+        update_tile_wide_df<T>(t * kDfWideRows, n, Q, ldq, k, V, ldv, nb, Ws, Xt);
+}
+
 template <typename T, int NB>
 cudaError_t launch_skinny(cudaStream_t st, int64_t n, const T* Q, int64_t ldq, int k,
                           const T* V, int64_t ldv, double* R, int ldr, const PipWork& w,
@@ -110,12 +177,60 @@ cudaError_t launch_update_skinny(cudaStream_t st, int64_t n, const T* Q, int64_t
     return cudaGetLastError();
 }
 
+template <typename T, int NB>
+cudaError_t launch_skinny_df(cudaStream_t st, int64_t n, const T* Q, int64_t ldq, int k,
+                             const T* V, int64_t ldv, double* R, int ldr, const PipWork& w,
+                             int32_t* d_status, int32_t* d_skip, int grid, int mode) {
+    const int kx = k + NB;
+    const dim3 g(grid, (kx + kMaxNB - 1) / kMaxNB);
+    const size_t sm = gram_skinny_df_smem(std::min(kx, kMaxNB) + NB);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(gram_skinny_df_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)gram_skinny_df_smem(kMaxNB + NB));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    gram_skinny_df_kernel<T, NB><<<g, kGramThreads, sm, st>>>(n, Q, ldq, k, V, ldv, R, ldr, w.partial,
+                                                              w.counter, w.gram, d_status, d_skip, mode);
+    return cudaGetLastError();
+}
+
+template <typename T, int NB>
+cudaError_t launch_update_skinny_df(cudaStream_t st, int64_t n, const T* Q, int64_t ldq, int k,
+                                    T* V, int64_t ldv, const double* R, int ldr,
+                                    const int32_t* d_status, const int32_t* d_skip, int mode) {
+    const size_t sm = (size_t)NB * NB * sizeof(double) + (size_t)(k + NB) * NB * sizeof(float2);
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(update_skinny_df_kernel<T, NB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t blocks = (n + 255) / 256;
+    const int grid = (int)(blocks < 8 * (int64_t)num_sms() ? blocks : 8 * (int64_t)num_sms());
+    update_skinny_df_kernel<T, NB><<<grid, 256, sm, st>>>(n, Q, ldq, k, V, ldv, R, ldr, d_status, d_skip, mode);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 template <typename T>
 cudaError_t pip_gram_chol_t(cudaStream_t st, int64_t n, const T* Q, int64_t ldq, int k,
                             const T* V, int64_t ldv, int nb, double* R, int ldr,
-                            const PipWork& w, int32_t* d_status, int32_t* d_skip, int grid, int mode) {
+                            const PipWork& w, int32_t* d_status, int32_t* d_skip, int grid, int mode,
+                            int arith) {
+    if (arith == kArithDD) {
+        switch (nb) {
+#define GM_CASE(NBV) case NBV: return launch_skinny_df<T, NBV>(st, n, Q, ldq, k, V, ldv, R, ldr, w, d_status, d_skip, grid, mode);
+            GM_CASE(1) GM_CASE(2) GM_CASE(3) GM_CASE(4) GM_CASE(5) GM_CASE(6) GM_CASE(7) GM_CASE(8)
+#undef GM_CASE
+            default: break;
+        }
+        const dim3 g(grid, (k + nb + kMaxNB - 1) / kMaxNB);
+        gram_wide_df_kernel<T><<<g, kGramThreads, kGramSmem, st>>>(n, Q, ldq, k, V, ldv, nb, R, ldr, w.partial,
+                                                                   w.counter, w.gram, d_status, d_skip, mode);
+        return cudaGetLastError();
+    }
     switch (nb) {
 #define GM_CASE(NBV) case NBV: return launch_skinny<T, NBV>(st, n, Q, ldq, k, V, ldv, R, ldr, w, d_status, d_skip, grid, mode);
         GM_CASE(1) GM_CASE(2) GM_CASE(3) GM_CASE(4) GM_CASE(5) GM_CASE(6) GM_CASE(7) GM_CASE(8)
@@ -133,7 +248,32 @@ cudaError_t pip_gram_chol_t(cudaStream_t st, int64_t n, const T* Q, int64_t ldq,
 template <typename T>
 cudaError_t pip_update_t(cudaStream_t st, int64_t n, const T* Q, int64_t ldq, int k,
                          T* V, int64_t ldv, int nb, const double* R, int ldr,
-                         const int32_t* d_status, const int32_t* d_skip, int mode) {
+                         const int32_t* d_status, const int32_t* d_skip, int mode, int arith) {
+    if (arith == kArithDD) {
+        switch (nb) {
+#define GM_CASE(NBV) case NBV: return launch_update_skinny_df<T, NBV>(st, n, Q, ldq, k, V, ldv, R, ldr, d_status, d_skip, mode);
+            GM_CASE(1) GM_CASE(2) GM_CASE(3) GM_CASE(4) GM_CASE(5) GM_CASE(6) GM_CASE(7) GM_CASE(8)
+            GM_CASE(9) GM_CASE(10) GM_CASE(11) GM_CASE(12) GM_CASE(13) GM_CASE(14) GM_CASE(15) GM_CASE(16)
+#undef GM_CASE
+            default: break;
+        }
+        if (k + nb <= kMaxNB) {
+            static bool attr_set[2] = {false, false};
+            bool& done = attr_set[sizeof(T) == sizeof(float)];
+            if (!done) {
+                cudaError_t e = cudaFuncSetAttribute(update_wide_df_kernel<T>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWideDfSmem);
+                if (e != cudaSuccess) return e;
+                done = true;
+            }
+            const int64_t tiles = (n + kDfWideRows - 1) / kDfWideRows;
+            const int grid = (int)(tiles < 4 * (int64_t)num_sms() ? tiles : 4 * (int64_t)num_sms());
+            update_wide_df_kernel<T><<<grid, 256, kWideDfSmem, st>>>(n, Q, ldq, k, V, ldv, nb, R, ldr, d_status,
+                                                                      d_skip, mode);
+            return cudaGetLastError();
+        }
+        // wider than one 64-column tile: the FP64-pipe kernel below
+    }
     switch (nb) {
 #define GM_CASE(NBV) case NBV: return launch_update_skinny<T, NBV>(st, n, Q, ldq, k, V, ldv, R, ldr, d_status, d_skip, mode);
         GM_CASE(1) GM_CASE(2) GM_CASE(3) GM_CASE(4) GM_CASE(5) GM_CASE(6) GM_CASE(7) GM_CASE(8)
@@ -149,23 +289,25 @@ cudaError_t pip_update_t(cudaStream_t st, int64_t n, const T* Q, int64_t ldq, in
 
 cudaError_t launch_pip_gram_chol(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k,
                                  const double* V, int64_t ldv, int nb, double* R, int ldr,
-                                 const PipWork& w, int32_t* d_status, int32_t* d_skip, int grid, int mode) {
-    return pip_gram_chol_t<double>(st, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode);
+                                 const PipWork& w, int32_t* d_status, int32_t* d_skip, int grid, int mode,
+                                 int arith) {
+    return pip_gram_chol_t<double>(st, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode, arith);
 }
 cudaError_t launch_pip_gram_chol(cudaStream_t st, int64_t n, const float* Q, int64_t ldq, int k,
                                  const float* V, int64_t ldv, int nb, double* R, int ldr,
-                                 const PipWork& w, int32_t* d_status, int32_t* d_skip, int grid, int mode) {
-    return pip_gram_chol_t<float>(st, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode);
+                                 const PipWork& w, int32_t* d_status, int32_t* d_skip, int grid, int mode,
+                                 int arith) {
+    return pip_gram_chol_t<float>(st, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode, arith);
 }
 cudaError_t launch_pip_update(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k,
                               double* V, int64_t ldv, int nb, const double* R, int ldr,
-                              const int32_t* d_status, const int32_t* d_skip, int mode) {
-    return pip_update_t<double>(st, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, d_skip, mode);
+                              const int32_t* d_status, const int32_t* d_skip, int mode, int arith) {
+    return pip_update_t<double>(st, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, d_skip, mode, arith);
 }
 cudaError_t launch_pip_update(cudaStream_t st, int64_t n, const float* Q, int64_t ldq, int k,
                               float* V, int64_t ldv, int nb, const double* R, int ldr,
-                              const int32_t* d_status, const int32_t* d_skip, int mode) {
-    return pip_update_t<float>(st, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, d_skip, mode);
+                              const int32_t* d_status, const int32_t* d_skip, int mode, int arith) {
+    return pip_update_t<float>(st, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, d_skip, mode, arith);
 }
 
 PipWork pip_work_layout(void* base, int64_t n, int k, int nb) {

@@ -166,6 +166,7 @@ static int check_opts(const gmres_opts* o) {
     const int panel = o->ortho == GMRES_ORTHO_BCGS_PIP2 ? o->s : o->panel;
     GM_ARG(panel >= o->s && panel % o->s == 0 && o->m % panel == 0, "need s | panel | m");
     GM_ARG(o->sigma >= 0.0 && std::isfinite(o->sigma), "sigma must be >= 0");
+    GM_ARG(o->arith == GMRES_ARITH_DD || o->arith == GMRES_ARITH_FP64, "unknown arith");
     return GMRES_OK;
 }
 
@@ -371,25 +372,27 @@ static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
             if (sizeof(T) == sizeof(double)) {
                 // BCGS-PIP (Fig. 4a): one reduction, Pythagorean Gram
                 e = launch_pip_gram_chol(s, c->n, basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, w, stat, done,
-                                         reduction_grid(c->n));
+                                         reduction_grid(c->n), 0, o.arith);
                 if (e == cudaSuccess)
-                    e = launch_pip_update(s, c->n, basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, stat, done);
+                    e = launch_pip_update(s, c->n, basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, stat, done, 0,
+                                          o.arith);
             } else {
                 // FP32 basis: project, then CholQR of the projected block with an
                 // explicit FP64 Gram (the Pythagorean identity needs an
                 // orthonormal stored basis, which FP32 storage is only to ~1e-7)
                 e = launch_pip_gram_chol(s, c->n, basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, w, stat, done,
-                                         reduction_grid(c->n), kPipGramOnly);
+                                         reduction_grid(c->n), kPipGramOnly, o.arith);
                 if (e == cudaSuccess)
                     e = launch_pip_update(s, c->n, basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, stat, done,
-                                          kPipNoTrsm);
+                                          kPipNoTrsm, o.arith);
                 if (e == cudaSuccess) {
                     PipWork w0 = pip_work_layout(c->pip_work, c->n, 0, o.s);
                     e = launch_pip_gram_chol(s, c->n, basis, c->ldq, 0, V, c->ldq, o.s, R + k, kMaxCols, w0, stat,
-                                             done, reduction_grid(c->n));
+                                             done, reduction_grid(c->n), 0, o.arith);
                 }
                 if (e == cudaSuccess)
-                    e = launch_pip_update(s, c->n, basis, c->ldq, 0, V, c->ldq, o.s, R + k, kMaxCols, stat, done);
+                    e = launch_pip_update(s, c->n, basis, c->ldq, 0, V, c->ldq, o.s, R + k, kMaxCols, stat, done, 0,
+                                          o.arith);
             }
         }
         if (e == cudaSuccess) e = mark(PH_S1);
@@ -404,9 +407,10 @@ static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
             int32_t* stat = &ds->blkstat[nblk + panel_idx];
             if (e == cudaSuccess)
                 e = launch_pip_gram_chol(s, c->n, basis, c->ldq, lo, V, c->ldq, np, R, kMaxCols, w, stat, done,
-                                         reduction_grid(c->n));
+                                         reduction_grid(c->n), 0, o.arith);
             if (e == cudaSuccess)
-                e = launch_pip_update(s, c->n, basis, c->ldq, lo, V, c->ldq, np, R, kMaxCols, stat, done);
+                e = launch_pip_update(s, c->n, basis, c->ldq, lo, V, c->ldq, np, R, kMaxCols, stat, done, 0,
+                                      o.arith);
             if (e == cudaSuccess) e = mark(PH_S2);
             if (e == cudaSuccess) e = mark(PH_LS);
             if (e == cudaSuccess) e = launch_hessenberg_ls(s, ds, lo, t);
@@ -630,9 +634,9 @@ static int ortho_pip(void* stream, int64_t n, const T* Q, int64_t ldq, int32_t k
 
 extern "C" {
 
-int ortho_gram_chol(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, const double* V,
+static int gram_chol_impl(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, const double* V,
                     int64_t ldv, int32_t nb, double* R, int32_t ldr, void* d_work, size_t work_bytes,
-                    int32_t* d_status) {
+                    int32_t* d_status, int arith) {
     clear_error();
     int code = GMRES_OK;
     if (check_pip_args(n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status, &code)) return code;
@@ -641,12 +645,25 @@ int ortho_gram_chol(void* stream, int64_t n, const double* Q, int64_t ldq, int32
     cudaError_t e = cudaMemsetAsync(w.counter, 0, 256, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(int32_t), s);
     if (e == cudaSuccess)
-        e = launch_pip_gram_chol(s, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, nullptr, reduction_grid(n));
+        e = launch_pip_gram_chol(s, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, nullptr, reduction_grid(n), 0,
+                                 arith);
     return cuda_rc(e, "gram launch");
 }
 
-int ortho_update(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,
-                 int32_t nb, const double* R, int32_t ldr, const int32_t* d_status) {
+int ortho_gram_chol(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, const double* V,
+                    int64_t ldv, int32_t nb, double* R, int32_t ldr, void* d_work, size_t work_bytes,
+                    int32_t* d_status) {
+    return gram_chol_impl(stream, n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status, kArithFP64);
+}
+
+int ortho_gram_chol_dd(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, const double* V,
+                       int64_t ldv, int32_t nb, double* R, int32_t ldr, void* d_work, size_t work_bytes,
+                       int32_t* d_status) {
+    return gram_chol_impl(stream, n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status, kArithDD);
+}
+
+static int update_impl(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,
+                 int32_t nb, const double* R, int32_t ldr, const int32_t* d_status, int arith) {
     clear_error();
     int code = GMRES_OK;
     // workspace is not used by the update: pass a dummy that satisfies the checks
@@ -658,8 +675,18 @@ int ortho_update(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t 
     GM_ARG(d_status != nullptr, "d_status is NULL");
     (void)code;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_pip_update(s, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, nullptr);
+    cudaError_t e = launch_pip_update(s, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, nullptr, 0, arith);
     return cuda_rc(e, "update launch");
+}
+
+int ortho_update(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,
+                 int32_t nb, const double* R, int32_t ldr, const int32_t* d_status) {
+    return update_impl(stream, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, kArithFP64);
+}
+
+int ortho_update_dd(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,
+                    int32_t nb, const double* R, int32_t ldr, const int32_t* d_status) {
+    return update_impl(stream, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, kArithDD);
 }
 
 int ortho_stage1(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,
