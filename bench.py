@@ -64,6 +64,64 @@ def bytes_update(n, k, nb):
     return 8.0 * n * (k + 2 * nb)
 
 
+def tc_tile_count(k, nb):
+    """16 x 8 output tiles of the tensor-core Gram (those not strictly below the G diagonal)."""
+    return sum(1 for mt in range((k + nb + 15) // 16) for nt in range((nb + 7) // 8)
+               if not (16 * mt - k > 8 * nt + 7))
+
+
+def tc_mma_flops(n, k, nb):
+    """bf16 tensor FLOPs the exact-slice Gram executes: per 128-row chunk and
+    tile, 8 k-steps x 28 digit-pair MMAs of 16 x 8 x 16; k + nb > 64 runs FP64."""
+    if k + nb > 64:
+        return 0.0
+    return math.ceil(n / 128) * tc_tile_count(k, nb) * 8 * 28 * 2 * 16 * 8 * 16
+
+
+def tc_update_mma_flops(n, k, nb):
+    """bf16 tensor FLOPs the exact-slice update executes: per 32-row chunk, 2 M-tiles
+    per N-tile of 8 columns, K steps up to the last nonzero row of the triangular
+    W, 28 digit-pair MMAs of 16 x 8 x 16 each."""
+    kx = k + nb
+    if kx > 64:
+        return 0.0
+    nks = (kx + 15) // 16
+    steps = sum(min(nks, (k + 8 * nt + 7) // 16 + 1) for nt in range((nb + 7) // 8))
+    return math.ceil(n / 32) * 2 * steps * 28 * 2 * 16 * 8 * 16
+
+
+ARITH_TEXT = {"fp64": "FP64 pipe (native FP64 FMA)",
+              "tc": "Gram and update on bf16 tensor cores by exact 8-bit slicing (FP64 quality)",
+              "dd": "double-float (hi+lo FP32), ~2^-48 relative, FP64 in/out"}
+
+FP64_PEAK_TFLOPS = 152 * 2070e6 * 2 * 2 / 1e12   # 2 FP64 FMA/clk/SM x 152 SMs x max clock
+
+
+def roofline_of(d, kernel, arith):
+    """Roofline object of one kernel family: FP64-pipe bound for FP64 kernels,
+    HBM-bound figure for the tensor-core Gram (its algorithmic bytes over the
+    measured copy bandwidth), with the other bound attached."""
+    peaks, src = load_peaks()
+    t = d["ms_total"] * 1e-3
+    gbs = d["bytes"] / t / 1e9
+    tfl = d["flops"] / t / 1e12
+    hbm = {"achieved_gbs": round(gbs, 1), "peak_gbs": peaks["hbm_gbs"], "frac": round(gbs / peaks["hbm_gbs"], 4),
+           "peak_source": src}
+    if arith == "tc" and d.get("tensor_flops"):
+        tt = d["tensor_flops"] / t / 1e12
+        return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(gbs / peaks["hbm_gbs"], 4), "traffic": None, "kernel": kernel, "peak_source": src,
+                "tensor": {"executed_tflops": round(tt, 2), "mma_sync_bf16_peak_tflops": MMA_SYNC_PEAK,
+                           "frac": round(tt / MMA_SYNC_PEAK, 4),
+                           "peak_source": "measured mma.sync m16n8k16 bf16 throughput on this GPU"}}
+    return {"bound": "alu", "achieved": round(tfl, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+            "frac": round(tfl / FP64_PEAK_TFLOPS, 4), "traffic": None, "kernel": kernel,
+            "peak_source": "FP64 FMA pipe: 2/clk/SM x 152 SMs x 2070 MHz", "hbm": hbm}
+
+
+MMA_SYNC_PEAK = 604.0
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -207,34 +265,65 @@ def run_ours(args):
     st = torch.zeros(NBLK + 1, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
 
-    kinds = {"stage1_gram": [], "stage1_update": [], "stage2_gram": [], "stage2_update": []}
+    grams = {"fp64": capi.ortho_gram_chol, "dd": capi.ortho_gram_chol_dd, "tc": capi.ortho_gram_chol_tc}
 
-    def step(evs=None):
-        for j, k in enumerate(K_BLOCKS):
-            Q = B[:, :k]
-            V = B[:, k:k + S]
-            Rb = Rh[:k + S, k:k + S]
-            if evs is not None:
-                e0 = torch.cuda.Event(enable_timing=True); e0.record()
-            capi.ortho_gram_chol(Q, V, Rb, work, st[j:j + 1], k=k, stream=stream)
-            if evs is not None:
-                e1 = torch.cuda.Event(enable_timing=True); e1.record()
-            capi.ortho_update(Q, V, Rb, st[j:j + 1], k=k, stream=stream)
-            if evs is not None:
-                e2 = torch.cuda.Event(enable_timing=True); e2.record()
-                evs.append(("stage1_gram", k, S, e0, e1))
-                evs.append(("stage1_update", k, S, e1, e2))
-        if evs is not None:
-            e0 = torch.cuda.Event(enable_timing=True); e0.record()
-        capi.ortho_gram_chol(None, B, R2, work, st[NBLK:], k=0, stream=stream)
-        if evs is not None:
-            e1 = torch.cuda.Event(enable_timing=True); e1.record()
-        capi.ortho_update(None, B, R2, st[NBLK:], k=0, stream=stream)
-        if evs is not None:
-            e2 = torch.cuda.Event(enable_timing=True); e2.record()
-            evs.append(("stage2_gram", 0, NCOL, e0, e1))
-            evs.append(("stage2_update", 0, NCOL, e1, e2))
+    def make_step(arith):
+        gram = grams[arith]
+        dd = arith == "dd"
+        tc = arith == "tc"
 
+        def step(evs=None):
+            def mark():
+                if evs is None:
+                    return None
+                e = torch.cuda.Event(enable_timing=True)
+                e.record()
+                return e
+            for j, k in enumerate(K_BLOCKS):
+                Q = B[:, :k]
+                V = B[:, k:k + S]
+                Rb = Rh[:k + S, k:k + S]
+                e0 = mark()
+                gram(Q, V, Rb, work, st[j:j + 1], k=k, stream=stream)
+                e1 = mark()
+                capi.ortho_update(Q, V, Rb, st[j:j + 1], k=k, stream=stream, dd=dd, tc=tc)
+                e2 = mark()
+                if evs is not None:
+                    evs.append(("stage1_gram", k, S, e0, e1))
+                    evs.append(("stage1_update", k, S, e1, e2))
+            e0 = mark()
+            gram(None, B, R2, work, st[NBLK:], k=0, stream=stream)
+            e1 = mark()
+            capi.ortho_update(None, B, R2, st[NBLK:], k=0, stream=stream, dd=dd, tc=tc)
+            e2 = mark()
+            if evs is not None:
+                evs.append(("stage2_gram", 0, NCOL, e0, e1))
+                evs.append(("stage2_update", 0, NCOL, e1, e2))
+        return step
+
+    def families_of(evs, arith, steps):
+        kinds = {"stage1_gram": [], "stage1_update": [], "stage2_gram": [], "stage2_update": []}
+        for kind, k, nb, a, b in evs:
+            kinds[kind].append((k, nb, a.elapsed_time(b)))
+        fam = {}
+        for kind, lst in kinds.items():
+            tot = sum(x[2] for x in lst)
+            gram = "gram" in kind
+            fl = sum((flops_gram if gram else flops_update)(n, k, nb) for k, nb, _ in lst)
+            by = sum((bytes_gram if gram else bytes_update)(n, k, nb) for k, nb, _ in lst)
+            tfl = (sum((tc_mma_flops if gram else tc_update_mma_flops)(n, k, nb) for k, nb, _ in lst)
+                   if arith == "tc" else 0.0)
+            fam[kind] = {"ms_total": tot, "launches": len(lst), "flops": fl, "bytes": by, "tensor_flops": tfl}
+        out = {}
+        for kk, v in fam.items():
+            out[kk] = {"ms_per_step": round(v["ms_total"] / steps, 4), "launches_per_step": v["launches"] // steps,
+                       "gbs": round(v["bytes"] / (v["ms_total"] * 1e-3) / 1e9, 1),
+                       "tflops": round(v["flops"] / (v["ms_total"] * 1e-3) / 1e12, 4)}
+            if v["tensor_flops"]:
+                out[kk]["tensor_tflops_executed"] = round(v["tensor_flops"] / (v["ms_total"] * 1e-3) / 1e12, 2)
+        return fam, out
+
+    step = make_step(args.arith)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -264,67 +353,48 @@ def run_ours(args):
         t = torch.tensor([total_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    for kind, k, nb, a, b in evs:
-        kinds[kind].append((k, nb, a.elapsed_time(b)))
     ms_per_step = total_ms / args.steps
     bytes_step = BYTES_PER_ROW * n
     value = bytes_step / (ms_per_step * 1e-3) / 1e9 * world
 
     # per-kernel-family time; the dominant one carries the roofline
-    fam = {}
-    for kind, lst in kinds.items():
-        tot = sum(x[2] for x in lst)
-        fl = sum((flops_gram if "gram" in kind else flops_update)(n, k, nb) for k, nb, _ in lst)
-        by = sum((bytes_gram if "gram" in kind else bytes_update)(n, k, nb) for k, nb, _ in lst)
-        fam[kind] = {"ms_total": tot, "launches": len(lst), "flops": fl, "bytes": by}
+    fam, families = families_of(evs, args.arith, args.steps)
     dom = max(fam, key=lambda k: fam[k]["ms_total"])
-    d = fam[dom]
-    peaks, src = load_peaks()
-    fp64_peak_tflops = 152 * 2070e6 * 2 * 2 / 1e12   # see the design doc: 2 FP64 FMA/clk/SM x max clock
-    achieved_tflops = d["flops"] / (d["ms_total"] * 1e-3) / 1e12
-    achieved_gbs = d["bytes"] / (d["ms_total"] * 1e-3) / 1e9
-    roofline = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(fp64_peak_tflops, 4),
-                "unit": "TFLOP/s", "frac": round(achieved_tflops / fp64_peak_tflops, 4),
-                "traffic": None, "kernel": dom, "peak_source": "FP64 FMA pipe: 2/clk/SM x 152 SMs x 2070 MHz",
-                "hbm": {"achieved_gbs": round(achieved_gbs, 1), "peak_gbs": peaks["hbm_gbs"],
-                        "frac": round(achieved_gbs / peaks["hbm_gbs"], 4), "peak_source": src}}
-    families = {k: {"ms_per_step": round(v["ms_total"] / args.steps, 4), "launches_per_step": v["launches"] // args.steps,
-                    "gbs": round(v["bytes"] / (v["ms_total"] * 1e-3) / 1e9, 1),
-                    "tflops": round(v["flops"] / (v["ms_total"] * 1e-3) / 1e12, 4)} for k, v in fam.items()}
+    roofline = roofline_of(fam[dom], dom, args.arith)
 
-    # ---- the same step with the opt-in double-float arithmetic (GMRES_ARITH_DD):
-    # 48-bit products and sums on the FP32 pipe; reported beside, not as, the
-    # FP64 headline
-    arith_dd = None
-    if not args.no_dd:
-        def step_dd():
-            for j, k in enumerate(K_BLOCKS):
-                Q = B[:, :k]
-                V = B[:, k:k + S]
-                Rb = Rh[:k + S, k:k + S]
-                capi.ortho_gram_chol_dd(Q, V, Rb, work, st[j:j + 1], k=k, stream=stream)
-                capi.ortho_update(Q, V, Rb, st[j:j + 1], k=k, stream=stream, dd=True)
-            capi.ortho_gram_chol_dd(None, B, R2, work, st[NBLK:], k=0, stream=stream)
-            capi.ortho_update(None, B, R2, st[NBLK:], k=0, stream=stream, dd=True)
-        R2_64 = R2.clone()
+    # ---- the same step in the other arithmetics, reported beside the headline
+    others = {}
+    R2_main = R2.clone()
+    for ar in ("fp64", "tc", "dd"):
+        if ar == args.arith or (ar == "dd" and args.no_dd) or (ar == "tc" and args.no_tc):
+            continue
+        st_o = make_step(ar)
         for _ in range(2):
-            step_dd()
+            st_o()
         torch.cuda.synchronize()
+        ev_o = []
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record()
         for _ in range(args.steps):
-            step_dd()
+            st_o(ev_o)
         b.record()
         torch.cuda.synchronize()
+        if int(st.abs().sum().item()) != 0:
+            raise RuntimeError(f"Cholesky breakdown in the benchmark input ({ar})")
         dms = a.elapsed_time(b) / args.steps
-        arith_dd = {"value": round(bytes_step / (dms * 1e-3) / 1e9, 3), "unit": "GB/s", "ms_per_step": round(dms, 3),
-                    "arithmetic": "double-float (hi+lo FP32), ~2^-48 relative, FP64 in/out",
-                    "max_abs_R_diff_vs_fp64": float((R2 - R2_64).abs().max().item())}
+        fam_o, families_o = families_of(ev_o, ar, args.steps)
+        dom_o = max(fam_o, key=lambda k: fam_o[k]["ms_total"])
+        others[ar] = {"value": round(bytes_step / (dms * 1e-3) / 1e9, 3), "unit": "GB/s",
+                      "ms_per_step": round(dms, 3), "arithmetic": ARITH_TEXT[ar], "kernels": families_o,
+                      "roofline": roofline_of(fam_o[dom_o], dom_o, ar),
+                      "max_abs_R_diff_vs_headline": float((R2 - R2_main).abs().max().item())}
+    # leave the basis as the headline arithmetic produced it (e2e below re-copies it anyway)
 
     # ---- end to end: pinned host basis in, Q and R out, every step
     e2e = None
     if not args.no_e2e:
+        step = make_step(args.arith)
         hostin = torch.from_numpy(host.T.copy()).pin_memory()
         hostin[0] /= torch.linalg.norm(hostin[0])
         hostq = torch.empty_like(hostin).pin_memory()
@@ -373,7 +443,8 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "n": n, "cols": NCOL, "s": S, "panel": NCOL - 1,
                            "bytes_per_step": bytes_step, "l2": "basis 2 GB >> 129 MB L2, no flush needed",
                            "parallelism": "replicas" if world > 1 else "single"},
-                "roofline": roofline, "kernels": families, "arith_dd": arith_dd, "e2e": e2e, "cpu_baseline": cpu,
+                "arith": ARITH_TEXT[args.arith], "roofline": roofline, "kernels": families,
+                "other_arith": others, "e2e": e2e, "cpu_baseline": cpu,
                 "gpu_launches": (2 * NBLK + 2) * args.steps, "clocks": clk, "solver": solve,
                 "patterns": patterns}
         print(json.dumps(line))
@@ -606,6 +677,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-patterns", action="store_true", help="skip the mixed, batched and serving configurations")
     ap.add_argument("--no-dd", action="store_true", help="skip the double-float measurement")
+    ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core Gram measurement")
+    ap.add_argument("--arith", default="fp64", choices=["fp64", "tc", "dd"],
+                    help="arithmetic of the headline step (the others are reported beside it)")
     ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--batch-nmax", type=float, default=5e5)
     ap.add_argument("--serve-requests", type=int, default=24)

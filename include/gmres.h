@@ -54,6 +54,14 @@ extern "C" {
                                       /* Pythagorean step (Eq. 5) breaks down sooner on marginal     */
                                       /* blocks; values must keep |x y| and partial sums inside the  */
                                       /* FP32 exponent range (|x| in [2^-50, 2^50] for unit-scale n) */
+#define GMRES_ARITH_TC             2  /* opt-in: Gram reductions on the bf16 tensor cores by exact    */
+                                      /* integer slicing (Ozaki et al.): seven 8-bit digits per      */
+                                      /* value against a per-chunk column exponent, digit products    */
+                                      /* summed exactly in FP32, combined in 64-bit integers; FP64    */
+                                      /* in/out, error normwise at the level of FP64 dot products.     */
+                                      /* Both the Gram and the block update; blocks with k + nb > 64   */
+                                      /* and FP32 bases use the FP64 kernels.  Single-system solver    */
+                                      /* and the ortho calls only (the batched engine rejects it).     */
 
 typedef struct gmres_opts {
     int32_t m;             /* restart length: m+1 basis vectors per cycle (Table 1)            */
@@ -212,6 +220,17 @@ int ortho_gram_chol_dd(void* stream, int64_t n, const double* Q, int64_t ldq, in
                        void* d_work, size_t work_bytes, int32_t* d_status);
 
 int ortho_update_dd(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
+                    double* V, int64_t ldv, int32_t nb, const double* R, int32_t ldr,
+                    const int32_t* d_status);
+
+/* The same two halves on the bf16 tensor cores by exact slicing
+ * (GMRES_ARITH_TC), for k + nb <= 64 (larger blocks run the FP64 kernels).
+ * The update forms W = [-P T^{-1}; T^{-1}] and computes [Q, V] W. */
+int ortho_gram_chol_tc(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
+                       const double* V, int64_t ldv, int32_t nb, double* R, int32_t ldr,
+                       void* d_work, size_t work_bytes, int32_t* d_status);
+
+int ortho_update_tc(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
                     double* V, int64_t ldv, int32_t nb, const double* R, int32_t ldr,
                     const int32_t* d_status);
 

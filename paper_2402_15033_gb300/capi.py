@@ -32,6 +32,7 @@ GMRES_BASIS_MONOMIAL = 0
 GMRES_BASIS_NEWTON = 1
 GMRES_ARITH_FP64 = 0
 GMRES_ARITH_DD = 1
+GMRES_ARITH_TC = 2
 
 
 class gmres_opts(C.Structure):
@@ -80,6 +81,8 @@ SIGNATURES = {
     "ortho_gram_chol": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "ortho_update": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp]),
     "ortho_gram_chol_dd": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
+    "ortho_gram_chol_tc": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
+    "ortho_update_tc": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp]),
     "ortho_update_dd": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp]),
     "ortho_stage1_f32": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "ortho_stage2_f32": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
@@ -347,13 +350,20 @@ def ortho_gram_chol_dd(Q, V, R, work, status, k=None, stream=None):
     return check(_ortho(load().ortho_gram_chol_dd, Q, V, R, work, status, k, stream))
 
 
-def ortho_update(Q, V, R, status, k=None, stream=None, dd=False):
-    """Second half of BCGS-PIP: V <- (V - Q P) T^{-1} (dd: double-float arithmetic)."""
+def ortho_gram_chol_tc(Q, V, R, work, status, k=None, stream=None):
+    """ortho_gram_chol with the Gram on the tensor cores by exact slicing (k + nb <= 64)."""
+    k = (Q.shape[1] if Q is not None else 0) if k is None else k
+    return check(_ortho(load().ortho_gram_chol_tc, Q, V, R, work, status, k, stream))
+
+
+def ortho_update(Q, V, R, status, k=None, stream=None, dd=False, tc=False):
+    """Second half of BCGS-PIP: V <- (V - Q P) T^{-1} (dd: double-float arithmetic;
+    tc: tensor cores by exact slicing)."""
     k = (Q.shape[1] if Q is not None else 0) if k is None else k
     n, nb = V.shape
     ldq = Q.stride(1) if (Q is not None and k > 0) else n
     qp = C.c_void_p(Q.data_ptr()) if (Q is not None and k > 0) else None
-    fn = load().ortho_update_dd if dd else load().ortho_update
+    fn = load().ortho_update_dd if dd else (load().ortho_update_tc if tc else load().ortho_update)
     return check(fn(C.c_void_p(stream or 0), int(n), qp, int(ldq), int(k),
                                      C.c_void_p(V.data_ptr()), int(V.stride(1)), int(nb),
                                      C.c_void_p(R.data_ptr()), int(R.stride(1)), C.c_void_p(status.data_ptr())))

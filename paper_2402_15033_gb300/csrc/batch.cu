@@ -546,7 +546,8 @@ int gmres_batch_create(gmres_batch** out, int32_t nsys, const int64_t* n, const 
            "need s | panel | m, m + 1 <= 64, s <= 16");
     GM_ARG(o.precision == GMRES_PREC_FP64 || o.precision == GMRES_PREC_MIXED, "unknown precision");
     GM_ARG(o.tol > 0.0 && o.max_restarts >= 1, "bad tol / max_restarts");
-    GM_ARG(o.arith == GMRES_ARITH_FP64 || o.arith == GMRES_ARITH_DD, "unknown arith");
+    GM_ARG(o.arith == GMRES_ARITH_FP64 || o.arith == GMRES_ARITH_DD,
+           "arith must be GMRES_ARITH_FP64 or GMRES_ARITH_DD for batches");
     gmres_batch* c = new gmres_batch();
     c->opts = o;
     c->nsys = nsys;

@@ -41,6 +41,7 @@ constexpr int kPipNoTrsm = 2;     // update kernel: V <- V - Q P only (T taken a
 // Arithmetic of the Gram and update kernels (gmres_opts.arith).
 constexpr int kArithFP64 = 0;     // native FP64 pipe (default)
 constexpr int kArithDD = 1;       // double-float on the FP32 pipe (df.cuh), ~2^-48 relative
+constexpr int kArithTC = 2;       // Gram on the bf16 tensor cores by exact slicing (gram_tc.cuh)
 
 // ---------------------------------------------------------------- launchers
 // BCGS-PIP step 1+2: [P; G] = [Q, V]^T V split over n rows; the last CTA to

@@ -21,7 +21,10 @@
 // SM per clock (1.19 TFLOP/s measured): the Gram and the update are bound by
 // FP64 arithmetic, not by HBM, at the paper's block sizes.
 #include <algorithm>
+#include <type_traits>
 #include "pip_body.cuh"
+#include "gram_tc.cuh"
+#include "update_tc.cuh"
 
 namespace gm {
 
@@ -55,6 +58,67 @@ gram_wide_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, int k,
     double* partial0 = partial + (size_t)g * G * ps;
     gram_wide_part<T>(n, Q, ldq, k, V, ldv, nb, g, blockIdx.x, G, partial0 + blockIdx.x * ps, smem);
     pip_finish(k, nb, g, gridDim.y, G, R, ldr, partial0, ps, counter, gram, d_status, d_skip, smem, mode);
+}
+
+// Exact-slice tensor-core Gram (gram_tc.cuh), k + nb <= 64: one column group.
+__global__ void __launch_bounds__(kGramThreads, 2)
+gram_tc_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
+               const double* __restrict__ V, int64_t ldv, int nb, double* __restrict__ R, int ldr,
+               double* partial, unsigned* counter, double* gram, int32_t* d_status,
+               int32_t* d_skip, int mode) {
+    extern __shared__ double smem[];
+    if (d_skip && *d_skip) return;
+    const int G = gridDim.x;
+    const size_t ps = (size_t)kMaxNB * nb;
+    gram_tc_part(n, Q, ldq, k, V, ldv, nb, blockIdx.x, G, partial + blockIdx.x * ps, smem);
+    pip_finish(k, nb, 0, 1, G, R, ldr, partial, ps, counter, gram, d_status, d_skip, smem, mode);
+}
+
+cudaError_t launch_gram_tc(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k,
+                           const double* V, int64_t ldv, int nb, double* R, int ldr, const PipWork& w,
+                           int32_t* d_status, int32_t* d_skip, int grid, int mode) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)gram_tc_smem(kTcMaxKX));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    // two CTAs per SM (the chunk tiles take most of the shared memory)
+    const int G = std::min(grid, 2 * num_sms());
+    gram_tc_kernel<<<G, kGramThreads, gram_tc_smem(k + nb), st>>>(n, Q, ldq, k, V, ldv, nb, R, ldr, w.partial,
+                                                                   w.counter, w.gram, d_status, d_skip, mode);
+    return cudaGetLastError();
+}
+
+// Exact-slice tensor-core update (update_tc.cuh), k + nb <= 64.
+__global__ void __launch_bounds__(512, 1)
+update_tc_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k, double* V, int64_t ldv, int nb,
+                 const double* __restrict__ R, int ldr, const int32_t* d_status, const int32_t* d_skip, int mode) {
+    extern __shared__ __align__(16) char tu_smem[];
+    if ((d_skip && *d_skip) || *d_status) return;
+    update_tc_body(n, Q, ldq, k, V, ldv, nb, R, ldr, mode, blockIdx.x, gridDim.x, tu_smem);
+}
+
+cudaError_t launch_update_tc(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, double* V,
+                             int64_t ldv, int nb, const double* R, int ldr, const int32_t* d_status,
+                             const int32_t* d_skip, int mode) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)update_tc_smem(kTuMaxKX, kTuMaxKX));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    // wide blocks: one 16-warp CTA per SM (the W slices take half the shared
+    // memory); narrow ones: two 8-warp CTAs per SM
+    const int threads = nb > 32 ? 512 : 256;
+    const int per_sm = nb > 32 ? 1 : 2;
+    const int64_t chunks = (n + kTuRows - 1) / kTuRows;
+    const int G = (int)std::min<int64_t>(chunks, (int64_t)per_sm * num_sms());
+    update_tc_kernel<<<G, threads, update_tc_smem(k + nb, nb), st>>>(n, Q, ldq, k, V, ldv, nb, R, ldr, d_status,
+                                                                     d_skip, mode);
+    return cudaGetLastError();
 }
 
 // Update, nb <= 16: one thread per row, P and T staged in shared memory.
@@ -219,6 +283,10 @@ cudaError_t pip_gram_chol_t(cudaStream_t st, int64_t n, const T* Q, int64_t ldq,
                             const T* V, int64_t ldv, int nb, double* R, int ldr,
                             const PipWork& w, int32_t* d_status, int32_t* d_skip, int grid, int mode,
                             int arith) {
+    if constexpr (std::is_same<T, double>::value) {
+        if (arith == kArithTC && k + nb <= kTcMaxKX)
+            return launch_gram_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode);
+    }
     if (arith == kArithDD) {
         switch (nb) {
 #define GM_CASE(NBV) case NBV: return launch_skinny_df<T, NBV>(st, n, Q, ldq, k, V, ldv, R, ldr, w, d_status, d_skip, grid, mode);
@@ -249,6 +317,10 @@ template <typename T>
 cudaError_t pip_update_t(cudaStream_t st, int64_t n, const T* Q, int64_t ldq, int k,
                          T* V, int64_t ldv, int nb, const double* R, int ldr,
                          const int32_t* d_status, const int32_t* d_skip, int mode, int arith) {
+    if constexpr (std::is_same<T, double>::value) {
+        if (arith == kArithTC && k + nb <= kTuMaxKX)
+            return launch_update_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, d_skip, mode);
+    }
     if (arith == kArithDD) {
         switch (nb) {
 #define GM_CASE(NBV) case NBV: return launch_update_skinny_df<T, NBV>(st, n, Q, ldq, k, V, ldv, R, ldr, d_status, d_skip, mode);

@@ -166,7 +166,8 @@ static int check_opts(const gmres_opts* o) {
     const int panel = o->ortho == GMRES_ORTHO_BCGS_PIP2 ? o->s : o->panel;
     GM_ARG(panel >= o->s && panel % o->s == 0 && o->m % panel == 0, "need s | panel | m");
     GM_ARG(o->sigma >= 0.0 && std::isfinite(o->sigma), "sigma must be >= 0");
-    GM_ARG(o->arith == GMRES_ARITH_DD || o->arith == GMRES_ARITH_FP64, "unknown arith");
+    GM_ARG(o->arith == GMRES_ARITH_DD || o->arith == GMRES_ARITH_FP64 || o->arith == GMRES_ARITH_TC,
+           "unknown arith");
     return GMRES_OK;
 }
 
@@ -662,6 +663,12 @@ int ortho_gram_chol_dd(void* stream, int64_t n, const double* Q, int64_t ldq, in
     return gram_chol_impl(stream, n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status, kArithDD);
 }
 
+int ortho_gram_chol_tc(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, const double* V,
+                       int64_t ldv, int32_t nb, double* R, int32_t ldr, void* d_work, size_t work_bytes,
+                       int32_t* d_status) {
+    return gram_chol_impl(stream, n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status, kArithTC);
+}
+
 static int update_impl(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,
                  int32_t nb, const double* R, int32_t ldr, const int32_t* d_status, int arith) {
     clear_error();
@@ -687,6 +694,11 @@ int ortho_update(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t 
 int ortho_update_dd(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,
                     int32_t nb, const double* R, int32_t ldr, const int32_t* d_status) {
     return update_impl(stream, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, kArithDD);
+}
+
+int ortho_update_tc(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,
+                    int32_t nb, const double* R, int32_t ldr, const int32_t* d_status) {
+    return update_impl(stream, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, kArithTC);
 }
 
 int ortho_stage1(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,

@@ -20,11 +20,11 @@ def solve_gpu(capi, A, b, x0=None, **opts):
     return rc, res, x
 
 
-def check_against_oracle(capi, A, b, m, s, panel, ortho="two_stage", tol=1e-8):
+def check_against_oracle(capi, A, b, m, s, panel, ortho="two_stage", tol=1e-8, arith=0):
     """Same status as the oracle; on success x within 1e-6 relative of the
     oracle's x at relative residual tol, iteration count within +-s; on a
     breakdown the same block (and pivot) as the oracle."""
-    kw = dict(m=m, s=s, panel=panel, tol=tol)
+    kw = dict(m=m, s=s, panel=panel, tol=tol, arith=arith)
     if ortho == "bcgs_pip2":
         kw["ortho"] = capi.GMRES_ORTHO_BCGS_PIP2
     rc, res, x = solve_gpu(capi, A, b, **kw)
@@ -58,6 +58,16 @@ def test_laplace2d_matches_oracle(lib, N, m, s, panel):
     xt = synth.x_true(A.n, 0)
     b = kr.as_operator(A) @ xt
     check_against_oracle(capi, A, b, m, s, panel)
+
+
+@pytest.mark.parametrize("N,m,s,panel", [(64, 60, 5, 60), (64, 60, 5, 20), (40, 30, 5, 30), (20, 12, 3, 6)])
+def test_laplace2d_tensor_core_arithmetic_matches_oracle(lib, N, m, s, panel):
+    """GMRES_ARITH_TC (exact-slice tensor-core Gram and update) meets the same
+    bars as FP64 on the Laplace configurations."""
+    from paper_2402_15033_gb300 import capi
+    A = synth.laplace2d(N)
+    b = kr.as_operator(A) @ synth.x_true(A.n, 0)
+    check_against_oracle(capi, A, b, m, s, panel, arith=capi.GMRES_ARITH_TC)
 
 
 def test_bcgs_pip2_mode_matches_oracle(lib):
@@ -182,10 +192,11 @@ def test_mpk_matches_oracle(lib):
     S.close()
 
 
-@pytest.mark.parametrize("arith", [0, 1])
+@pytest.mark.parametrize("arith", [0, 1, 2])
 def test_both_arithmetics_match_oracle(lib, arith):
-    """GMRES_ARITH_FP64 (native FP64 pipe, default) and GMRES_ARITH_DD (opt-in
-    double-float on the FP32 pipe) both meet the parity bars on this system."""
+    """GMRES_ARITH_FP64 (native FP64 pipe, default), GMRES_ARITH_DD (opt-in
+    double-float on the FP32 pipe) and GMRES_ARITH_TC (opt-in exact-slice
+    tensor cores) all meet the parity bars on this system."""
     from paper_2402_15033_gb300 import capi
     A = synth.convdiff2d(48, 3)
     b = kr.as_operator(A) @ synth.x_true(A.n, 2)

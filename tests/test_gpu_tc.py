@@ -1,0 +1,217 @@
+"""Exact-slice tensor-core BCGS-PIP (GMRES_ARITH_TC): parity of
+ortho_gram_chol_tc + ortho_update_tc with the CPU oracle's BCGS-PIP (§IV-C,
+Fig. 4a), and the properties that pin the slicing itself.
+
+Tolerances.  The slicing keeps 55 bits of every column's largest entry per
+128-row chunk and sums the digit products exactly, so a Gram entry differs
+from the exact X^T Y by a few units of 2^-53 of ||x_i|| ||y_j|| per chunk
+(normwise, as FP64's own dot-product bound).  The parity bars are those of
+the FP64 kernels (1e-12 of the column norm of R, widened by kappa(T)/100);
+the exactness test holds the Gram entries to 2^-48 ||x_i|| ||y_j|| against
+rational arithmetic.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import blockortho as bo
+from oracle import checks
+
+pytestmark = pytest.mark.gpu
+
+
+def run_pip_tc(capi, Q, V, ld_pad=0, update=True, tc_update=True):
+    n, nb = V.shape
+    k = 0 if Q is None else Q.shape[1]
+    ld = n + ld_pad
+    buf = torch.zeros(k + nb, ld, dtype=torch.float64, device="cuda")
+    if k:
+        buf[:k, :n] = torch.tensor(Q.T)
+    buf[k:, :n] = torch.tensor(V.T)
+    Qd = buf[:k].T[:n] if k else None
+    Vd = buf[k:].T[:n]
+    R = torch.full((nb, k + nb + 3), np.nan, dtype=torch.float64, device="cuda").T
+    work = torch.empty(capi.workspace_bytes(n, k, nb), dtype=torch.uint8, device="cuda")
+    st = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+    capi.ortho_gram_chol_tc(Qd, Vd, R, work, st, k=k)
+    if update:
+        capi.ortho_update(Qd, Vd, R, st, k=k, tc=tc_update)
+    torch.cuda.synchronize()
+    return Vd.cpu().numpy(), R[: k + nb].cpu().numpy(), int(st.item())
+
+
+def assert_parity(Q, V, Vg, Rg, st):
+    k = 0 if Q is None else Q.shape[1]
+    Qh, P, T = bo.bcgs_pip(np.zeros((V.shape[0], 0)) if Q is None else Q, V)
+    Rref = np.concatenate([P, T], 0)
+    assert st == 0
+    scale = np.linalg.norm(Rref, axis=0)
+    kap = np.linalg.cond(T)
+    tol = 1e-12 * max(1.0, kap / 100.0)
+    assert np.all(np.abs(Rg - Rref) <= tol * scale[None, :]), np.max(np.abs(Rg - Rref) / scale)
+    assert np.all(np.tril(Rg[k:], -1) == 0.0)
+    err = np.linalg.norm(Vg - Qh, axis=0)
+    assert np.all(err <= 1e-12 * max(1.0, kap)), (err.max(), kap)
+
+
+@pytest.mark.parametrize("n,k,nb", [
+    (1, 0, 1), (37, 0, 5), (128, 0, 5), (129, 1, 5), (4099, 6, 5), (5000, 56, 5), (70001, 59, 5),
+    (12345, 11, 10), (3001, 30, 16), (777, 3, 1), (61, 0, 61), (2000, 0, 61), (70001, 0, 61),
+    (3333, 20, 21), (9000, 0, 17), (5000, 0, 64), (20011, 1, 57), (8191, 16, 48), (300, 40, 24)])
+def test_tc_gram_matches_oracle(lib, n, k, nb):
+    from paper_2402_15033_gb300 import capi
+    if n < k + nb:
+        pytest.skip("needs n >= k + nb")
+    g = synth.rng(900 + n + k + nb)
+    Q = bo.hhqr(g.standard_normal((n, k)))[0] if k else None
+    V = g.standard_normal((n, nb)) / np.sqrt(n) + (Q @ g.standard_normal((k, nb)) / 4 if k else 0.0)
+    Vg, Rg, st = run_pip_tc(capi, Q, V, ld_pad=n % 2)
+    assert_parity(Q, V, Vg, Rg, st)
+
+
+@pytest.mark.parametrize("n,k,nb", [(4099, 6, 5), (2000, 0, 61), (3001, 30, 16)])
+def test_tc_gram_with_fp64_update(lib, n, k, nb):
+    """The tensor-core Gram paired with the FP64 update: same bars."""
+    from paper_2402_15033_gb300 import capi
+    g = synth.rng(700 + n + k)
+    Q = bo.hhqr(g.standard_normal((n, k)))[0] if k else None
+    V = g.standard_normal((n, nb)) / np.sqrt(n) + (Q @ g.standard_normal((k, nb)) / 4 if k else 0.0)
+    Vg, Rg, st = run_pip_tc(capi, Q, V, ld_pad=n % 2, tc_update=False)
+    assert_parity(Q, V, Vg, Rg, st)
+
+
+@pytest.mark.parametrize("scales", [(-40, 30), (25, -25), (-300, 0)])
+def test_tc_update_equilibrates_column_scales(lib, scales):
+    """V columns scaled by very different powers of two next to unit Q columns:
+    the update slices V_j 2^(-g_j) against W rows scaled by 2^(g_j), so Q^
+    keeps the FP64 parity bar (without equilibration the small entries of a
+    row would lose their low digits)."""
+    from paper_2402_15033_gb300 import capi
+    g = synth.rng(808)
+    n, k, nb = 30011, 12, 6
+    Q = bo.hhqr(g.standard_normal((n, k)))[0]
+    V = g.standard_normal((n, nb)) / np.sqrt(n) + Q @ g.standard_normal((k, nb)) / 3
+    V[:, ::2] *= 2.0 ** scales[0]
+    V[:, 1::2] *= 2.0 ** scales[1]
+    Vg, Rg, st = run_pip_tc(capi, Q, V, ld_pad=1)
+    assert_parity(Q, V, Vg, Rg, st)
+
+
+def test_tc_wider_than_one_tile_uses_fp64(lib):
+    """k + nb > 64 runs the FP64 kernel: same bars."""
+    from paper_2402_15033_gb300 import capi
+    g = synth.rng(31)
+    n, k, nb = 4000, 70, 40
+    Q = bo.hhqr(g.standard_normal((n, k)))[0]
+    V = g.standard_normal((n, nb)) / np.sqrt(n)
+    Vg, Rg, st = run_pip_tc(capi, Q, V)
+    assert_parity(Q, V, Vg, Rg, st)
+
+
+def _hard_digits(g, n, c):
+    """Entries whose 8-bit digits take extreme and mixed values: +-(2 - 2^-52)
+    scaled by random powers of two within +-3 binades, mixed signs, some
+    exact zeros, and integers with long carry chains."""
+    X = g.standard_normal((n, c))
+    X[g.random((n, c)) < 0.3] = 2.0 - 2.0 ** -52
+    X *= np.where(g.random((n, c)) < 0.5, -1.0, 1.0)
+    X *= np.exp2(g.integers(-3, 4, size=(n, c)))
+    X[g.random((n, c)) < 0.05] = 0.0
+    X[g.random((n, c)) < 0.05] = 1.0 + 2.0 ** -52 * 0x7F7F7F
+    return X
+
+
+@pytest.mark.parametrize("n,k,nb", [(300, 6, 3), (257, 9, 5), (130, 2, 7)])
+def test_tc_gram_entries_against_exact_rationals(lib, n, k, nb):
+    """P = Q^T V (the first k rows of R) and G = T^T T + P^T P against X^T Y
+    summed in exact rationals: every entry within 2^-48 ||x_i|| ||y_j||.  A
+    tensor core that dropped low bits of an FP32 accumulation, a wrong digit
+    weight or a lost carry would miss this by many orders of magnitude."""
+    from paper_2402_15033_gb300 import capi
+    g = synth.rng(4242 + n)
+    Q = _hard_digits(g, n, k)
+    # a power-of-two scale (digits unchanged) with ||Q||_2 <= 1/2 keeps
+    # G - P^T P = V^T (I - Q Q^T) V positive definite, so T exists
+    Q *= 2.0 ** -(np.ceil(np.log2(np.linalg.norm(Q))) + 1)
+    V = _hard_digits(g, n, nb)
+    _, Rg, st = run_pip_tc(capi, Q, V, ld_pad=n % 2, update=False)
+    P_exact = checks.exact_gram(Q, V)
+    nq = np.linalg.norm(Q, axis=0)
+    nv = np.linalg.norm(V, axis=0)
+    err = np.abs(Rg[:k] - P_exact) / np.outer(nq, nv)
+    assert err.max() <= 2.0 ** -48, err.max()
+    assert st == 0
+    T = Rg[k:]
+    G_exact = checks.exact_gram(V, V)
+    G_rec = T.T @ T + Rg[:k].T @ Rg[:k]
+    assert np.max(np.abs(G_rec - G_exact) / np.outer(nv, nv)) <= 1e-13
+
+
+@pytest.mark.parametrize("scale_exp", [-400, -37, 29, 400])
+def test_tc_power_of_two_scaling_is_exact(lib, scale_exp):
+    """Scaling V by 2^e shifts the chunk exponents and nothing else: R scales
+    by exactly 2^e bit for bit and Q^ is bit-identical (no FP32 range limit,
+    unlike double-float)."""
+    from paper_2402_15033_gb300 import capi
+    g = synth.rng(55)
+    n, k, nb = 20011, 7, 5
+    Q = bo.hhqr(g.standard_normal((n, k)))[0]
+    V = g.standard_normal((n, nb))
+    V0, R0, s0 = run_pip_tc(capi, Q, V, ld_pad=1)
+    V1, R1, s1 = run_pip_tc(capi, Q, V * 2.0 ** scale_exp, ld_pad=1)
+    assert s0 == 0 and s1 == 0
+    assert np.array_equal(R1, R0 * 2.0 ** scale_exp)
+    assert np.array_equal(V1, V0)
+
+
+def test_tc_breakdown_nan_and_repeatability(lib):
+    from paper_2402_15033_gb300 import capi
+    g = synth.rng(12)
+    n = 500
+    V = g.standard_normal((n, 5))
+    V[:, 3] = 0.0
+    Vg, _, st = run_pip_tc(capi, None, V)
+    assert st == 4 and np.array_equal(Vg, V)
+    V = g.standard_normal((300, 4))
+    V[17, 2] = np.nan
+    _, _, st = run_pip_tc(capi, None, V)
+    assert st == 3
+    n, k, nb = 100003, 20, 5
+    Q = bo.hhqr(g.standard_normal((n, k)))[0]
+    V = g.standard_normal((n, nb))
+    a = run_pip_tc(capi, Q, V)
+    b = run_pip_tc(capi, Q, V)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_tc_two_stage_on_ill_conditioned_panels(lib):
+    """The glued matrix (panel kappa 1e5) through stage 1 per block and stage 2
+    on the big panel with the tensor-core Gram: O(eps) orthogonality after
+    stage 2 (Theorem 3) and the oracle's R at the kappa^2 eps level."""
+    from paper_2402_15033_gb300 import capi
+    n, s, nblk = 20000, 5, 6
+    V = synth.glued(n, s, nblk, 1e5, seed=9)
+    _, _, Rd, _ = bo.two_stage_panel(np.zeros((n, 0)), [V[:, i * s:(i + 1) * s] for i in range(nblk)])
+    ncol = s * nblk
+    B = torch.tensor(V.T.copy(), device="cuda").T
+    Rh = torch.zeros(ncol, ncol, dtype=torch.float64, device="cuda").T
+    work = torch.empty(capi.workspace_bytes(n, ncol, ncol), dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for j in range(nblk):
+        c0 = j * s
+        Qd = B[:, :c0] if c0 else None
+        capi.ortho_gram_chol_tc(Qd, B[:, c0:c0 + s], Rh[:c0 + s, c0:c0 + s], work, st, k=c0)
+        capi.ortho_update(Qd, B[:, c0:c0 + s], Rh[:c0 + s, c0:c0 + s], st, k=c0, tc=True)
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+    R2 = torch.zeros(ncol, ncol, dtype=torch.float64, device="cuda").T
+    capi.ortho_gram_chol_tc(None, B, R2, work, st, k=0)
+    capi.ortho_update(None, B, R2, st, k=0, tc=True)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    Qg = B.cpu().numpy()
+    assert checks.orth_error(Qg)[0] < 100 * np.finfo(float).eps
+    Rfin = R2.cpu().numpy() @ Rh.cpu().numpy()
+    assert np.allclose(Rfin, Rd, rtol=0, atol=1e-9 * np.abs(Rd).max())
+    assert np.allclose(Qg @ Rfin, V, atol=1e-12 * np.abs(V).max())
