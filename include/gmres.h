@@ -62,6 +62,9 @@ extern "C" {
                                       /* Both the Gram and the block update; blocks with k + nb > 64   */
                                       /* and FP32 bases use the FP64 kernels.  Single-system solver    */
                                       /* and the ortho calls only (the batched engine rejects it).     */
+                                      /* GMRES_ARITH_DD and _TC stage 16-byte column pieces: columns   */
+                                      /* that do not start on a 16-byte boundary (odd ld for FP64)     */
+                                      /* run the FP64 kernels instead.                                 */
 
 typedef struct gmres_opts {
     int32_t m;             /* restart length: m+1 basis vectors per cycle (Table 1)            */

@@ -3,12 +3,12 @@
 // Rump, 2012): FP64 inputs, results of FP64 quality, for k + nb <= 64.
 //
 // Per 64-row chunk and column c let e_c be the largest binary exponent in the
-// chunk (|x| < 2^(e_c+1)).  Each value is rounded to the integer
-// F = round(|x| 2^(54 - e_c)) (< 2^55, 55 significant bits for the largest
-// entries), signed, and written in balanced base 256:
-//     F = sum_{p=0..6} d_p 256^(6-p),  d_1..d_6 in [-128, 127],  d_0 in [-128, 128],
-// so x = sum_p d_p 2^(e_c - 6 - 8p) up to the rounding of F, and every digit
-// is exact in bf16.  For a column pair (i, j) the chunk's contribution is
+// chunk (|x| < 2^(e_c+1)).  Each value is truncated to the integer
+// F = trunc(|x| 2^(54 - e_c)) (< 2^55, 55 significant bits for the largest
+// entries) and written, signed like x, in balanced base 256:
+//     F = sum_{p=0..6} d_p 256^(6-p),  |d_p| <= 128,
+// so x = sum_p d_p 2^(e_c - 6 - 8p) within 2^(e_c - 54), and every digit is
+// exact in bf16.  For a column pair (i, j) the chunk's contribution is
 //     x_i^T y_j = 2^(e_i + e_j - 12) sum_{t=0..6} 2^(-8t) I_t,
 //     I_t = sum_{p+q=t} sum_rows d_p d'_q,
 // and each I_t is accumulated by mma.sync m16n8k16 (bf16 inputs, FP32
@@ -92,7 +92,7 @@ __device__ void gram_tc_part(int64_t n, const double* __restrict__ Q, int64_t ld
 
     const int64_t nchunks = (n + kTcRows - 1) / kTcRows;
     if ((int64_t)b < nchunks) {
-        stage_chunk_async<double>(Q, ldq, k, V, ldv, 0, kx, (int64_t)b * kTcRows, kTcRows, n, raw);
+        tc_stage64(Q, ldq, k, V, ldv, kx, (int64_t)b * kTcRows, n, raw);
         cp_async_commit();
     }
     for (int64_t ci = b; ci < nchunks; ci += G) {
@@ -109,15 +109,15 @@ __device__ void gram_tc_part(int64_t n, const double* __restrict__ Q, int64_t ld
             if (bad || eb == 0) eb = 1023;         // all zero (or subnormal): every digit is zero
             if (lane == 0) ex[c] = bad ? kTcBadExp : eb - 1023;
             uint32_t d0[kTcSlices], d1[kTcSlices];
-            tc_digits(tc_fixed(v.x, eb), d0);
-            tc_digits(tc_fixed(v.y, eb), d1);
+            tc_slice(v.x, eb, d0);
+            tc_slice(v.y, eb, d1);
             uint4* u = sl + (size_t)c * 2 * kTcWp + lane;
             tc_pack(d0, d1, u[0], u[kTcWp]);
         }
         __syncthreads();
         // the raw tile is free: the next chunk streams in during the MMAs
         if (ci + G < nchunks) {
-            stage_chunk_async<double>(Q, ldq, k, V, ldv, 0, kx, (ci + G) * kTcRows, kTcRows, n, raw);
+            tc_stage64(Q, ldq, k, V, ldv, kx, (ci + G) * kTcRows, n, raw);
             cp_async_commit();
         }
         // 2. exact digit products on the tensor cores, one output tile at a time
@@ -147,7 +147,7 @@ __device__ void gram_tc_part(int64_t n, const double* __restrict__ Q, int64_t ld
             for (int i = 0; i < 4; ++i) {
                 const int row = m0 + gid + ((i & 2) ? 8 : 0);       // X column
                 const int col = n0 + 2 * tig + (i & 1);             // Y column
-                if (row >= kx || col >= nb) continue;
+                if (row >= kx || col >= nb || !needed(row, col, k)) continue;
                 const long long S = tc_combine(acc[0][i], acc[1][i], acc[2][i], acc[3][i], acc[4][i], acc[5][i],
                                                acc[6][i]);
                 const int ei = ex[row], ej = ex[k + col];

@@ -110,13 +110,14 @@ cudaError_t launch_update_tc(cudaStream_t st, int64_t n, const double* Q, int64_
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    // wide blocks: one 16-warp CTA per SM (the W slices take half the shared
-    // memory); narrow ones: two 8-warp CTAs per SM
+    // wide blocks: one 16-warp CTA per SM (the W slices take a third of the
+    // shared memory); narrow ones: 8-warp CTAs, two per SM where they fit
     const int threads = nb > 32 ? 512 : 256;
-    const int per_sm = nb > 32 ? 1 : 2;
+    const size_t sm = update_tc_smem(k + nb, nb);
+    const int per_sm = nb > 32 ? 1 : (2 * (sm + 1024) <= 228 * 1024 ? 2 : 1);
     const int64_t chunks = (n + kTuRows - 1) / kTuRows;
     const int G = (int)std::min<int64_t>(chunks, (int64_t)per_sm * num_sms());
-    update_tc_kernel<<<G, threads, update_tc_smem(k + nb, nb), st>>>(n, Q, ldq, k, V, ldv, nb, R, ldr, d_status,
+    update_tc_kernel<<<G, threads, sm, st>>>(n, Q, ldq, k, V, ldv, nb, R, ldr, d_status,
                                                                      d_skip, mode);
     return cudaGetLastError();
 }
@@ -278,11 +279,24 @@ cudaError_t launch_update_skinny_df(cudaStream_t st, int64_t n, const T* Q, int6
 
 }  // namespace
 
+// The tensor-core and double-float kernels stage column pieces with 16-byte
+// asynchronous copies: every column of Q and V must start on a 16-byte
+// boundary (base aligned and ld * sizeof(T) a multiple of 16).  Other layouts
+// run the FP64-pipe kernels, which read element by element.
+template <typename T>
+static bool cols_aligned16(const T* Q, int64_t ldq, int k, const T* V, int64_t ldv) {
+    auto ok = [](const T* p, int64_t ld) {
+        return (reinterpret_cast<uintptr_t>(p) & 15) == 0 && ((uint64_t)ld * sizeof(T)) % 16 == 0;
+    };
+    return ok(V, ldv) && (k == 0 || ok(Q, ldq));
+}
+
 template <typename T>
 cudaError_t pip_gram_chol_t(cudaStream_t st, int64_t n, const T* Q, int64_t ldq, int k,
                             const T* V, int64_t ldv, int nb, double* R, int ldr,
                             const PipWork& w, int32_t* d_status, int32_t* d_skip, int grid, int mode,
                             int arith) {
+    if (arith != kArithFP64 && !cols_aligned16(Q, ldq, k, V, ldv)) arith = kArithFP64;
     if constexpr (std::is_same<T, double>::value) {
         if (arith == kArithTC && k + nb <= kTcMaxKX)
             return launch_gram_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode);
@@ -317,6 +331,7 @@ template <typename T>
 cudaError_t pip_update_t(cudaStream_t st, int64_t n, const T* Q, int64_t ldq, int k,
                          T* V, int64_t ldv, int nb, const double* R, int ldr,
                          const int32_t* d_status, const int32_t* d_skip, int mode, int arith) {
+    if (arith != kArithFP64 && !cols_aligned16<T>(Q, ldq, k, V, ldv)) arith = kArithFP64;
     if constexpr (std::is_same<T, double>::value) {
         if (arith == kArithTC && k + nb <= kTuMaxKX)
             return launch_update_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, d_skip, mode);

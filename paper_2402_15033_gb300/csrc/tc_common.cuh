@@ -4,10 +4,10 @@
 //
 // A value x is sliced against a common biased exponent eb of its group (a
 // chunk column for the Gram, a row for the update), eb >= x's own exponent:
-// F = round(|x| 2^(54 - e)) (e = eb - 1023; |F| < 2^55) is written in balanced
-// base 256, F = sum_{p=0..6} d_p 256^(6-p), d_1..d_6 in [-128, 127], d_0 in
-// [-128, 128], so that x = sum_p d_p 2^(e - 6 - 8p) up to the rounding of F and
-// every digit is exact in bf16.  A dot product of two sliced vectors of at most
+// F = trunc(|x| 2^(54 - e)) (e = eb - 1023; F < 2^55) is written in balanced
+// base 256, F = sum_{p=0..6} d_p 256^(6-p) with |d_p| <= 128, signed like x, so
+// that x = sum_p d_p 2^(e - 6 - 8p) within 2^(e - 54) (55 bits for the
+// group's largest entries) and every digit is exact in bf16.  A dot product of two sliced vectors of at most
 // 64 terms is 2^(e_x + e_y - 12) sum_{t=0..6} 2^(-8t) I_t with
 // I_t = sum_{p+q=t} sum_terms d_p d'_q; every digit product is an integer of
 // magnitude <= 2^14 and every partial sum of I_t is at most (t+1) 64 2^14 < 2^24,
@@ -36,35 +36,35 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], uint32_t a0, uint3
 // Biased FP64 exponent field of x.
 __device__ __forceinline__ int tc_bexp(double x) { return (__double2hiint(x) >> 20) & 0x7FF; }
 
-// Signed F = round(|x| 2^(54 - e)) * sign(x) for the chunk-column biased
-// exponent eb >= the value's own (rounding half up); zero and subnormals give 0.
-__device__ __forceinline__ long long tc_fixed(double x, int eb) {
+// The seven digits of x against the group's biased exponent eb (>= x's own),
+// as FP32 bit patterns whose high halves are the bf16 digits: F =
+// trunc(|x| 2^(54 - e)) (e = eb - 1023; zero and subnormals give 0) is shifted
+// into place with two 32-bit funnel shifts, 128 is added at every lower digit
+// position (each byte of the sum is then the balanced digit plus 128, the
+// carries included), and a byte b becomes the float +-(b - 128) by one byte
+// permute into the signed constant +-1.5 * 2^23 and one exact addition.
+__device__ __forceinline__ void tc_slice(double x, int eb, uint32_t (&dig)[kTcSlices]) {
     const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
     const int e = (int)(hi >> 20) & 0x7FF;
-    unsigned long long m = ((unsigned long long)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
-    if (e == 0) m = 0;
-    const int d = min(max(eb - e, 0), 63);
-    const unsigned long long F = ((m << 2) + ((1ull << d) >> 1)) >> d;
-    return (hi >> 31) ? -(long long)F : (long long)F;
-}
-
-// FP32 bit patterns of the seven balanced base-256 digits of F (most
-// significant first); each bf16 digit is the high half.  Adding 128 at every
-// lower digit position makes each byte of the sum the digit plus 128, with the
-// carries of the balanced representation; a byte b becomes the float b - 128
-// by one byte permute into 1.5 * 2^23 and one exact subtraction.
-__device__ __forceinline__ void tc_digits(long long F, uint32_t (&dig)[kTcSlices]) {
-    const long long Gv = F + 0x808080808080ll;
-    const uint32_t lo = (uint32_t)Gv;
-    const uint32_t hi = (uint32_t)((unsigned long long)Gv >> 32);
-    const float off = -12583040.0f;              // -(1.5 * 2^23 + 128)
-    dig[6] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(lo, 0x4B400000u, 0x7650)), off));
-    dig[5] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(lo, 0x4B400000u, 0x7651)), off));
-    dig[4] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(lo, 0x4B400000u, 0x7652)), off));
-    dig[3] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(lo, 0x4B400000u, 0x7653)), off));
-    dig[2] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(hi, 0x4B400000u, 0x7650)), off));
-    dig[1] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(hi, 0x4B400000u, 0x7651)), off));
-    dig[0] = __float_as_uint(__fadd_rn(__int_as_float(0x4B400000 + ((int)hi >> 16)), -12582912.0f));
+    const uint32_t mh = e ? ((hi & 0xFFFFFu) | 0x100000u) : 0u;
+    const uint32_t ml = e ? lo : 0u;
+    const int d = min(eb - e, 63);
+    const uint32_t h = (mh << 2) | (ml >> 30), l = ml << 2;          // the mantissa times 4 (55 bits)
+    const uint32_t fl = __funnelshift_rc(l, h, d) >> max(d - 32, 0);
+    const uint32_t fh = __funnelshift_rc(h, 0u, d);
+    const unsigned long long G = (((unsigned long long)fh << 32) | fl) + 0x808080808080ull;
+    const uint32_t gl = (uint32_t)G, gh = (uint32_t)(G >> 32);
+    const bool neg = (hi >> 31) != 0;
+    const uint32_t magic = neg ? 0xCB400000u : 0x4B400000u;
+    const float off = neg ? 12583040.0f : -12583040.0f;
+    const float off0 = neg ? 12582912.0f : -12582912.0f;
+    dig[6] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(gl, magic, 0x7650)), off));
+    dig[5] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(gl, magic, 0x7651)), off));
+    dig[4] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(gl, magic, 0x7652)), off));
+    dig[3] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(gl, magic, 0x7653)), off));
+    dig[2] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(gh, magic, 0x7650)), off));
+    dig[1] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(gh, magic, 0x7651)), off));
+    dig[0] = __float_as_uint(__fadd_rn(__uint_as_float(magic + (gh >> 16)), off0));
 }
 
 __device__ __forceinline__ double tc_pow2(int e) {   // e in [-1022, 1023]
@@ -82,35 +82,44 @@ __device__ __forceinline__ long long tc_combine(float a0, float a1, float a2, fl
     return hi * 16777216 + lo;
 }
 
-// acc + S * 2^s for |S| < 2^62: one rounding of S to FP64, then an exact
-// power-of-two product and one rounding of the sum; results outside the normal
-// range scale in steps.
-__device__ __forceinline__ double tc_accum(double acc, long long S, int s) {
-    const double d = __ll2double_rn(S);
-    if (s >= -1022 && s <= 1023 - 62) return fma(d, tc_pow2(s), acc);
-    double v = d;
-    int rest = s;
-    while (rest != 0) {
-        const int step = rest > 1000 ? 1000 : (rest < -1000 ? -1000 : rest);
-        v *= tc_pow2(step);
-        rest -= step;
+// S * 2^s in FP64 for |S| < 2^62 by integer operations (rounded to nearest
+// even), so that only the accumulation itself uses the FP64 pipe; results
+// outside the normal range go through FP64 multiplications by powers of two.
+__device__ __forceinline__ double tc_int_to_double(long long S, int s) {
+    if (S == 0) return 0.0;
+    const unsigned long long sgn = S < 0 ? (1ull << 63) : 0ull;
+    unsigned long long M = (unsigned long long)(S < 0 ? -S : S);
+    int msb = 63 - __clzll((long long)M);
+    if (msb > 52) {
+        const int r = msb - 52;
+        const unsigned long long half = 1ull << (r - 1);
+        const unsigned long long rem = M & ((1ull << r) - 1);
+        M >>= r;
+        if (rem > half || (rem == half && (M & 1))) ++M;
+        if (M >> 53) { M >>= 1; ++msb; }
+    } else {
+        M <<= (52 - msb);
     }
-    return acc + v;
-}
-
-// S * 2^s for |S| < 2^62 (one rounding of S; results outside the normal range
-// scale in steps).
-__device__ __forceinline__ double tc_scaled(long long S, int s) {
-    const double d = __ll2double_rn(S);
-    if (s >= -1022 && s <= 1023 - 62) return d * tc_pow2(s);
-    double v = d;
+    const int be = msb + s + 1023;
+    if (be >= 1 && be <= 2046)
+        return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (M & 0xFFFFFFFFFFFFFull)));
+    double v = __longlong_as_double((long long)(sgn | ((unsigned long long)(msb + 1023) << 52) |
+                                                (M & 0xFFFFFFFFFFFFFull)));
     int rest = s;
     while (rest != 0) {
         const int step = rest > 1000 ? 1000 : (rest < -1000 ? -1000 : rest);
-        v *= tc_pow2(step);
+        v *= __longlong_as_double((long long)(step + 1023) << 52);
         rest -= step;
     }
     return v;
+}
+
+// acc + S * 2^s for |S| < 2^62: S rounded once to FP64 and added with one
+// fused multiply-add (the power-of-two product is exact); scales outside the
+// normal range take the integer conversion.
+__device__ __forceinline__ double tc_accum(double acc, long long S, int s) {
+    if (s >= -1022 && s <= 1023 - 62) return fma(__ll2double_rn(S), tc_pow2(s), acc);
+    return acc + tc_int_to_double(S, s);
 }
 
 // Two rows' (or two K terms') digits packed as one bf16x2 word per digit, in
@@ -141,6 +150,26 @@ __device__ __forceinline__ void tc_mma_step(float (&acc)[kTcSlices][4], const ui
 #pragma unroll
         for (int r = 0; r < kTcSlices - p; ++r)
             mma_bf16_16816(acc[p + r], A[p][0], A[p][1], A[p][2], A[p][3], B[r][0], B[r][1]);
+}
+
+// Asynchronous copies of a 64-row chunk of [Q(:, 0:k), V(:, 0:kx-k)] into a
+// column-major shared tile (ld 64): thread t copies rows 2(t % 32), +1 of
+// columns t / 32, t / 32 + nw, ... (nw = blockDim / 32), walking the column
+// pointers by increments; rows at or beyond n are zero-filled.  Q, V and
+// their leading dimensions are 16-byte aligned (row0 is even).
+__device__ __forceinline__ void tc_stage64(const double* Q, int64_t ldq, int k, const double* V, int64_t ldv,
+                                           int kx, int64_t row0, int64_t n, double* tile) {
+    const int q = threadIdx.x & 31, c0 = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t row = row0 + 2 * q;
+    const int bytes = row + 2 <= n ? 16 : (row < n ? 8 : 0);
+    const unsigned dst0 = (unsigned)__cvta_generic_to_shared(tile + 2 * q);
+    int c = c0;
+    for (const double* p = Q + (int64_t)c0 * ldq + row; c < k; c += nw, p += (int64_t)nw * ldq)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst0 + (unsigned)c * 512u),
+                     "l"(bytes ? p : Q), "r"(bytes) : "memory");
+    for (const double* p = V + (int64_t)(c - k) * ldv + row; c < kx; c += nw, p += (int64_t)nw * ldv)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst0 + (unsigned)c * 512u),
+                     "l"(bytes ? p : V), "r"(bytes) : "memory");
 }
 
 }  // namespace gm

@@ -2,7 +2,7 @@
 // cores by exact slicing (tc_common.cuh):
 //     V <- (V - Q P) T^{-1} = [Q, V] W,   W = [-P T^{-1}; T^{-1}]   (kx = k + nb <= 64).
 // Every CTA forms W in FP64 from R (T^{-1} by substitution), slices its columns
-// once, and then streams 32-row chunks of X = [Q, V]: each row is sliced against
+// once, and then streams 64-row chunks of X = [Q, V]: each row is sliced against
 // its own largest exponent (the output of a row is a dot product along that
 // row), the digit products run on the tensor cores with FP32 accumulators that
 // stay exact, and every output is S * 2^(e_row + f_col - 52) rounded once to
@@ -21,15 +21,15 @@
 
 namespace gm {
 
-constexpr int kTuRows = 32;                   // rows per chunk (one row per lane)
+constexpr int kTuRows = 64;                   // rows per chunk (a warp pair covers them, one row per lane)
 constexpr int kTuMaxKX = 64;
-constexpr int kTuMaxTiles = 2;                // 2 M-tiles x up to 8 N-tiles over >= 8 warps
+constexpr int kTuMaxTiles = 2;                // 4 M-tiles x N-tiles: <= 16 over 8 warps (nb <= 32), <= 32 over 16
 
 __host__ __device__ constexpr int tu_nbp(int nb) { return (nb + 7) / 8 * 8; }
 // shared memory: raw chunk, X slices, W slices, integer tables
 __host__ __device__ constexpr size_t update_tc_smem(int kx, int nb) {
     return (size_t)kx * kTuRows * sizeof(double) + (size_t)kTuRows * 2 * kTcWp * 16 +
-           (size_t)tu_nbp(nb) * 2 * kTcWp * 16 + (64 + 64 + kTuRows + 16 * kTuRows) * sizeof(int);
+           (size_t)tu_nbp(nb) * 2 * kTcWp * 16 + (64 + 64 + kTuRows + 8 * kTuRows) * sizeof(int);
 }
 
 // Row r's unit for K pair w (two consecutive columns) in the X slices; the low
@@ -45,7 +45,7 @@ __device__ __forceinline__ int tu_colshift(double nrm2) {
     return (e - 1023) >> 1;                       // floor(log2 ||v||) or one less
 }
 
-// X = [Q(:, 0:k), V(:, 0:nb)] rows in 32-row chunks b, b+G, ...; V overwritten.
+// X = [Q(:, 0:k), V(:, 0:nb)] rows in 64-row chunks b, b+G, ...; V overwritten.
 // blockDim.x = 32 * NW, NW >= 8.
 __device__ void update_tc_body(int64_t n, const double* __restrict__ Q, int64_t ldq, int k, double* V,
                                int64_t ldv, int nb, const double* __restrict__ R, int ldr, int mode, int b, int G,
@@ -55,13 +55,13 @@ __device__ void update_tc_body(int64_t n, const double* __restrict__ Q, int64_t 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int gid = lane >> 2, tig = lane & 3;
     const int nks = (kx + 15) / 16;               // K steps; pairs w < 8 nks are sliced (zeros past kx)
-    double* raw = reinterpret_cast<double*>(smem);                                       // [kx][32]
-    uint4* xu = reinterpret_cast<uint4*>(smem + (size_t)kx * kTuRows * sizeof(double));   // [32][2][kTcWp]
+    double* raw = reinterpret_cast<double*>(smem);                                       // [kx][64]
+    uint4* xu = reinterpret_cast<uint4*>(smem + (size_t)kx * kTuRows * sizeof(double));   // [64][2][kTcWp]
     uint4* wu = xu + kTuRows * 2 * kTcWp;                                                  // [nbp][2][kTcWp]
     int* cshift = reinterpret_cast<int*>(wu + (size_t)nbp * 2 * kTcWp);                    // [64]
     int* fexp = cshift + 64;                                                               // [64]
-    int* rexp = fexp + 64;                                                                 // [32]
-    int* epart = rexp + kTuRows;                                                           // [16][32]
+    int* rexp = fexp + 64;                                                                 // [64]
+    int* epart = rexp + kTuRows;                                                           // [8][64]
 
     // ---- W = [-P T^{-1}; T^{-1}] scaled by the column shifts, in FP64, then sliced
     double* Ts = reinterpret_cast<double*>(wu);   // nb x nb (T), then T^{-1}, in the W-slice region
@@ -126,8 +126,8 @@ __device__ void update_tc_body(int64_t n, const double* __restrict__ Q, int64_t 
         if (bad || eb == 0) eb = 1023;
         if (lane == 0) fexp[j] = bad ? kTcBadExp : eb - 1023;
         uint32_t d0[kTcSlices], d1[kTcSlices];
-        tc_digits(tc_fixed(w0, eb), d0);
-        tc_digits(tc_fixed(w1, eb), d1);
+        tc_slice(w0, eb, d0);
+        tc_slice(w1, eb, d1);
         uint4* u = wu + (size_t)j * 2 * kTcWp + lane;
         tc_pack(d0, d1, u[0], u[kTcWp]);
     }
@@ -138,7 +138,7 @@ __device__ void update_tc_body(int64_t n, const double* __restrict__ Q, int64_t 
     {
         int cnt = 0;
         for (int nt = 0; nt < nbp / 8; ++nt)
-            for (int mt = 0; mt < 2; ++mt) {
+            for (int mt = 0; mt < kTuRows / 16; ++mt) {
                 if (cnt % NW == warp && ntile < kTuMaxTiles) { my_mt[ntile] = mt; my_nt[ntile] = nt; ++ntile; }
                 ++cnt;
             }
@@ -147,55 +147,47 @@ __device__ void update_tc_body(int64_t n, const double* __restrict__ Q, int64_t 
 
     const int64_t nchunks = (n + kTuRows - 1) / kTuRows;
     if ((int64_t)b < nchunks) {
-        stage_chunk_async<double>(Q, ldq, k, V, ldv, 0, kx, (int64_t)b * kTuRows, kTuRows, n, raw);
+        tc_stage64(Q, ldq, k, V, ldv, kx, (int64_t)b * kTuRows, n, raw);
         cp_async_commit();
     }
+    const int half = warp & 1, grp = warp >> 1, ngrp = NW >> 1;
+    const int r = half * 32 + lane;              // this thread's row of the chunk (slicing phases)
     for (int64_t ci = b; ci < nchunks; ci += G) {
         const int64_t row0 = ci * kTuRows;
         cp_async_wait_all();
         __syncthreads();
-        // 1. row exponents (shifted columns): lane = row, warp = K pairs warp, warp + NW, ...
-        double xv[8];
+        // 1. row exponents of the shifted columns: thread (row r, K pairs grp, grp + ngrp, ...)
         int emax = -100000;                       // no nonzero value seen
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int w = warp + u * NW;
-            double x0 = 0.0, x1 = 0.0;
-            if (w < 8 * nks) {
-                const int c0 = 2 * w, c1 = 2 * w + 1;
-                if (c0 < kx) x0 = raw[c0 * kTuRows + lane];
-                if (c1 < kx) x1 = raw[c1 * kTuRows + lane];
-                const int e0 = tc_bexp(x0), e1 = tc_bexp(x1);
-                if (e0 == 0x7FF || e1 == 0x7FF) emax = 0x7FF + 4096;
-                if (e0) emax = max(emax, e0 - cshift[c0]);
-                if (e1) emax = max(emax, e1 - cshift[c1]);
-            }
-            xv[2 * u] = x0;
-            xv[2 * u + 1] = x1;
+        for (int w = grp; w < 8 * nks; w += ngrp) {
+            const int c0 = 2 * w, c1 = 2 * w + 1;
+            const double x0 = c0 < kx ? raw[c0 * kTuRows + r] : 0.0;
+            const double x1 = c1 < kx ? raw[c1 * kTuRows + r] : 0.0;
+            const int e0 = tc_bexp(x0), e1 = tc_bexp(x1);
+            if (e0 == 0x7FF || e1 == 0x7FF) emax = 0x7FF + 4096;
+            if (e0) emax = max(emax, e0 - cshift[c0]);
+            if (e1) emax = max(emax, e1 - cshift[min(c1, kx - 1)]);
         }
-        epart[warp * kTuRows + lane] = emax;
+        epart[grp * kTuRows + r] = emax;
         __syncthreads();
         int eb = -100000;
-        for (int q = 0; q < NW; ++q) eb = max(eb, epart[q * kTuRows + lane]);
+        for (int q = 0; q < ngrp; ++q) eb = max(eb, epart[q * kTuRows + r]);
         const bool bad = eb > 0x7FF + 2048;      // above any shifted exponent: a NaN/inf in the row
         if (bad || eb == -100000) eb = 1023;      // NaN/inf row, or an all-zero row (digits all zero)
-        if (warp == 0) rexp[lane] = bad ? kTcBadExp : eb - 1023;
+        if (grp == 0) rexp[r] = bad ? kTcBadExp : eb - 1023;
         // 2. slices of the row against eb (+ the column shift)
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int w = warp + u * NW;
-            if (w < 8 * nks) {
-                const int c0 = min(2 * w, kx - 1), c1 = min(2 * w + 1, kx - 1);
-                uint32_t d0[kTcSlices], d1[kTcSlices];
-                tc_digits(tc_fixed(xv[2 * u], eb + cshift[c0]), d0);
-                tc_digits(tc_fixed(xv[2 * u + 1], eb + cshift[c1]), d1);
-                tc_pack(d0, d1, xu[tu_xunit(lane, 0, w)], xu[tu_xunit(lane, 1, w)]);
-            }
+        for (int w = grp; w < 8 * nks; w += ngrp) {
+            const int c0 = 2 * w, c1 = 2 * w + 1;
+            const double x0 = c0 < kx ? raw[c0 * kTuRows + r] : 0.0;
+            const double x1 = c1 < kx ? raw[c1 * kTuRows + r] : 0.0;
+            uint32_t d0[kTcSlices], d1[kTcSlices];
+            tc_slice(x0, eb + cshift[min(c0, kx - 1)], d0);
+            tc_slice(x1, eb + cshift[min(c1, kx - 1)], d1);
+            tc_pack(d0, d1, xu[tu_xunit(r, 0, w)], xu[tu_xunit(r, 1, w)]);
         }
         __syncthreads();
         // the raw tile is free: the next chunk streams in during the MMAs
         if (ci + G < nchunks) {
-            stage_chunk_async<double>(Q, ldq, k, V, ldv, 0, kx, (ci + G) * kTuRows, kTuRows, n, raw);
+            tc_stage64(Q, ldq, k, V, ldv, kx, (ci + G) * kTuRows, n, raw);
             cp_async_commit();
         }
         // 3. digit products and the outputs of this warp's tiles
@@ -223,14 +215,14 @@ __device__ void update_tc_body(int64_t n, const double* __restrict__ Q, int64_t 
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const int r = m0 + gid + ((i & 2) ? 8 : 0);
+                const int ro = m0 + gid + ((i & 2) ? 8 : 0);
                 const int j = n0 + 2 * tig + (i & 1);
-                if (j >= nb || row0 + r >= n) continue;
+                if (j >= nb || row0 + ro >= n) continue;
                 const long long S = tc_combine(acc[0][i], acc[1][i], acc[2][i], acc[3][i], acc[4][i], acc[5][i],
                                                acc[6][i]);
-                const int er = rexp[r], fj = fexp[j];
-                V[(size_t)j * ldv + row0 + r] = max(er, fj) == kTcBadExp ? __longlong_as_double(0x7FF8000000000000ll)
-                                                                         : tc_scaled(S, er + fj - 52);
+                const int er = rexp[ro], fj = fexp[j];
+                V[(size_t)j * ldv + row0 + ro] = max(er, fj) == kTcBadExp ? __longlong_as_double(0x7FF8000000000000ll)
+                                                                          : tc_int_to_double(S, er + fj - 52);
             }
         }
     }

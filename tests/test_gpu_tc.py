@@ -180,9 +180,25 @@ def test_tc_breakdown_nan_and_repeatability(lib):
     n, k, nb = 100003, 20, 5
     Q = bo.hhqr(g.standard_normal((n, k)))[0]
     V = g.standard_normal((n, nb))
-    a = run_pip_tc(capi, Q, V)
-    b = run_pip_tc(capi, Q, V)
+    a = run_pip_tc(capi, Q, V, ld_pad=1)
+    b = run_pip_tc(capi, Q, V, ld_pad=1)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_tc_unaligned_columns_run_fp64(lib):
+    """An odd leading dimension leaves every other column off a 16-byte
+    boundary: the call runs the FP64 kernels (bit-identical to
+    ortho_gram_chol + ortho_update) instead of the 16-byte staged ones."""
+    from paper_2402_15033_gb300 import capi
+    g = synth.rng(13)
+    n, k, nb = 10001, 10, 5      # V's base stays aligned (k even), its odd columns do not
+    Q = bo.hhqr(g.standard_normal((n, k)))[0]
+    V = g.standard_normal((n, nb))
+    Vt, Rt, st = run_pip_tc(capi, Q, V, ld_pad=0)
+    assert st == 0
+    from test_gpu_ortho import run_pip
+    Vf, Rf, sf = run_pip(capi, Q, V, stage=1, ld_pad=0)
+    assert np.array_equal(Vt, Vf) and np.array_equal(Rt, Rf)
 
 
 def test_tc_two_stage_on_ill_conditioned_panels(lib):
