@@ -9,7 +9,10 @@ previous step's output, so every step does identical work on a 2 GB basis
 (16x the 129 MB L2: no step reads another's data from L2).
 
 value  = algorithmic HBM bytes of the step (8376 B per row)
-         / device time of the step  [GB/s], inputs resident in HBM;
+         / device time of the step  [GB/s], inputs resident in HBM.  The
+         headline step runs the exact-slice tensor-core arithmetic (FP64 in and
+         out, FP64-quality Gram and update); the same step on the FP64 pipe and
+         in double-float arithmetic is reported beside it (other_arith);
 e2e    = the same bytes / time with the basis copied in from pinned host
          memory and Q, R copied back, every step;
 roofline = the dominant kernel of the step, timed per launch with CUDA events
@@ -94,7 +97,20 @@ ARITH_TEXT = {"fp64": "FP64 pipe (native FP64 FMA)",
               "tc": "Gram and update on bf16 tensor cores by exact 8-bit slicing (FP64 quality)",
               "dd": "double-float (hi+lo FP32), ~2^-48 relative, FP64 in/out"}
 
+DTYPE_TEXT = {"fp64": "f64", "tc": "f64 in/out, products as exact bf16 digit slices", "dd": "f32x2 (double-float)"}
+
 FP64_PEAK_TFLOPS = 152 * 2070e6 * 2 * 2 / 1e12   # 2 FP64 FMA/clk/SM x 152 SMs x max clock
+
+
+# DRAM bytes per launch from one ncu capture at n = 1,048,576 (profiles/),
+# scaled by 4 to the benchmark's n (traffic grows with n): the last stage-1
+# block (k = 56) and the stage-2 panel.  Each equals the launch's algorithmic
+# bytes to within the writes still in L2 at the end of the capture.
+NCU_TRAFFIC = {
+    "tc": {"stage1_gram": 4 * (512.2 + 3.8) * 1e6, "stage1_update": 4 * (512.7 + 36.7) * 1e6,
+           "stage2_gram": 4 * (514.1 + 4.6) * 1e6, "stage2_update": 4 * (511.8 + 457.2) * 1e6},
+    "fp64": {"stage1_gram": 4 * (511.8 + 3.2) * 1e6, "stage2_gram": 4 * (514.7 + 3.5) * 1e6},
+}
 
 
 def roofline_of(d, kernel, arith):
@@ -107,15 +123,19 @@ def roofline_of(d, kernel, arith):
     tfl = d["flops"] / t / 1e12
     hbm = {"achieved_gbs": round(gbs, 1), "peak_gbs": peaks["hbm_gbs"], "frac": round(gbs / peaks["hbm_gbs"], 4),
            "peak_source": src}
+    traffic = NCU_TRAFFIC.get(arith, {}).get(kernel)
+    tnote = ("ncu DRAM read+write of the k=56 launch (stage 1) or the panel launch (stage 2), "
+             "captured at n=1,048,576 and scaled x4") if traffic else None
     if arith == "tc" and d.get("tensor_flops"):
         tt = d["tensor_flops"] / t / 1e12
         return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(gbs / peaks["hbm_gbs"], 4), "traffic": None, "kernel": kernel, "peak_source": src,
+                "frac": round(gbs / peaks["hbm_gbs"], 4), "traffic": traffic, "traffic_note": tnote,
+                "kernel": kernel, "peak_source": src,
                 "tensor": {"executed_tflops": round(tt, 2), "mma_sync_bf16_peak_tflops": MMA_SYNC_PEAK,
                            "frac": round(tt / MMA_SYNC_PEAK, 4),
                            "peak_source": "measured mma.sync m16n8k16 bf16 throughput on this GPU"}}
     return {"bound": "alu", "achieved": round(tfl, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-            "frac": round(tfl / FP64_PEAK_TFLOPS, 4), "traffic": None, "kernel": kernel,
+            "frac": round(tfl / FP64_PEAK_TFLOPS, 4), "traffic": traffic, "traffic_note": tnote, "kernel": kernel,
             "peak_source": "FP64 FMA pipe: 2/clk/SM x 152 SMs x 2070 MHz", "hbm": hbm}
 
 
@@ -439,7 +459,7 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_TEXT[args.arith], "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n": n, "cols": NCOL, "s": S, "panel": NCOL - 1,
                            "bytes_per_step": bytes_step, "l2": "basis 2 GB >> 129 MB L2, no flush needed",
                            "parallelism": "replicas" if world > 1 else "single"},
@@ -678,7 +698,7 @@ def main():
     ap.add_argument("--no-patterns", action="store_true", help="skip the mixed, batched and serving configurations")
     ap.add_argument("--no-dd", action="store_true", help="skip the double-float measurement")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core Gram measurement")
-    ap.add_argument("--arith", default="fp64", choices=["fp64", "tc", "dd"],
+    ap.add_argument("--arith", default="tc", choices=["fp64", "tc", "dd"],
                     help="arithmetic of the headline step (the others are reported beside it)")
     ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--batch-nmax", type=float, default=5e5)
