@@ -497,25 +497,50 @@ def solver_numbers(capi, dev, args):
     S1.close()
     out["laplace64_fp64"] = {"time_to_solution_ms": round(1e3 * statistics.median(times), 3), "status": rc,
                              "iters": res["iters"], "relres": res["relres_true"]}
-    # 2048 x 2048 Laplace: one restart cycle (60 iterations), per-phase times
+    # the same with the tensor-core arithmetic
+    S1 = capi.Solver.from_csr(A, capi.default_opts(m=60, s=5, panel=60, tol=1e-8, arith=capi.GMRES_ARITH_TC))
+    S1.solve(bd, xd)
+    times = []
+    for _ in range(5):
+        xd.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, res = S1.solve(bd, xd)
+        times.append(time.perf_counter() - t0)
+    S1.close()
+    out["laplace64_tc"] = {"time_to_solution_ms": round(1e3 * statistics.median(times), 3), "status": rc,
+                           "iters": res["iters"], "relres": res["relres_true"]}
+    # 2048 x 2048 Laplace: one restart cycle (60 iterations), per-phase times, for
+    # the two-stage scheme and the paper's one-stage comparisons (BCGS-PIP2 and the
+    # BCGS2-CholQR2 baseline of §VIII), FP64 and tensor-core arithmetic
     if args.rows == N_ROWS:
         A = synth.laplace2d(2048)
         xt = synth.x_true(A.n, 0)
         b = csr_matrix((A.vals, A.colind, A.rowptr), shape=(A.n, A.n)) @ xt
-        opts = capi.default_opts(m=60, s=5, panel=60, tol=1e-14, max_restarts=1, timing=1)
-        S2 = capi.Solver.from_csr(A, opts)
         bd = torch.tensor(b, device=dev)
         xd = torch.zeros(A.n, dtype=torch.float64, device=dev)
-        S2.solve(bd, xd)
-        xd.zero_()
-        rc, res = S2.solve(bd, xd)
-        S2.close()
-        cyc = res["t_total_ms"]
-        out["laplace2048_fp64_cycle"] = {"ms_per_restart_cycle": round(cyc, 3), "iters": res["iters"],
-                                         "iters_per_s": round(res["iters"] / (cyc * 1e-3), 1),
-                                         "t_mpk_ms": round(res["t_mpk_ms"], 3), "t_stage1_ms": round(res["t_stage1_ms"], 3),
-                                         "t_stage2_ms": round(res["t_stage2_ms"], 3), "t_ls_ms": round(res["t_ls_ms"], 3),
-                                         "relres_after_one_cycle": res["relres_true"], "status": rc}
+        schemes = [("two_stage", capi.GMRES_ORTHO_TWO_STAGE), ("bcgs_pip2", capi.GMRES_ORTHO_BCGS_PIP2),
+                   ("bcgs2_cholqr2", capi.GMRES_ORTHO_BCGS2_CHOLQR2)]
+        cycles = {}
+        for name, ortho in schemes:
+            for aname, arith in (("fp64", capi.GMRES_ARITH_FP64), ("tc", capi.GMRES_ARITH_TC)):
+                opts = capi.default_opts(m=60, s=5, panel=60, tol=1e-14, max_restarts=1, timing=1, ortho=ortho,
+                                         arith=arith)
+                S2 = capi.Solver.from_csr(A, opts)
+                S2.solve(bd, xd)
+                xd.zero_()
+                rc, res = S2.solve(bd, xd)
+                S2.close()
+                cyc = res["t_total_ms"]
+                cycles[f"{name}_{aname}"] = {
+                    "ms_per_restart_cycle": round(cyc, 3), "iters": res["iters"],
+                    "iters_per_s": round(res["iters"] / (cyc * 1e-3), 1), "t_mpk_ms": round(res["t_mpk_ms"], 3),
+                    "t_stage1_ms": round(res["t_stage1_ms"], 3), "t_stage2_ms": round(res["t_stage2_ms"], 3),
+                    "t_ls_ms": round(res["t_ls_ms"], 3), "relres_after_one_cycle": res["relres_true"], "status": rc}
+        out["laplace2048_cycle"] = cycles
+        base = cycles["bcgs2_cholqr2_fp64"]["ms_per_restart_cycle"]
+        out["laplace2048_speedup_vs_bcgs2_cholqr2_fp64"] = {
+            k: round(base / v["ms_per_restart_cycle"], 3) for k, v in cycles.items()}
     return out
 
 

@@ -43,6 +43,9 @@ extern "C" {
 /* ---------------------------------------------------------------- options */
 #define GMRES_ORTHO_TWO_STAGE      0  /* §V, Fig. 5: BCGS-PIP per block + BCGS-PIP per big panel   */
 #define GMRES_ORTHO_BCGS_PIP2      1  /* §IV-C, Fig. 4b: the two-stage scheme with panel = s (§V)  */
+#define GMRES_ORTHO_BCGS2_CHOLQR2  2  /* §IV-B, Fig. 2b with CholQR2 (the paper's baseline): per   */
+                                      /* block BCGS, CholQR2, BCGS, CholQR = five reductions;      */
+                                      /* panel = s.  Single-system solver and server only.         */
 #define GMRES_PREC_FP64            0  /* everything FP64                                          */
 #define GMRES_PREC_MIXED           1  /* FP32 basis + MPK, FP64 Gram/Cholesky/Hessenberg, FP64 IR */
 #define GMRES_BASIS_MONOMIAL       0  /* §VI: monomial basis (scaled by a power of two)           */

@@ -26,6 +26,7 @@ GMRES_ERR_WORKSPACE = -7
 
 GMRES_ORTHO_TWO_STAGE = 0
 GMRES_ORTHO_BCGS_PIP2 = 1
+GMRES_ORTHO_BCGS2_CHOLQR2 = 2
 GMRES_PREC_FP64 = 0
 GMRES_PREC_MIXED = 1
 GMRES_BASIS_MONOMIAL = 0

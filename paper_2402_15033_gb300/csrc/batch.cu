@@ -548,6 +548,8 @@ int gmres_batch_create(gmres_batch** out, int32_t nsys, const int64_t* n, const 
     GM_ARG(o.tol > 0.0 && o.max_restarts >= 1, "bad tol / max_restarts");
     GM_ARG(o.arith == GMRES_ARITH_FP64 || o.arith == GMRES_ARITH_DD,
            "arith must be GMRES_ARITH_FP64 or GMRES_ARITH_DD for batches");
+    GM_ARG(o.ortho == GMRES_ORTHO_TWO_STAGE || o.ortho == GMRES_ORTHO_BCGS_PIP2,
+           "ortho must be GMRES_ORTHO_TWO_STAGE or GMRES_ORTHO_BCGS_PIP2 for batches");
     gmres_batch* c = new gmres_batch();
     c->opts = o;
     c->nsys = nsys;

@@ -11,6 +11,13 @@ __global__ void __launch_bounds__(256) hessenberg_ls_kernel(DevState* st, int lo
     hessenberg_ls_body(st, lo, t);
 }
 
+__global__ void __launch_bounds__(256) bcgs2_combine_kernel(const DevState* st, int k, int s, const double* S,
+                                                            double* R) {
+    bcgs2_combine_body(st, k, s, S, R);
+}
+
+__global__ void __launch_bounds__(256) eye_panel_kernel(DevState* st, int lo, int t) { eye_panel_body(st, lo, t); }
+
 }  // namespace
 
 cudaError_t launch_cycle_begin(cudaStream_t st, DevState* ds) {
@@ -20,6 +27,16 @@ cudaError_t launch_cycle_begin(cudaStream_t st, DevState* ds) {
 
 cudaError_t launch_hessenberg_ls(cudaStream_t st, DevState* ds, int lo, int t) {
     hessenberg_ls_kernel<<<1, 256, 0, st>>>(ds, lo, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bcgs2_combine(cudaStream_t st, const DevState* ds, int k, int s, const double* S, double* R) {
+    bcgs2_combine_kernel<<<1, 256, 0, st>>>(ds, k, s, S, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eye_panel(cudaStream_t st, DevState* ds, int lo, int t) {
+    eye_panel_kernel<<<1, 256, 0, st>>>(ds, lo, t);
     return cudaGetLastError();
 }
 

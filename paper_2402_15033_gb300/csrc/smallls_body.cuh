@@ -123,4 +123,50 @@ __device__ inline void hessenberg_ls_body(DevState* st, int lo, int t) {
     }
 }
 
+// BCGS2-CholQR2 block factor (§IV-B, Fig. 2b with CholQR2): from the five
+// reductions' factors in scratch blocks of leading dimension kLsLd
+//   S0 = P1 (k x s: first projection), S1 = T1a, S2 = T1b (CholQR2 of the
+//   projected block, T1 = T1b T1a), S3 = P2 (second projection), S4 = T2,
+// write R = [P1 + P2 T1; T2 T1] into the block column R (rows 0 .. k+s-1).
+__device__ inline void bcgs2_combine_body(const DevState* st, int k, int s, const double* S, double* R) {
+    __shared__ double T1[16 * 16];
+    if (st->done) return;
+    const int tid = threadIdx.x;
+    const double* P1 = S;
+    const double* T1a = S + kLsLd * kLsLd;
+    const double* T1b = S + 2 * kLsLd * kLsLd;
+    const double* P2 = S + 3 * kLsLd * kLsLd;
+    const double* T2 = S + 4 * kLsLd * kLsLd;
+    for (int e = tid; e < s * s; e += blockDim.x) {          // T1 = T1b T1a (upper triangular)
+        const int i = e % s, j = e / s;
+        double acc = 0.0;
+        for (int l = i; l <= j; ++l) acc = fma(T1b[i + l * kLsLd], T1a[l + j * kLsLd], acc);
+        T1[i + j * 16] = i <= j ? acc : 0.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < (k + s) * s; e += blockDim.x) {
+        const int i = e % (k + s), j = e / (k + s);
+        double acc;
+        if (i < k) {
+            acc = P1[i + j * kLsLd];
+            for (int l = 0; l <= j; ++l) acc = fma(P2[i + l * kLsLd], T1[l + j * 16], acc);
+        } else {
+            const int ii = i - k;
+            acc = 0.0;
+            for (int l = ii; l <= j; ++l) acc = fma(T2[ii + l * kLsLd], T1[l + j * 16], acc);
+        }
+        R[i + j * kLsLd] = acc;
+    }
+}
+
+// Stage-2 factor of a one-stage scheme whose blocks come out final: the
+// identity on the panel's columns [lo, t] (no projection part).
+__device__ inline void eye_panel_body(DevState* st, int lo, int t) {
+    if (st->done) return;
+    for (int e = threadIdx.x; e < (t + 1) * (t - lo + 1); e += blockDim.x) {
+        const int i = e % (t + 1), c = lo + e / (t + 1);
+        st->Cm[i + c * kLsLd] = i == c ? 1.0 : 0.0;
+    }
+}
+
 }  // namespace gm

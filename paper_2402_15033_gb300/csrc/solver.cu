@@ -79,6 +79,7 @@ struct gmres_ctx {
     unsigned* red_counter = nullptr;
     void* pip_work = nullptr;
     size_t pip_bytes = 0;
+    double* bscr = nullptr;      // BCGS2-CholQR2: the five reductions' factors (5 x kMaxCols^2)
     DevState* st = nullptr;      // device
     DevState* hst = nullptr;     // pinned host mirror
     std::vector<cudaEvent_t> ev;
@@ -149,6 +150,7 @@ size_t ctx_bytes(int64_t n, int64_t nnz, const gmres_opts& o) {
     if (mixed) b += up(nz * 4) + up(ldq * 8);
     b += up((size_t)(o.m + 1) * ldq * esz) + 2 * up(ldq * 8);
     b += up(norm_grid(n) * 8) + up(256) + up(pip_bytes_for(n, o)) + up(sizeof(DevState)) + up(16);
+    if (o.ortho == GMRES_ORTHO_BCGS2_CHOLQR2) b += up(5 * (size_t)kMaxCols * kMaxCols * sizeof(double));
     return b;
 }
 
@@ -160,10 +162,12 @@ static int check_opts(const gmres_opts* o) {
     GM_ARG(o->s >= 1 && o->s <= 16, "s must be in [1, 16]");
     GM_ARG(o->tol > 0.0, "tol must be positive");
     GM_ARG(o->max_restarts >= 1, "max_restarts must be >= 1");
-    GM_ARG(o->ortho == GMRES_ORTHO_TWO_STAGE || o->ortho == GMRES_ORTHO_BCGS_PIP2, "unknown ortho");
+    GM_ARG(o->ortho == GMRES_ORTHO_TWO_STAGE || o->ortho == GMRES_ORTHO_BCGS_PIP2 ||
+               o->ortho == GMRES_ORTHO_BCGS2_CHOLQR2,
+           "unknown ortho");
     GM_ARG(o->precision == GMRES_PREC_FP64 || o->precision == GMRES_PREC_MIXED, "unknown precision");
     GM_ARG(o->basis == GMRES_BASIS_MONOMIAL || o->basis == GMRES_BASIS_NEWTON, "unknown basis");
-    const int panel = o->ortho == GMRES_ORTHO_BCGS_PIP2 ? o->s : o->panel;
+    const int panel = o->ortho != GMRES_ORTHO_TWO_STAGE ? o->s : o->panel;
     GM_ARG(panel >= o->s && panel % o->s == 0 && o->m % panel == 0, "need s | panel | m");
     GM_ARG(o->sigma >= 0.0 && std::isfinite(o->sigma), "sigma must be >= 0");
     GM_ARG(o->arith == GMRES_ARITH_DD || o->arith == GMRES_ARITH_FP64 || o->arith == GMRES_ARITH_TC,
@@ -187,6 +191,7 @@ int gmres_destroy(gmres_ctx* c) {
     cudaFree(c->red_partial);
     cudaFree(c->red_counter);
     cudaFree(c->pip_work);
+    cudaFree(c->bscr);
     cudaFree(c->st);
     cudaFreeHost(c->hst);
     delete c;
@@ -215,7 +220,7 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
     GM_ARG(rowptr != nullptr && (nnz == 0 || (colind != nullptr && vals != nullptr)), "NULL CSR array");
     gmres_opts o;
     if (opts) o = *opts; else gmres_default_opts(&o);
-    if (o.ortho == GMRES_ORTHO_BCGS_PIP2) o.panel = o.s;
+    if (o.ortho != GMRES_ORTHO_TWO_STAGE) o.panel = o.s;
     {
         int rc = check_opts(&o);
         if (rc) return rc;
@@ -313,6 +318,11 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
     c->pip_bytes = wb;
     CK(cuda_rc(cudaMalloc(&c->pip_work, wb), "cudaMalloc workspace"));
     CK(cuda_rc(cudaMemsetAsync(c->pip_work, 0, wb, s), "memset workspace"));
+    if (o.ortho == GMRES_ORTHO_BCGS2_CHOLQR2) {
+        const size_t sb = 5 * (size_t)kMaxCols * kMaxCols * sizeof(double);
+        CK(cuda_rc(cudaMalloc(&c->bscr, sb), "cudaMalloc bcgs2 scratch"));
+        CK(cuda_rc(cudaMemsetAsync(c->bscr, 0, sb, s), "memset bcgs2 scratch"));
+    }
     CK(cuda_rc(cudaMalloc(&c->st, sizeof(DevState)), "cudaMalloc state"));
     CK(cuda_rc(cudaMallocHost(&c->hst, sizeof(DevState)), "cudaMallocHost state"));
     std::memset(c->hst, 0, sizeof(DevState));
@@ -370,7 +380,30 @@ static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
             T* V = basis + (size_t)k * c->ldq;
             double* R = ds->Rhat + (size_t)k * kMaxCols;
             int32_t* stat = &ds->blkstat[j];
-            if (sizeof(T) == sizeof(double)) {
+            if (o.ortho == GMRES_ORTHO_BCGS2_CHOLQR2) {
+                // BCGS2-CholQR2 (§IV-B, Fig. 2b): BCGS, CholQR2, BCGS, CholQR, five
+                // reductions; the factors go to scratch blocks, their product to R
+                const int grid = reduction_grid(c->n);
+                const size_t SB = (size_t)kMaxCols * kMaxCols;
+                double* S = c->bscr;
+                PipWork w0 = pip_work_layout(c->pip_work, c->n, 0, o.s);
+                struct Step { int kk; double* R; int gmode; int umode; };
+                const Step steps[5] = {{k, S, kPipGramOnly, kPipNoTrsm},     // P1, V <- V - Q P1
+                                       {0, S + SB, 0, 0},                    // T1a, V <- V T1a^{-1}
+                                       {0, S + 2 * SB, 0, 0},                // T1b, V <- V T1b^{-1}
+                                       {k, S + 3 * SB, kPipGramOnly, kPipNoTrsm},   // P2
+                                       {0, S + 4 * SB, 0, 0}};               // T2
+                for (int q = 0; q < 5 && e == cudaSuccess; ++q) {
+                    const Step& st_ = steps[q];
+                    const PipWork& wq = st_.kk ? w : w0;
+                    e = launch_pip_gram_chol(s, c->n, basis, c->ldq, st_.kk, V, c->ldq, o.s, st_.R, kMaxCols, wq, stat,
+                                             done, grid, st_.gmode, o.arith);
+                    if (e == cudaSuccess)
+                        e = launch_pip_update(s, c->n, basis, c->ldq, st_.kk, V, c->ldq, o.s, st_.R, kMaxCols, stat,
+                                              done, st_.umode, o.arith);
+                }
+                if (e == cudaSuccess) e = launch_bcgs2_combine(s, ds, k, o.s, S, R);
+            } else if (sizeof(T) == sizeof(double)) {
                 // BCGS-PIP (Fig. 4a): one reduction, Pythagorean Gram
                 e = launch_pip_gram_chol(s, c->n, basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, w, stat, done,
                                          reduction_grid(c->n), 0, o.arith);
@@ -406,12 +439,17 @@ static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
             T* V = basis + (size_t)lo * c->ldq;
             double* R = ds->Cm + (size_t)lo * kMaxCols;
             int32_t* stat = &ds->blkstat[nblk + panel_idx];
-            if (e == cudaSuccess)
-                e = launch_pip_gram_chol(s, c->n, basis, c->ldq, lo, V, c->ldq, np, R, kMaxCols, w, stat, done,
-                                         reduction_grid(c->n), 0, o.arith);
-            if (e == cudaSuccess)
-                e = launch_pip_update(s, c->n, basis, c->ldq, lo, V, c->ldq, np, R, kMaxCols, stat, done, 0,
-                                      o.arith);
+            if (o.ortho == GMRES_ORTHO_BCGS2_CHOLQR2) {
+                // the block is final after its five reductions: identity stage-2 factor
+                if (e == cudaSuccess) e = launch_eye_panel(s, ds, lo, t);
+            } else {
+                if (e == cudaSuccess)
+                    e = launch_pip_gram_chol(s, c->n, basis, c->ldq, lo, V, c->ldq, np, R, kMaxCols, w, stat, done,
+                                             reduction_grid(c->n), 0, o.arith);
+                if (e == cudaSuccess)
+                    e = launch_pip_update(s, c->n, basis, c->ldq, lo, V, c->ldq, np, R, kMaxCols, stat, done, 0,
+                                          o.arith);
+            }
             if (e == cudaSuccess) e = mark(PH_S2);
             if (e == cudaSuccess) e = mark(PH_LS);
             if (e == cudaSuccess) e = launch_hessenberg_ls(s, ds, lo, t);
@@ -587,7 +625,7 @@ size_t gmres_footprint(int64_t n, int64_t nnz, const gmres_opts* opts) {
     if (n <= 0 || nnz < 0) return 0;
     gmres_opts o;
     if (opts) o = *opts; else gmres_default_opts(&o);
-    if (o.ortho == GMRES_ORTHO_BCGS_PIP2) o.panel = o.s;
+    if (o.ortho != GMRES_ORTHO_TWO_STAGE) o.panel = o.s;
     if (check_opts(&o)) return 0;
     return ctx_bytes(n, nnz, o);
 }

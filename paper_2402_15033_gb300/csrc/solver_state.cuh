@@ -61,5 +61,9 @@ cudaError_t launch_rowabs(cudaStream_t st, const DevCSR& A, unsigned long long* 
 cudaError_t launch_rowptr_narrow(cudaStream_t st, int64_t m, const int64_t* in, int32_t* out);
 cudaError_t launch_cycle_begin(cudaStream_t st, DevState* ds);
 cudaError_t launch_hessenberg_ls(cudaStream_t st, DevState* ds, int lo, int t);
+// BCGS2-CholQR2 block factor from the five reductions' factors (S: 5 blocks of kMaxCols^2)
+cudaError_t launch_bcgs2_combine(cudaStream_t st, const DevState* ds, int k, int s, const double* S, double* R);
+// identity stage-2 factor on the panel [lo, t] (one-stage schemes)
+cudaError_t launch_eye_panel(cudaStream_t st, DevState* ds, int lo, int t);
 
 }  // namespace gm

@@ -27,6 +27,8 @@ def check_against_oracle(capi, A, b, m, s, panel, ortho="two_stage", tol=1e-8, a
     kw = dict(m=m, s=s, panel=panel, tol=tol, arith=arith)
     if ortho == "bcgs_pip2":
         kw["ortho"] = capi.GMRES_ORTHO_BCGS_PIP2
+    elif ortho == "bcgs2_cholqr2":
+        kw["ortho"] = capi.GMRES_ORTHO_BCGS2_CHOLQR2
     rc, res, x = solve_gpu(capi, A, b, **kw)
     xr, info = kr.sstep_gmres(A, b, m=m, s=s, panel=panel, tol=tol, ortho=ortho)
     if info["status"] == kr.STATUS_BREAKDOWN:
@@ -76,6 +78,25 @@ def test_bcgs_pip2_mode_matches_oracle(lib):
     b = kr.as_operator(A) @ synth.x_true(A.n, 4)
     rc, res, info = check_against_oracle(capi, A, b, 60, 5, 5, ortho="bcgs_pip2")
     assert rc == 0
+
+
+@pytest.mark.parametrize("N,m,s,arith", [(48, 60, 5, 0), (40, 30, 5, 2), (33, 24, 4, 0)])
+def test_bcgs2_cholqr2_mode_matches_oracle(lib, N, m, s, arith):
+    """The paper's baseline scheme (§IV-B, Fig. 2b with CholQR2: BCGS, CholQR2,
+    BCGS, CholQR per block, five reductions) on the GPU against the oracle's
+    bcgs2_cholqr2 arm: same status, x within 1e-6, iterations within s."""
+    from paper_2402_15033_gb300 import capi
+    A = synth.laplace2d(N)
+    b = kr.as_operator(A) @ synth.x_true(A.n, 5)
+    rc, res, info = check_against_oracle(capi, A, b, m, s, s, ortho="bcgs2_cholqr2", arith=arith)
+    assert rc == 0
+
+
+def test_bcgs2_cholqr2_nonsymmetric_matches_oracle(lib):
+    from paper_2402_15033_gb300 import capi
+    A = synth.convdiff2d(40, 7)
+    b = kr.as_operator(A) @ synth.x_true(A.n, 6)
+    check_against_oracle(capi, A, b, 30, 5, 5, ortho="bcgs2_cholqr2")
 
 
 @pytest.mark.parametrize("gen,seed,m,s,panel", [("convdiff2d", 3, 30, 5, 30), ("convdiff2d", 11, 60, 5, 60),
