@@ -94,7 +94,8 @@ def tc_update_mma_flops(n, k, nb):
 
 
 ARITH_TEXT = {"fp64": "FP64 pipe (native FP64 FMA)",
-              "tc": "Gram and update on bf16 tensor cores by exact 8-bit slicing (FP64 quality)",
+              "tc": "Gram and update on bf16 tensor cores by exact 8-bit slicing (FP64 quality); "
+                    "resident digit basis: each column sliced once",
               "dd": "double-float (hi+lo FP32), ~2^-48 relative, FP64 in/out"}
 
 DTYPE_TEXT = {"fp64": "f64", "tc": "f64 in/out, products as exact bf16 digit slices", "dd": "f32x2 (double-float)"}
@@ -286,11 +287,16 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev).cuda_stream
 
     grams = {"fp64": capi.ortho_gram_chol, "dd": capi.ortho_gram_chol_dd, "tc": capi.ortho_gram_chol_tc}
+    # digit basis of the tensor-core step: every column is sliced once (column 0
+    # by a fill, each block by its update) and read back by the later Grams
+    CAPC = 64
+    digits = torch.empty(capi.digits_bytes(n, CAPC), dtype=torch.uint8, device=dev)
 
     def make_step(arith):
         gram = grams[arith]
         dd = arith == "dd"
         tc = arith == "tc"
+        tcd = tc and not args.no_digits
 
         def step(evs=None):
             def mark():
@@ -304,15 +310,26 @@ def run_ours(args):
                 V = B[:, k:k + S]
                 Rb = Rh[:k + S, k:k + S]
                 e0 = mark()
-                gram(Q, V, Rb, work, st[j:j + 1], k=k, stream=stream)
+                if tcd:
+                    if j == 0:
+                        capi.digits_fill(B[:, :1], 0, digits, CAPC, stream=stream)
+                    capi.ortho_gram_chol_tcd(Q, V, Rb, work, st[j:j + 1], digits, CAPC, k, k=k, stream=stream)
+                else:
+                    gram(Q, V, Rb, work, st[j:j + 1], k=k, stream=stream)
                 e1 = mark()
-                capi.ortho_update(Q, V, Rb, st[j:j + 1], k=k, stream=stream, dd=dd, tc=tc)
+                if tcd:
+                    capi.ortho_update_tcd(Q, V, Rb, st[j:j + 1], digits, CAPC, k=k, stream=stream)
+                else:
+                    capi.ortho_update(Q, V, Rb, st[j:j + 1], k=k, stream=stream, dd=dd, tc=tc)
                 e2 = mark()
                 if evs is not None:
                     evs.append(("stage1_gram", k, S, e0, e1))
                     evs.append(("stage1_update", k, S, e1, e2))
             e0 = mark()
-            gram(None, B, R2, work, st[NBLK:], k=0, stream=stream)
+            if tcd:
+                capi.ortho_gram_chol_tcd(None, B, R2, work, st[NBLK:], digits, CAPC, NCOL, k=0, stream=stream)
+            else:
+                gram(None, B, R2, work, st[NBLK:], k=0, stream=stream)
             e1 = mark()
             capi.ortho_update(None, B, R2, st[NBLK:], k=0, stream=stream, dd=dd, tc=tc)
             e2 = mark()
@@ -465,7 +482,9 @@ def run_ours(args):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "arith": ARITH_TEXT[args.arith], "roofline": roofline, "kernels": families,
                 "other_arith": others, "e2e": e2e, "cpu_baseline": cpu,
-                "gpu_launches": (2 * NBLK + 2) * args.steps, "clocks": clk, "solver": solve,
+                "gpu_launches": (2 * NBLK + 2 + (1 if args.arith == "tc" and not args.no_digits else 0)) * args.steps,
+                "clocks": clk,
+                "solver": solve,
                 "patterns": patterns}
         print(json.dumps(line))
     if world > 1:
@@ -723,6 +742,8 @@ def main():
     ap.add_argument("--no-patterns", action="store_true", help="skip the mixed, batched and serving configurations")
     ap.add_argument("--no-dd", action="store_true", help="skip the double-float measurement")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core Gram measurement")
+    ap.add_argument("--no-digits", action="store_true",
+                    help="tensor-core step without the resident digit basis (every read re-slices)")
     ap.add_argument("--arith", default="tc", choices=["fp64", "tc", "dd"],
                     help="arithmetic of the headline step (the others are reported beside it)")
     ap.add_argument("--batch-systems", type=int, default=256)

@@ -240,6 +240,39 @@ int ortho_update_tc(void* stream, int64_t n, const double* Q, int64_t ldq, int32
                     double* V, int64_t ldv, int32_t nb, const double* R, int32_t ldr,
                     const int32_t* d_status);
 
+/* Digit basis: the seven digit slices that the tensor-core arithmetic makes of
+ * every FP64 value (per 64-row chunk of a column), kept in device memory so that
+ * a basis column is sliced once however many blocks later read it (stage 1
+ * projects every block against all accumulated columns, §V).  No counterpart in
+ * the paper; results are bit-identical to the ortho_*_tc calls.
+ *   ortho_digits_bytes: size of a digit basis of capc columns for n rows
+ *                       (about 14 bytes per value); capc <= 64.
+ *   ortho_digits_fill:  slice X(:, 0:nc) into digit columns c0 .. c0+nc-1.
+ *   ortho_gram_chol_tcd: ortho_gram_chol_tc whose first kc columns of [Q, V]
+ *                       (kc <= k + nb) are read from digit columns 0 .. kc-1,
+ *                       which must hold exactly those columns' current values.
+ *   ortho_update_tcd:   ortho_update_tc that also writes the digits of the new V
+ *                       into digit columns k .. k+nb-1; for nb <= 8 it reads Q's
+ *                       digits from digit columns 0 .. k-1 (which must hold Q)
+ *                       instead of slicing Q's rows, so results agree with
+ *                       ortho_update_tc to rounding (not bit for bit).
+ * Q, V and X columns must start on 16-byte boundaries (ld even); k + nb <= 64;
+ * k + nb <= capc.  The digit buffer (d_digits) is owned by the caller, 16-byte
+ * aligned, and may not be shared by calls that overlap on the GPU. */
+size_t ortho_digits_bytes(int64_t n, int32_t capc);
+
+int ortho_digits_fill(void* stream, int64_t n, const double* X, int64_t ldx, int32_t c0, int32_t nc,
+                      void* d_digits, int32_t capc);
+
+int ortho_gram_chol_tcd(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
+                        const double* V, int64_t ldv, int32_t nb, double* R, int32_t ldr,
+                        void* d_work, size_t work_bytes, int32_t* d_status,
+                        const void* d_digits, int32_t capc, int32_t kc);
+
+int ortho_update_tcd(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
+                     double* V, int64_t ldv, int32_t nb, const double* R, int32_t ldr,
+                     const int32_t* d_status, void* d_digits, int32_t capc);
+
 /* ------------------------------------------------ batched solver (many uneven systems)
  * nsys independent systems of different sizes and matrices share one set of
  * options (m, s, panel, tol, precision) and advance together: one restart

@@ -84,6 +84,11 @@ SIGNATURES = {
     "ortho_gram_chol_dd": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "ortho_gram_chol_tc": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "ortho_update_tc": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp]),
+    "ortho_digits_bytes": (_sz, [_i64, _i32]),
+    "ortho_digits_fill": (_i32, [_vp, _i64, _vp, _i64, _i32, _i32, _vp, _i32]),
+    "ortho_gram_chol_tcd": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp,
+                                   _vp, _i32, _i32]),
+    "ortho_update_tcd": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _vp, _i32]),
     "ortho_update_dd": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp]),
     "ortho_stage1_f32": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "ortho_stage2_f32": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
@@ -368,6 +373,44 @@ def ortho_update(Q, V, R, status, k=None, stream=None, dd=False, tc=False):
     return check(fn(C.c_void_p(stream or 0), int(n), qp, int(ldq), int(k),
                                      C.c_void_p(V.data_ptr()), int(V.stride(1)), int(nb),
                                      C.c_void_p(R.data_ptr()), int(R.stride(1)), C.c_void_p(status.data_ptr())))
+
+
+def digits_bytes(n, capc):
+    """Bytes of a digit basis of capc columns for n rows (about 14 per value)."""
+    return int(load().ortho_digits_bytes(int(n), int(capc)))
+
+
+def digits_fill(X, c0, digits, capc, stream=None):
+    """Slice the columns of X (column-major CUDA tensor view) into digit columns c0 ..."""
+    n, nc = X.shape
+    return check(load().ortho_digits_fill(C.c_void_p(stream or 0), int(n), C.c_void_p(X.data_ptr()),
+                                          int(X.stride(1)), int(c0), int(nc), C.c_void_p(digits.data_ptr()),
+                                          int(capc)))
+
+
+def ortho_gram_chol_tcd(Q, V, R, work, status, digits, capc, kc, k=None, stream=None):
+    """ortho_gram_chol_tc reading the first kc columns of [Q, V] from the digit basis."""
+    k = (Q.shape[1] if Q is not None else 0) if k is None else k
+    n, nb = V.shape
+    ldq = Q.stride(1) if (Q is not None and k > 0) else n
+    qp = C.c_void_p(Q.data_ptr()) if (Q is not None and k > 0) else None
+    return check(load().ortho_gram_chol_tcd(C.c_void_p(stream or 0), int(n), qp, int(ldq), int(k),
+                                            C.c_void_p(V.data_ptr()), int(V.stride(1)), int(nb),
+                                            C.c_void_p(R.data_ptr()), int(R.stride(1)), C.c_void_p(work.data_ptr()),
+                                            int(work.numel() * work.element_size()), C.c_void_p(status.data_ptr()),
+                                            C.c_void_p(digits.data_ptr()), int(capc), int(kc)))
+
+
+def ortho_update_tcd(Q, V, R, status, digits, capc, k=None, stream=None):
+    """ortho_update_tc that also writes the new V's digits into digit columns k .. k+nb-1."""
+    k = (Q.shape[1] if Q is not None else 0) if k is None else k
+    n, nb = V.shape
+    ldq = Q.stride(1) if (Q is not None and k > 0) else n
+    qp = C.c_void_p(Q.data_ptr()) if (Q is not None and k > 0) else None
+    return check(load().ortho_update_tcd(C.c_void_p(stream or 0), int(n), qp, int(ldq), int(k),
+                                         C.c_void_p(V.data_ptr()), int(V.stride(1)), int(nb),
+                                         C.c_void_p(R.data_ptr()), int(R.stride(1)), C.c_void_p(status.data_ptr()),
+                                         C.c_void_p(digits.data_ptr()), int(capc)))
 
 
 def ortho_stage1_noalloc(Q, V, R, status, k=None, stream=None):

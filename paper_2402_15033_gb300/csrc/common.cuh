@@ -69,6 +69,20 @@ cudaError_t launch_pip_update(cudaStream_t st, int64_t n,
                               const double* R, int ldr, const int32_t* d_status,
                               const int32_t* d_skip, int mode = 0, int arith = kArithFP64);
 
+// Tensor-core halves with a digit basis (the seven digit slices of basis
+// columns kept in HBM, tc_common.cuh): the Gram reads the first kc columns of
+// [Q, V] from it; the update writes the new columns' digits into columns
+// k .. k+nb-1; the fill slices X(:, 0:nc) into columns c0 ...  Columns of Q, V
+// and X must start on 16-byte boundaries; k + nb <= 64.
+cudaError_t launch_gram_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, const double* V,
+                                  int64_t ldv, int nb, double* R, int ldr, const PipWork& w, int32_t* d_status,
+                                  int grid, const void* digits, int capc, int kc);
+cudaError_t launch_update_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, double* V,
+                                    int64_t ldv, int nb, const double* R, int ldr, const int32_t* d_status,
+                                    void* digits, int capc);
+cudaError_t launch_digits_fill_cols(cudaStream_t st, int64_t n, const double* X, int64_t ldx, int c0, int nc,
+                                    void* digits, int capc);
+
 }  // namespace gm
 
 #define GM_CUDA_RET(call)                                                              \

@@ -60,11 +60,14 @@ __host__ __device__ inline int tc_tile_count(int k, int nb) {
 }
 
 // One virtual CTA's partial block of [Q(:, 0:k), V(:, 0:nb)]^T V(:, 0:nb) over
-// the 64-row chunks b, b+G, ...; entry (c, j) goes to slot[c * nb + j].
-// 256 threads (8 warps); k + nb <= 64; dynamic shared memory gram_tc_smem(k + nb).
+// the 64-row chunks b, b+G, ...; entry (c, j) goes to slot[c * nb + j].  The
+// first kc columns of [Q, V] may come from a digit basis (dig, dex, capc:
+// tc_digits_store) instead of being staged and sliced.  256 threads (8 warps);
+// k + nb <= 64; dynamic shared memory gram_tc_smem(k + nb).
 __device__ void gram_tc_part(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
                              const double* __restrict__ V, int64_t ldv, int nb, int b, int G,
-                             double* slot, double* smem) {
+                             double* slot, double* smem, const uint4* __restrict__ dig = nullptr,
+                             const int* __restrict__ dex = nullptr, int capc = 0, int kc = 0) {
     const int kx = k + nb;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gid = lane >> 2, tig = lane & 3;
@@ -74,13 +77,21 @@ __device__ void gram_tc_part(int64_t n, const double* __restrict__ Q, int64_t ld
 
     for (int e = threadIdx.x; e < kTcCols * 2 * kTcWp; e += blockDim.x) sl[e] = make_uint4(0u, 0u, 0u, 0u);
 
+    // Wide blocks: tiles round robin over the 8 warps.  Narrow blocks (nb <= 8,
+    // at most 4 tiles) give each tile a warp pair that splits the chunk's rows
+    // (k-steps 0-1 and 2-3): half the chain of dependent MMAs per accumulator,
+    // every warp busy; the pair's FP64 sums are added in a fixed order at the end.
+    const bool narrow = nb <= 8;
+    const int khalf = narrow ? (warp & 1) : 0;
+    const int ks0 = narrow ? 2 * khalf : 0, ks1 = narrow ? ks0 + 2 : kTcRows / 16;
     int my_mt[kTcMaxTiles], my_nt[kTcMaxTiles], ntile = 0;
     {
+        const int who = narrow ? (warp >> 1) : warp, nwho = narrow ? 4 : 8;
         int cnt = 0;
         for (int mt = 0; mt < (kx + 15) / 16; ++mt)
             for (int nt = 0; nt < (nb + 7) / 8; ++nt) {
                 if (!tc_tile_needed(mt, nt, k)) continue;
-                if (cnt % 8 == warp && ntile < kTcMaxTiles) { my_mt[ntile] = mt; my_nt[ntile] = nt; ++ntile; }
+                if (cnt % nwho == who && ntile < kTcMaxTiles) { my_mt[ntile] = mt; my_nt[ntile] = nt; ++ntile; }
                 ++cnt;
             }
     }
@@ -91,16 +102,26 @@ __device__ void gram_tc_part(int64_t n, const double* __restrict__ Q, int64_t ld
         for (int i = 0; i < 4; ++i) out[q][i] = 0.0;
 
     const int64_t nchunks = (n + kTcRows - 1) / kTcRows;
-    if ((int64_t)b < nchunks) {
-        tc_stage64(Q, ldq, k, V, ldv, kx, (int64_t)b * kTcRows, n, raw);
+    if ((int64_t)b < nchunks && kc < kx) {
+        tc_stage64(Q, ldq, k, V, ldv, kx, (int64_t)b * kTcRows, n, raw, kc);
         cp_async_commit();
     }
     for (int64_t ci = b; ci < nchunks; ci += G) {
         cp_async_wait_all();
         __syncthreads();
-        // 1. per column (one warp): exponent of the chunk maximum, then the digit
-        //    slices; lane l holds rows 2l and 2l + 1
-        for (int c = warp; c < kx; c += 8) {
+        // 0. columns held in the digit basis: their digit units and exponents
+        if (kc > 0) {
+            const uint4* src = dig + (size_t)ci * capc * 64;
+            for (int e = threadIdx.x; e < kc * 64; e += blockDim.x) {
+                const int c = e >> 6, u = e & 63;
+                cp_async16(sl + (size_t)(c * 2 + (u >> 5)) * kTcWp + (u & 31), src + e, 16);
+            }
+            cp_async_commit();
+            for (int c = threadIdx.x; c < kc; c += blockDim.x) ex[c] = dex[(size_t)ci * capc + c];
+        }
+        // 1. per other column (one warp): exponent of the chunk maximum, then the
+        //    digit slices; lane l holds rows 2l and 2l + 1
+        for (int c = kc + warp; c < kx; c += 8) {
             const double2 v = reinterpret_cast<const double2*>(raw + (size_t)c * kTcRows)[lane];
             int eb = max(tc_bexp(v.x), tc_bexp(v.y));
 #pragma unroll
@@ -114,10 +135,11 @@ __device__ void gram_tc_part(int64_t n, const double* __restrict__ Q, int64_t ld
             uint4* u = sl + (size_t)c * 2 * kTcWp + lane;
             tc_pack(d0, d1, u[0], u[kTcWp]);
         }
+        if (kc > 0) cp_async_wait_all();
         __syncthreads();
         // the raw tile is free: the next chunk streams in during the MMAs
-        if (ci + G < nchunks) {
-            tc_stage64(Q, ldq, k, V, ldv, kx, (ci + G) * kTcRows, n, raw);
+        if (ci + G < nchunks && kc < kx) {
+            tc_stage64(Q, ldq, k, V, ldv, kx, (ci + G) * kTcRows, n, raw, kc);
             cp_async_commit();
         }
         // 2. exact digit products on the tensor cores, one output tile at a time
@@ -135,7 +157,7 @@ __device__ void gram_tc_part(int64_t n, const double* __restrict__ Q, int64_t ld
 #pragma unroll
                 for (int i = 0; i < 4; ++i) acc[t][i] = 0.f;
 #pragma unroll 1
-            for (int ks = 0; ks < kTcRows / 16; ++ks) {
+            for (int ks = ks0; ks < ks1; ++ks) {
                 const int w = ks * 8;
                 // digits 0-3 (.x..w) and 4-6 of the four A and two B fragment positions
                 tc_mma_step(acc, pa[w], pa[w + kTcWp], pa[C8 + w], pa[C8 + w + kTcWp], pa[w + 4], pa[w + 4 + kTcWp],
@@ -157,6 +179,28 @@ __device__ void gram_tc_part(int64_t n, const double* __restrict__ Q, int64_t ld
         }
     }
     cp_async_wait_all();
+    if (narrow) {
+        // the pair's second warp hands its sums to the first through the (now
+        // idle) digit slices; the first adds them in a fixed order
+        double* red = reinterpret_cast<double*>(sl);
+        __syncthreads();
+        if (khalf == 1) {
+#pragma unroll
+            for (int q = 0; q < kTcMaxTiles; ++q) {
+                if (q >= ntile) break;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) red[(((warp >> 1) * kTcMaxTiles + q) * 4 + i) * 32 + lane] = out[q][i];
+            }
+        }
+        __syncthreads();
+        if (khalf == 1) return;
+#pragma unroll
+        for (int q = 0; q < kTcMaxTiles; ++q) {
+            if (q >= ntile) break;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) out[q][i] += red[(((warp >> 1) * kTcMaxTiles + q) * 4 + i) * 32 + lane];
+        }
+    }
 #pragma unroll
     for (int q = 0; q < kTcMaxTiles; ++q) {
         if (q >= ntile) break;

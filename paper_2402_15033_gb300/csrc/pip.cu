@@ -25,6 +25,7 @@
 #include "pip_body.cuh"
 #include "gram_tc.cuh"
 #include "update_tc.cuh"
+#include "update_tcd.cuh"
 
 namespace gm {
 
@@ -61,22 +62,24 @@ gram_wide_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, int k,
 }
 
 // Exact-slice tensor-core Gram (gram_tc.cuh), k + nb <= 64: one column group.
+// The first kc columns of [Q, V] come from the digit basis when kc > 0.
 __global__ void __launch_bounds__(kGramThreads, 2)
 gram_tc_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
                const double* __restrict__ V, int64_t ldv, int nb, double* __restrict__ R, int ldr,
                double* partial, unsigned* counter, double* gram, int32_t* d_status,
-               int32_t* d_skip, int mode) {
+               int32_t* d_skip, int mode, const uint4* dig, const int* dex, int capc, int kc) {
     extern __shared__ double smem[];
     if (d_skip && *d_skip) return;
     const int G = gridDim.x;
     const size_t ps = (size_t)kMaxNB * nb;
-    gram_tc_part(n, Q, ldq, k, V, ldv, nb, blockIdx.x, G, partial + blockIdx.x * ps, smem);
+    gram_tc_part(n, Q, ldq, k, V, ldv, nb, blockIdx.x, G, partial + blockIdx.x * ps, smem, dig, dex, capc, kc);
     pip_finish(k, nb, 0, 1, G, R, ldr, partial, ps, counter, gram, d_status, d_skip, smem, mode);
 }
 
 cudaError_t launch_gram_tc(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k,
                            const double* V, int64_t ldv, int nb, double* R, int ldr, const PipWork& w,
-                           int32_t* d_status, int32_t* d_skip, int grid, int mode) {
+                           int32_t* d_status, int32_t* d_skip, int grid, int mode,
+                           const void* digits = nullptr, int capc = 0, int kc = 0) {
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -84,41 +87,117 @@ cudaError_t launch_gram_tc(cudaStream_t st, int64_t n, const double* Q, int64_t 
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    const uint4* dig = static_cast<const uint4*>(digits);
+    const int* dex = digits ? reinterpret_cast<const int*>(dig + tc_digits_units(n, capc)) : nullptr;
     // two CTAs per SM (the chunk tiles take most of the shared memory)
     const int G = std::min(grid, 2 * num_sms());
     gram_tc_kernel<<<G, kGramThreads, gram_tc_smem(k + nb), st>>>(n, Q, ldq, k, V, ldv, nb, R, ldr, w.partial,
-                                                                   w.counter, w.gram, d_status, d_skip, mode);
+                                                                   w.counter, w.gram, d_status, d_skip, mode, dig,
+                                                                   dex, capc, digits ? kc : 0);
     return cudaGetLastError();
 }
 
-// Exact-slice tensor-core update (update_tc.cuh), k + nb <= 64.
+// Digit-basis fill: columns c0 .. c0+nc-1 of the digit basis from X(:, 0:nc).
+__global__ void __launch_bounds__(256)
+digits_fill_kernel(int64_t n, const double* __restrict__ X, int64_t ldx, int c0, int nc, uint4* dig, int* dex,
+                   int capc) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int64_t nchunks = (n + 63) / 64;
+    for (int64_t e = (int64_t)blockIdx.x * nw + warp; e < nchunks * nc; e += (int64_t)gridDim.x * nw) {
+        const int64_t ch = e / nc;
+        const int c = (int)(e % nc);
+        const int64_t r0 = ch * 64 + 2 * lane;
+        const double* p = X + (int64_t)c * ldx + r0;
+        double x0 = 0.0, x1 = 0.0;
+        if (r0 + 1 < n) {
+            const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+            x0 = v.x;
+            x1 = v.y;
+        } else if (r0 < n) {
+            x0 = __ldg(p);
+        }
+        tc_digits_store(x0, x1, ch, c0 + c, capc, dig, dex);
+    }
+}
+
+cudaError_t launch_digits_fill(cudaStream_t st, int64_t n, const double* X, int64_t ldx, int c0, int nc,
+                               void* digits, int capc) {
+    uint4* dig = static_cast<uint4*>(digits);
+    int* dex = reinterpret_cast<int*>(dig + tc_digits_units(n, capc));
+    const int64_t items = (n + 63) / 64 * nc;
+    const int grid = (int)std::min<int64_t>((items + 7) / 8, 8 * (int64_t)num_sms());
+    digits_fill_kernel<<<grid, 256, 0, st>>>(n, X, ldx, c0, nc, dig, dex, capc);
+    return cudaGetLastError();
+}
+
+// Exact-slice tensor-core update (update_tc.cuh), k + nb <= 64; with DIG it also
+// writes the new columns into the digit basis.
+template <bool DIG>
 __global__ void __launch_bounds__(512, 1)
 update_tc_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k, double* V, int64_t ldv, int nb,
-                 const double* __restrict__ R, int ldr, const int32_t* d_status, const int32_t* d_skip, int mode) {
+                 const double* __restrict__ R, int ldr, const int32_t* d_status, const int32_t* d_skip, int mode,
+                 uint4* dig, int* dex, int capc) {
     extern __shared__ __align__(16) char tu_smem[];
     if ((d_skip && *d_skip) || *d_status) return;
-    update_tc_body(n, Q, ldq, k, V, ldv, nb, R, ldr, mode, blockIdx.x, gridDim.x, tu_smem);
+    update_tc_body<DIG>(n, Q, ldq, k, V, ldv, nb, R, ldr, mode, blockIdx.x, gridDim.x, tu_smem, dig, dex, capc);
 }
 
 cudaError_t launch_update_tc(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, double* V,
                              int64_t ldv, int nb, const double* R, int ldr, const int32_t* d_status,
-                             const int32_t* d_skip, int mode) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)update_tc_smem(kTuMaxKX, kTuMaxKX));
+                             const int32_t* d_skip, int mode, void* digits = nullptr, int capc = 0) {
+    static bool attr[2] = {false, false};
+    const bool dg = digits != nullptr;
+    if (!attr[dg]) {
+        cudaError_t e = dg ? cudaFuncSetAttribute(update_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)update_tc_smem(kTuMaxKX, kTuMaxKX, true))
+                           : cudaFuncSetAttribute(update_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)update_tc_smem(kTuMaxKX, kTuMaxKX, false));
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[dg] = true;
     }
     // wide blocks: one 16-warp CTA per SM (the W slices take a third of the
     // shared memory); narrow ones: 8-warp CTAs, two per SM where they fit
     const int threads = nb > 32 ? 512 : 256;
-    const size_t sm = update_tc_smem(k + nb, nb);
+    const size_t sm = update_tc_smem(k + nb, nb, dg);
     const int per_sm = nb > 32 ? 1 : (2 * (sm + 1024) <= 228 * 1024 ? 2 : 1);
     const int64_t chunks = (n + kTuRows - 1) / kTuRows;
     const int G = (int)std::min<int64_t>(chunks, (int64_t)per_sm * num_sms());
-    update_tc_kernel<<<G, threads, sm, st>>>(n, Q, ldq, k, V, ldv, nb, R, ldr, d_status,
-                                                                     d_skip, mode);
+    uint4* dig = static_cast<uint4*>(digits);
+    int* dex = dg ? reinterpret_cast<int*>(dig + tc_digits_units(n, capc)) : nullptr;
+    if (dg)
+        update_tc_kernel<true><<<G, threads, sm, st>>>(n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, d_skip, mode, dig,
+                                                       dex, capc);
+    else
+        update_tc_kernel<false><<<G, threads, sm, st>>>(n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, d_skip, mode,
+                                                        nullptr, nullptr, 0);
+    return cudaGetLastError();
+}
+
+// Narrow update from the digit basis (update_tcd.cuh), nb <= 8, k + nb <= 64.
+__global__ void __launch_bounds__(256, 2)
+update_tcd_kernel(int64_t n, int k, double* V, int64_t ldv, int nb, const double* __restrict__ R, int ldr,
+                  const int32_t* d_status, const int32_t* d_skip, int mode, uint4* dig, int* dex, int capc) {
+    extern __shared__ __align__(16) char td_smem[];
+    if ((d_skip && *d_skip) || *d_status) return;
+    update_tcd_body(n, k, V, ldv, nb, R, ldr, mode, blockIdx.x, gridDim.x, td_smem, dig, dex, capc);
+}
+
+cudaError_t launch_update_tcd(cudaStream_t st, int64_t n, int k, double* V, int64_t ldv, int nb, const double* R,
+                              int ldr, const int32_t* d_status, const int32_t* d_skip, int mode, void* digits,
+                              int capc) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(update_tcd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)update_tcd_smem(kTuMaxKX, kUdMaxNB));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int64_t chunks = (n + kUdRows - 1) / kUdRows;
+    const int G = (int)std::min<int64_t>(chunks, 2 * (int64_t)num_sms());
+    uint4* dig = static_cast<uint4*>(digits);
+    int* dex = reinterpret_cast<int*>(dig + tc_digits_units(n, capc));
+    update_tcd_kernel<<<G, 256, update_tcd_smem(k + nb, nb), st>>>(n, k, V, ldv, nb, R, ldr, d_status, d_skip, mode,
+                                                                   dig, dex, capc);
     return cudaGetLastError();
 }
 
@@ -395,6 +474,24 @@ cudaError_t launch_pip_update(cudaStream_t st, int64_t n, const float* Q, int64_
                               float* V, int64_t ldv, int nb, const double* R, int ldr,
                               const int32_t* d_status, const int32_t* d_skip, int mode, int arith) {
     return pip_update_t<float>(st, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, d_skip, mode, arith);
+}
+
+// Tensor-core halves with a digit basis (entry points ortho_*_tcd, ortho_digits_fill).
+cudaError_t launch_gram_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, const double* V,
+                                  int64_t ldv, int nb, double* R, int ldr, const PipWork& w, int32_t* d_status,
+                                  int grid, const void* digits, int capc, int kc) {
+    return launch_gram_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, nullptr, grid, 0, digits, capc, kc);
+}
+cudaError_t launch_update_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, double* V,
+                                    int64_t ldv, int nb, const double* R, int ldr, const int32_t* d_status,
+                                    void* digits, int capc) {
+    // narrow blocks read Q's digits instead of slicing its rows
+    if (nb <= kUdMaxNB) return launch_update_tcd(st, n, k, V, ldv, nb, R, ldr, d_status, nullptr, 0, digits, capc);
+    return launch_update_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, nullptr, 0, digits, capc);
+}
+cudaError_t launch_digits_fill_cols(cudaStream_t st, int64_t n, const double* X, int64_t ldx, int c0, int nc,
+                                    void* digits, int capc) {
+    return launch_digits_fill(st, n, X, ldx, c0, nc, digits, capc);
 }
 
 PipWork pip_work_layout(void* base, int64_t n, int k, int nb) {

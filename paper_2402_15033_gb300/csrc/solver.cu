@@ -27,6 +27,7 @@
 #include <vector>
 #include <algorithm>
 #include "solver_run.cuh"
+#include "tc_common.cuh"
 
 namespace gm {
 
@@ -737,6 +738,67 @@ int ortho_update_dd(void* stream, int64_t n, const double* Q, int64_t ldq, int32
 int ortho_update_tc(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,
                     int32_t nb, const double* R, int32_t ldr, const int32_t* d_status) {
     return update_impl(stream, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, kArithTC);
+}
+
+static bool col16(const double* p, int64_t ld) {
+    return (reinterpret_cast<uintptr_t>(p) & 15) == 0 && (ld % 2) == 0;
+}
+
+size_t ortho_digits_bytes(int64_t n, int32_t capc) {
+    if (n < 1 || capc < 1 || capc > kMaxNB) return 0;
+    return tc_digits_bytes(n, capc);
+}
+
+int ortho_digits_fill(void* stream, int64_t n, const double* X, int64_t ldx, int32_t c0, int32_t nc,
+                      void* d_digits, int32_t capc) {
+    clear_error();
+    GM_ARG(n >= 1 && nc >= 1 && c0 >= 0 && capc >= 1 && capc <= kMaxNB && c0 + nc <= capc,
+           "need n >= 1, nc >= 1, 0 <= c0, c0 + nc <= capc <= 64");
+    GM_ARG(X != nullptr && ldx >= n && col16(X, ldx), "X must be non-NULL, ldx >= n, columns 16-byte aligned");
+    GM_ARG(d_digits != nullptr && (reinterpret_cast<uintptr_t>(d_digits) & 15) == 0,
+           "d_digits must be non-NULL and 16-byte aligned");
+    cudaError_t e = launch_digits_fill_cols(static_cast<cudaStream_t>(stream), n, X, ldx, c0, nc, d_digits, capc);
+    return cuda_rc(e, "digits fill launch");
+}
+
+int ortho_gram_chol_tcd(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, const double* V,
+                        int64_t ldv, int32_t nb, double* R, int32_t ldr, void* d_work, size_t work_bytes,
+                        int32_t* d_status, const void* d_digits, int32_t capc, int32_t kc) {
+    clear_error();
+    int code = GMRES_OK;
+    if (check_pip_args(n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status, &code)) return code;
+    GM_ARG(k + nb <= kMaxNB && k + nb <= capc && capc <= kMaxNB && kc >= 0 && kc <= k + nb,
+           "need k + nb <= capc <= 64 and 0 <= kc <= k + nb");
+    GM_ARG(col16(V, ldv) && (k == 0 || col16(Q, ldq)), "Q and V columns must start on 16-byte boundaries");
+    GM_ARG(d_digits != nullptr && (reinterpret_cast<uintptr_t>(d_digits) & 15) == 0,
+           "d_digits must be non-NULL and 16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PipWork w = pip_work_layout(d_work, n, k, nb);
+    cudaError_t e = cudaMemsetAsync(w.counter, 0, 256, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess)
+        e = launch_gram_tc_digits(s, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, reduction_grid(n), d_digits, capc,
+                                  kc);
+    return cuda_rc(e, "gram launch");
+}
+
+int ortho_update_tcd(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,
+                     int32_t nb, const double* R, int32_t ldr, const int32_t* d_status, void* d_digits,
+                     int32_t capc) {
+    clear_error();
+    GM_ARG(n >= 1, "n must be >= 1");
+    GM_ARG(k >= 0 && nb >= 1 && k + nb <= kMaxNB && k + nb <= capc && capc <= kMaxNB,
+           "need k >= 0, nb >= 1, k + nb <= capc <= 64");
+    GM_ARG(k == 0 || (Q != nullptr && ldq >= n), "Q must be non-NULL with ldq >= n when k > 0");
+    GM_ARG(V != nullptr && ldv >= n, "V must be non-NULL with ldv >= n");
+    GM_ARG(R != nullptr && ldr >= k + nb, "R must be non-NULL with ldr >= k + nb");
+    GM_ARG(d_status != nullptr, "d_status is NULL");
+    GM_ARG(col16(V, ldv) && (k == 0 || col16(Q, ldq)), "Q and V columns must start on 16-byte boundaries");
+    GM_ARG(d_digits != nullptr && (reinterpret_cast<uintptr_t>(d_digits) & 15) == 0,
+           "d_digits must be non-NULL and 16-byte aligned");
+    cudaError_t e = launch_update_tc_digits(static_cast<cudaStream_t>(stream), n, Q, ldq, k, V, ldv, nb, R, ldr,
+                                            d_status, d_digits, capc);
+    return cuda_rc(e, "update launch");
 }
 
 int ortho_stage1(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,

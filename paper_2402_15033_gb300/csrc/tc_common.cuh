@@ -152,24 +152,61 @@ __device__ __forceinline__ void tc_mma_step(float (&acc)[kTcSlices][4], const ui
             mma_bf16_16816(acc[p + r], A[p][0], A[p][1], A[p][2], A[p][3], B[r][0], B[r][1]);
 }
 
-// Asynchronous copies of a 64-row chunk of [Q(:, 0:k), V(:, 0:kx-k)] into a
-// column-major shared tile (ld 64): thread t copies rows 2(t % 32), +1 of
-// columns t / 32, t / 32 + nw, ... (nw = blockDim / 32), walking the column
-// pointers by increments; rows at or beyond n are zero-filled.  Q, V and
+// Asynchronous copies of a 64-row chunk of [Q(:, 0:k), V(:, 0:kx-k)] (columns
+// cb and up) into a column-major shared tile (ld 64): thread t copies rows
+// 2(t % 32), +1 of columns t / 32, t / 32 + nw, ... (nw = blockDim / 32),
+// walking the column pointers by increments; rows at or beyond n are
+// zero-filled.  Q, V and
 // their leading dimensions are 16-byte aligned (row0 is even).
 __device__ __forceinline__ void tc_stage64(const double* Q, int64_t ldq, int k, const double* V, int64_t ldv,
-                                           int kx, int64_t row0, int64_t n, double* tile) {
+                                           int kx, int64_t row0, int64_t n, double* tile, int cb = 0) {
     const int q = threadIdx.x & 31, c0 = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int64_t row = row0 + 2 * q;
     const int bytes = row + 2 <= n ? 16 : (row < n ? 8 : 0);
     const unsigned dst0 = (unsigned)__cvta_generic_to_shared(tile + 2 * q);
     int c = c0;
-    for (const double* p = Q + (int64_t)c0 * ldq + row; c < k; c += nw, p += (int64_t)nw * ldq)
+    if (c < cb) c += (cb - c + nw - 1) / nw * nw;   // columns below cb are not staged
+    for (const double* p = Q + (int64_t)c * ldq + row; c < k; c += nw, p += (int64_t)nw * ldq)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst0 + (unsigned)c * 512u),
                      "l"(bytes ? p : Q), "r"(bytes) : "memory");
     for (const double* p = V + (int64_t)(c - k) * ldv + row; c < kx; c += nw, p += (int64_t)nw * ldv)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst0 + (unsigned)c * 512u),
                      "l"(bytes ? p : V), "r"(bytes) : "memory");
+}
+
+// ---- digit basis: the seven digit slices of basis columns, kept in HBM so that
+// a column is sliced once however often it is read.  For 64-row chunk ch and
+// column c, units [(ch * capc + c) * 64, +64) hold the 32 row pairs' digits
+// 0-3 (units 0-31) and 4-6 (units 32-63) in the shared-memory unit format of the
+// Gram kernel (without its padding), and exps[ch * capc + c] the chunk column's
+// unbiased exponent (kTcBadExp for a NaN or infinity).  The exponents follow
+// the units in one buffer.
+__host__ __device__ inline size_t tc_digits_units(int64_t n, int capc) {
+    return (size_t)((n + 63) / 64) * (size_t)capc * 64;
+}
+__host__ __device__ inline size_t tc_digits_bytes(int64_t n, int capc) {
+    return tc_digits_units(n, capc) * 16 + (size_t)((n + 63) / 64) * (size_t)capc * sizeof(int) + 256;
+}
+
+// Slice column c of a 64-row chunk (lane l holds rows 2l, 2l+1: x0, x1) into
+// the digit basis; one warp.
+__device__ __forceinline__ void tc_digits_store(double x0, double x1, int64_t ch, int c, int capc, uint4* units,
+                                                int* exps) {
+    const int lane = threadIdx.x & 31;
+    int eb = max(tc_bexp(x0), tc_bexp(x1));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, off));
+    const bool bad = eb == 0x7FF;
+    if (bad || eb == 0) eb = 1023;
+    uint32_t d0[kTcSlices], d1[kTcSlices];
+    tc_slice(x0, eb, d0);
+    tc_slice(x1, eb, d1);
+    uint4 lo, hi;
+    tc_pack(d0, d1, lo, hi);
+    uint4* u = units + ((size_t)ch * capc + c) * 64;
+    u[lane] = lo;
+    u[32 + lane] = hi;
+    if (lane == 0) exps[(size_t)ch * capc + c] = bad ? kTcBadExp : eb - 1023;
 }
 
 }  // namespace gm

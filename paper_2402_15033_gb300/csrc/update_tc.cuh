@@ -27,9 +27,10 @@ constexpr int kTuMaxTiles = 2;                // 4 M-tiles x N-tiles: <= 16 over
 
 __host__ __device__ constexpr int tu_nbp(int nb) { return (nb + 7) / 8 * 8; }
 // shared memory: raw chunk, X slices, W slices, integer tables
-__host__ __device__ constexpr size_t update_tc_smem(int kx, int nb) {
+__host__ __device__ constexpr size_t update_tc_smem(int kx, int nb, bool digits = false) {
     return (size_t)kx * kTuRows * sizeof(double) + (size_t)kTuRows * 2 * kTcWp * 16 +
-           (size_t)tu_nbp(nb) * 2 * kTcWp * 16 + (64 + 64 + kTuRows + 8 * kTuRows) * sizeof(int);
+           (size_t)tu_nbp(nb) * 2 * kTcWp * 16 + (64 + 64 + kTuRows + 8 * kTuRows) * sizeof(int) +
+           (digits ? (size_t)nb * kTuRows * sizeof(double) : 0);   // output tile of the digit-basis writes
 }
 
 // Row r's unit for K pair w (two consecutive columns) in the X slices; the low
@@ -45,11 +46,13 @@ __device__ __forceinline__ int tu_colshift(double nrm2) {
     return (e - 1023) >> 1;                       // floor(log2 ||v||) or one less
 }
 
-// X = [Q(:, 0:k), V(:, 0:nb)] rows in 64-row chunks b, b+G, ...; V overwritten.
+// X = [Q(:, 0:k), V(:, 0:nb)] rows in 64-row chunks b, b+G, ...; V overwritten;
+// with DIG the new columns' digits also go to digit-basis columns k .. k+nb-1.
 // blockDim.x = 32 * NW, NW >= 8.
+template <bool DIG>
 __device__ void update_tc_body(int64_t n, const double* __restrict__ Q, int64_t ldq, int k, double* V,
                                int64_t ldv, int nb, const double* __restrict__ R, int ldr, int mode, int b, int G,
-                               char* smem) {
+                               char* smem, uint4* dig, int* dex, int capc) {
     const int kx = k + nb, nbp = tu_nbp(nb);
     const int NW = blockDim.x >> 5;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -62,6 +65,7 @@ __device__ void update_tc_body(int64_t n, const double* __restrict__ Q, int64_t 
     int* fexp = cshift + 64;                                                               // [64]
     int* rexp = fexp + 64;                                                                 // [64]
     int* epart = rexp + kTuRows;                                                           // [8][64]
+    double* otile = reinterpret_cast<double*>(epart + 8 * kTuRows);                        // [nb][64]
 
     // ---- W = [-P T^{-1}; T^{-1}] scaled by the column shifts, in FP64, then sliced
     double* Ts = reinterpret_cast<double*>(wu);   // nb x nb (T), then T^{-1}, in the W-slice region
@@ -221,8 +225,24 @@ __device__ void update_tc_body(int64_t n, const double* __restrict__ Q, int64_t 
                 const long long S = tc_combine(acc[0][i], acc[1][i], acc[2][i], acc[3][i], acc[4][i], acc[5][i],
                                                acc[6][i]);
                 const int er = rexp[ro], fj = fexp[j];
-                V[(size_t)j * ldv + row0 + ro] = max(er, fj) == kTcBadExp ? __longlong_as_double(0x7FF8000000000000ll)
-                                                                          : tc_int_to_double(S, er + fj - 52);
+                const double v = max(er, fj) == kTcBadExp ? __longlong_as_double(0x7FF8000000000000ll)
+                                                          : tc_int_to_double(S, er + fj - 52);
+                if (DIG) otile[j * kTuRows + ro] = v;
+                else V[(size_t)j * ldv + row0 + ro] = v;
+            }
+        }
+        if (DIG) {
+            // digit-basis copy of the new columns: one warp per column, lane l
+            // holds rows 2l, 2l + 1; the FP64 rows go out in pairs
+            __syncthreads();
+            for (int j = warp; j < nb; j += NW) {
+                const int64_t r0 = row0 + 2 * lane;
+                const double x0 = r0 < n ? otile[j * kTuRows + 2 * lane] : 0.0;
+                const double x1 = r0 + 1 < n ? otile[j * kTuRows + 2 * lane + 1] : 0.0;
+                double* dst = V + (size_t)j * ldv + r0;
+                if (r0 + 1 < n) *reinterpret_cast<double2*>(dst) = make_double2(x0, x1);
+                else if (r0 < n) *dst = x0;
+                tc_digits_store(x0, x1, ci, k + j, capc, dig, dex);
             }
         }
     }

@@ -231,3 +231,149 @@ def test_tc_two_stage_on_ill_conditioned_panels(lib):
     Rfin = R2.cpu().numpy() @ Rh.cpu().numpy()
     assert np.allclose(Rfin, Rd, rtol=0, atol=1e-9 * np.abs(Rd).max())
     assert np.allclose(Qg @ Rfin, V, atol=1e-12 * np.abs(V).max())
+
+
+# ---------------------------------------------------------------- digit basis
+def _cols(n, c, ld_pad, g):
+    """n x c column-major CUDA view with ld = n + ld_pad, N(0,1)/sqrt(n) entries."""
+    buf = torch.zeros(c, n + ld_pad, dtype=torch.float64, device="cuda")
+    buf[:, :n] = torch.tensor(g.standard_normal((c, n)) / np.sqrt(n))
+    return buf.T[:n]
+
+
+@pytest.mark.parametrize("n,k,nb", [(4099, 6, 5), (3001, 30, 16), (20000, 0, 61), (130, 56, 5), (64, 1, 5)])
+def test_digit_basis_gram_is_bit_identical(lib, n, k, nb):
+    """The Gram that reads Q's (and V's) digits from the digit basis equals the
+    one that slices them, bit for bit (the digits are the same)."""
+    from paper_2402_15033_gb300 import capi
+    g = synth.rng(1300 + n + k)
+    pad = n % 2
+    X = _cols(n, k + nb, pad, g)
+    Q, V = (X[:, :k] if k else None), X[:, k:]
+    capc = 64
+    dig = torch.zeros(capi.digits_bytes(n, capc), dtype=torch.uint8, device="cuda")
+    capi.digits_fill(X, 0, dig, capc)
+    work = torch.empty(capi.workspace_bytes(n, k, nb), dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    outs = []
+    for kc in (None, k, k + nb):
+        R = torch.full((nb, k + nb), np.nan, dtype=torch.float64, device="cuda").T
+        if kc is None:
+            capi.ortho_gram_chol_tc(Q, V, R, work, st, k=k)
+        else:
+            capi.ortho_gram_chol_tcd(Q, V, R, work, st, dig, capc, kc, k=k)
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        outs.append(R.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("n,k,nb", [(4099, 6, 5), (777, 20, 21), (20001, 56, 5), (1000, 0, 8), (131, 3, 1)])
+def test_digit_basis_update_matches_oracle_and_writes_digits(lib, n, k, nb):
+    """ortho_update_tcd (Q's digits read from the digit basis for nb <= 8) meets
+    the FP64 parity bars against the oracle's BCGS-PIP, and the digits it writes
+    for the new V equal those of ortho_digits_fill on the result."""
+    from paper_2402_15033_gb300 import capi
+    g = synth.rng(1400 + n + k)
+    pad = n % 2
+    Qh = bo.hhqr(g.standard_normal((n, k)))[0] if k else np.zeros((n, 0))
+    Vh = g.standard_normal((n, nb)) / np.sqrt(n) + (Qh @ g.standard_normal((k, nb)) / 3 if k else 0.0)
+    X = _cols(n, k + nb, pad, g)
+    X[:, :k] = torch.tensor(Qh, device="cuda")
+    X[:, k:] = torch.tensor(Vh, device="cuda")
+    capc = 64
+    dig = torch.zeros(capi.digits_bytes(n, capc), dtype=torch.uint8, device="cuda")
+    if k:
+        capi.digits_fill(X[:, :k], 0, dig, capc)
+    work = torch.empty(capi.workspace_bytes(n, k, nb), dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    R = torch.zeros(nb, k + nb, dtype=torch.float64, device="cuda").T
+    Qd = X[:, :k] if k else None
+    capi.ortho_gram_chol_tcd(Qd, X[:, k:], R, work, st, dig, capc, k, k=k)
+    capi.ortho_update_tcd(Qd, X[:, k:], R, st, dig, capc, k=k)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert_parity(Qh if k else None, Vh, X[:, k:].cpu().numpy(), R.cpu().numpy(), 0)
+    ref = torch.zeros_like(dig)
+    capi.digits_fill(X[:, k:], k, ref, capc)
+    torch.cuda.synchronize()
+    nch = (n + 63) // 64
+    units = dig[: nch * capc * 1024].view(nch, capc, 1024)
+    runits = ref[: nch * capc * 1024].view(nch, capc, 1024)
+    assert torch.equal(units[:, k:k + nb], runits[:, k:k + nb])
+    ex = dig[nch * capc * 1024: nch * capc * 1024 + nch * capc * 4].view(torch.int32).view(nch, capc)
+    rex = ref[nch * capc * 1024: nch * capc * 1024 + nch * capc * 4].view(torch.int32).view(nch, capc)
+    assert torch.equal(ex[:, k:k + nb], rex[:, k:k + nb])
+
+
+@pytest.mark.parametrize("scales", [(-40, 30), (25, -25)])
+def test_digit_basis_update_with_unbalanced_columns(lib, scales):
+    """V columns scaled by very different powers of two: the per-chunk column
+    exponents of the digit basis balance them (W'' = D W), so Q^ keeps the FP64
+    parity bar."""
+    from paper_2402_15033_gb300 import capi
+    g = synth.rng(909)
+    n, k, nb = 30011, 12, 6
+    Qh = bo.hhqr(g.standard_normal((n, k)))[0]
+    Vh = g.standard_normal((n, nb)) / np.sqrt(n) + Qh @ g.standard_normal((k, nb)) / 3
+    Vh[:, ::2] *= 2.0 ** scales[0]
+    Vh[:, 1::2] *= 2.0 ** scales[1]
+    X = _cols(n, k + nb, 1, g)
+    X[:, :k] = torch.tensor(Qh, device="cuda")
+    X[:, k:] = torch.tensor(Vh, device="cuda")
+    capc = 64
+    dig = torch.zeros(capi.digits_bytes(n, capc), dtype=torch.uint8, device="cuda")
+    capi.digits_fill(X[:, :k], 0, dig, capc)
+    work = torch.empty(capi.workspace_bytes(n, k, nb), dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    R = torch.zeros(nb, k + nb, dtype=torch.float64, device="cuda").T
+    capi.ortho_gram_chol_tcd(X[:, :k], X[:, k:], R, work, st, dig, capc, k, k=k)
+    capi.ortho_update_tcd(X[:, :k], X[:, k:], R, st, dig, capc, k=k)
+    torch.cuda.synchronize()
+    assert_parity(Qh, Vh, X[:, k:].cpu().numpy(), R.cpu().numpy(), int(st.item()))
+
+
+def test_digit_basis_two_stage_sequence_matches_oracle(lib):
+    """The benchmark's sequence (column 0, blocks of 5 through stage 1, stage 2 on
+    the panel) with the digit basis, against the oracle: R of every block and of
+    stage 2, and the final Q, within the FP64 bars; O(eps) orthogonality."""
+    from paper_2402_15033_gb300 import capi
+    g = synth.rng(1500)
+    n, s, nblk = 30001, 5, 6
+    ncol = 1 + s * nblk
+    B = _cols(n, ncol, 1, g)
+    B[:, 0] /= torch.linalg.norm(B[:, 0])
+    X = B.cpu().numpy().copy()
+    capc = 64
+    Rh = torch.zeros(ncol, ncol, dtype=torch.float64, device="cuda").T
+    R2 = torch.zeros(ncol, ncol, dtype=torch.float64, device="cuda").T
+    work = torch.empty(capi.workspace_bytes(n, ncol, ncol), dtype=torch.uint8, device="cuda")
+    st = torch.zeros(nblk + 1, dtype=torch.int32, device="cuda")
+    dig = torch.zeros(capi.digits_bytes(n, capc), dtype=torch.uint8, device="cuda")
+    capi.digits_fill(B[:, :1], 0, dig, capc)
+    for j in range(nblk):
+        k = 1 + s * j
+        Q, V, Rb = B[:, :k], B[:, k:k + s], Rh[:k + s, k:k + s]
+        capi.ortho_gram_chol_tcd(Q, V, Rb, work, st[j:j + 1], dig, capc, k, k=k)
+        capi.ortho_update_tcd(Q, V, Rb, st[j:j + 1], dig, capc, k=k)
+    capi.ortho_gram_chol_tcd(None, B, R2, work, st[nblk:], dig, capc, ncol, k=0)
+    capi.ortho_update(None, B, R2, st[nblk:], k=0, tc=True)
+    torch.cuda.synchronize()
+    assert int(st.abs().sum().item()) == 0
+    Rh_ref = np.zeros((ncol, ncol))
+    for j in range(nblk):
+        k = 1 + s * j
+        Qh, P, T = bo.stage1(X[:, :k], X[:, k:k + s])
+        X[:, k:k + s] = Qh
+        Rh_ref[:k, k:k + s] = P
+        Rh_ref[k:k + s, k:k + s] = T
+    Qf, _, T2 = bo.stage2(np.zeros((n, 0)), X)
+    Rhg, R2g, Qg = Rh.cpu().numpy(), R2.cpu().numpy(), B.cpu().numpy()
+    msk = np.triu(np.ones((ncol, ncol), bool), 1)
+    msk[:, 0] = False
+    scale = np.maximum(np.linalg.norm(Rh_ref, axis=0), 1e-300)
+    assert np.all(np.abs(Rhg - Rh_ref)[msk] <= (1e-12 * scale[None, :].repeat(ncol, 0))[msk])
+    sc = np.linalg.norm(T2, axis=0)
+    assert np.all(np.abs(R2g - T2) <= 1e-12 * sc[None, :])
+    assert np.max(np.abs(Qg - Qf)) <= 1e-12
+    assert checks.orth_error(Qg)[0] < 100 * np.finfo(float).eps
