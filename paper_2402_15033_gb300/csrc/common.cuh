@@ -76,10 +76,10 @@ cudaError_t launch_pip_update(cudaStream_t st, int64_t n,
 // and X must start on 16-byte boundaries; k + nb <= 64.
 cudaError_t launch_gram_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, const double* V,
                                   int64_t ldv, int nb, double* R, int ldr, const PipWork& w, int32_t* d_status,
-                                  int grid, const void* digits, int capc, int kc);
+                                  int grid, const void* digits, int capc, int kc, int32_t* d_skip = nullptr);
 cudaError_t launch_update_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, double* V,
                                     int64_t ldv, int nb, const double* R, int ldr, const int32_t* d_status,
-                                    void* digits, int capc);
+                                    void* digits, int capc, const int32_t* d_skip = nullptr);
 cudaError_t launch_digits_fill_cols(cudaStream_t st, int64_t n, const double* X, int64_t ldx, int c0, int nc,
                                     void* digits, int capc);
 

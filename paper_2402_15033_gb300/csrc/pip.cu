@@ -479,15 +479,15 @@ cudaError_t launch_pip_update(cudaStream_t st, int64_t n, const float* Q, int64_
 // Tensor-core halves with a digit basis (entry points ortho_*_tcd, ortho_digits_fill).
 cudaError_t launch_gram_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, const double* V,
                                   int64_t ldv, int nb, double* R, int ldr, const PipWork& w, int32_t* d_status,
-                                  int grid, const void* digits, int capc, int kc) {
-    return launch_gram_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, nullptr, grid, 0, digits, capc, kc);
+                                  int grid, const void* digits, int capc, int kc, int32_t* d_skip) {
+    return launch_gram_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, 0, digits, capc, kc);
 }
 cudaError_t launch_update_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, double* V,
                                     int64_t ldv, int nb, const double* R, int ldr, const int32_t* d_status,
-                                    void* digits, int capc) {
+                                    void* digits, int capc, const int32_t* d_skip) {
     // narrow blocks read Q's digits instead of slicing its rows
-    if (nb <= kUdMaxNB) return launch_update_tcd(st, n, k, V, ldv, nb, R, ldr, d_status, nullptr, 0, digits, capc);
-    return launch_update_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, nullptr, 0, digits, capc);
+    if (nb <= kUdMaxNB) return launch_update_tcd(st, n, k, V, ldv, nb, R, ldr, d_status, d_skip, 0, digits, capc);
+    return launch_update_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, d_skip, 0, digits, capc);
 }
 cudaError_t launch_digits_fill_cols(cudaStream_t st, int64_t n, const double* X, int64_t ldx, int c0, int nc,
                                     void* digits, int capc) {

@@ -81,6 +81,7 @@ struct gmres_ctx {
     void* pip_work = nullptr;
     size_t pip_bytes = 0;
     double* bscr = nullptr;      // BCGS2-CholQR2: the five reductions' factors (5 x kMaxCols^2)
+    void* digits = nullptr;      // tensor-core arithmetic: digit basis of the m+1 columns (tc_common.cuh)
     DevState* st = nullptr;      // device
     DevState* hst = nullptr;     // pinned host mirror
     std::vector<cudaEvent_t> ev;
@@ -92,6 +93,7 @@ enum { PH_MPK = 0, PH_S1 = 1, PH_S2 = 2, PH_LS = 3 };
 
 size_t pip_bytes_for(int64_t n, const gmres_opts& o);
 size_t ctx_bytes(int64_t n, int64_t nnz, const gmres_opts& o);
+bool uses_digits(const gmres_opts& o);
 
 }  // namespace gm
 
@@ -141,6 +143,13 @@ size_t pip_bytes_for(int64_t n, const gmres_opts& o) {
 
 // Device bytes gmres_create allocates for a host-CSR context (each piece
 // rounded up to the 256-byte allocation granule).
+// The tensor-core arithmetic keeps a digit basis of the FP64 basis (every column
+// sliced once; stage 1 reads the accumulated columns' digits).
+bool uses_digits(const gmres_opts& o) {
+    return o.arith == GMRES_ARITH_TC && o.precision == GMRES_PREC_FP64 && o.ortho != GMRES_ORTHO_BCGS2_CHOLQR2 &&
+           o.m + 1 <= kMaxNB;
+}
+
 size_t ctx_bytes(int64_t n, int64_t nnz, const gmres_opts& o) {
     auto up = [](size_t b) { return (b + 511) & ~(size_t)511; };
     const int64_t ldq = (n + 31) / 32 * 32;
@@ -152,6 +161,7 @@ size_t ctx_bytes(int64_t n, int64_t nnz, const gmres_opts& o) {
     b += up((size_t)(o.m + 1) * ldq * esz) + 2 * up(ldq * 8);
     b += up(norm_grid(n) * 8) + up(256) + up(pip_bytes_for(n, o)) + up(sizeof(DevState)) + up(16);
     if (o.ortho == GMRES_ORTHO_BCGS2_CHOLQR2) b += up(5 * (size_t)kMaxCols * kMaxCols * sizeof(double));
+    if (uses_digits(o)) b += up(tc_digits_bytes(n, o.m + 1));
     return b;
 }
 
@@ -193,6 +203,7 @@ int gmres_destroy(gmres_ctx* c) {
     cudaFree(c->red_counter);
     cudaFree(c->pip_work);
     cudaFree(c->bscr);
+    cudaFree(c->digits);
     cudaFree(c->st);
     cudaFreeHost(c->hst);
     delete c;
@@ -319,6 +330,11 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
     c->pip_bytes = wb;
     CK(cuda_rc(cudaMalloc(&c->pip_work, wb), "cudaMalloc workspace"));
     CK(cuda_rc(cudaMemsetAsync(c->pip_work, 0, wb, s), "memset workspace"));
+    if (uses_digits(o)) {
+        const size_t db = tc_digits_bytes(n, o.m + 1);
+        CK(cuda_rc(cudaMalloc(&c->digits, db), "cudaMalloc digit basis"));
+        CK(cuda_rc(cudaMemsetAsync(c->digits, 0, db, s), "memset digit basis"));
+    }
     if (o.ortho == GMRES_ORTHO_BCGS2_CHOLQR2) {
         const size_t sb = 5 * (size_t)kMaxCols * kMaxCols * sizeof(double);
         CK(cuda_rc(cudaMalloc(&c->bscr, sb), "cudaMalloc bcgs2 scratch"));
@@ -365,6 +381,10 @@ static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
     int panel_idx = 0;
     cudaError_t e = launch_cycle_begin(s, ds);
     if (e == cudaSuccess) e = launch_scale(s, c->n, c->r ? c->r : static_cast<double*>(c->basis), basis, ds);
+    const int capc = o.m + 1;
+    void* dig = (sizeof(T) == sizeof(double)) ? c->digits : nullptr;   // the digit basis (tensor-core arithmetic)
+    if (e == cudaSuccess && dig)
+        e = launch_digits_fill_cols(s, c->n, reinterpret_cast<const double*>(basis), c->ldq, 0, 1, dig, capc);
     for (int j = 0; j < nblk && e == cudaSuccess; ++j) {
         const int st0 = j * o.s;
         e = mark(PH_MPK);
@@ -404,6 +424,15 @@ static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
                                               done, st_.umode, o.arith);
                 }
                 if (e == cudaSuccess) e = launch_bcgs2_combine(s, ds, k, o.s, S, R);
+            } else if (sizeof(T) == sizeof(double) && dig) {
+                // BCGS-PIP (Fig. 4a) on the tensor cores, the accumulated columns'
+                // digits read from the digit basis, the block's written back
+                const double* Bd = reinterpret_cast<const double*>(basis);
+                e = launch_gram_tc_digits(s, c->n, Bd, c->ldq, k, reinterpret_cast<const double*>(V), c->ldq, o.s, R,
+                                          kMaxCols, w, stat, reduction_grid(c->n), dig, capc, k, done);
+                if (e == cudaSuccess)
+                    e = launch_update_tc_digits(s, c->n, Bd, c->ldq, k, reinterpret_cast<double*>(V), c->ldq, o.s, R,
+                                                kMaxCols, stat, dig, capc, done);
             } else if (sizeof(T) == sizeof(double)) {
                 // BCGS-PIP (Fig. 4a): one reduction, Pythagorean Gram
                 e = launch_pip_gram_chol(s, c->n, basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, w, stat, done,
@@ -443,6 +472,19 @@ static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
             if (o.ortho == GMRES_ORTHO_BCGS2_CHOLQR2) {
                 // the block is final after its five reductions: identity stage-2 factor
                 if (e == cudaSuccess) e = launch_eye_panel(s, ds, lo, t);
+            } else if (dig) {
+                // every column 0 .. t is in the digit basis; the panel's final
+                // columns are written back for the panels and blocks after it
+                const double* Bd = reinterpret_cast<const double*>(basis);
+                if (e == cudaSuccess)
+                    e = launch_gram_tc_digits(s, c->n, Bd, c->ldq, lo, reinterpret_cast<const double*>(V), c->ldq, np,
+                                              R, kMaxCols, w, stat, reduction_grid(c->n), dig, capc, lo + np, done);
+                // the cycle's last panel: no later block reads its digits
+                if (e == cudaSuccess)
+                    e = t < o.m ? launch_update_tc_digits(s, c->n, Bd, c->ldq, lo, reinterpret_cast<double*>(V),
+                                                          c->ldq, np, R, kMaxCols, stat, dig, capc, done)
+                                : launch_pip_update(s, c->n, basis, c->ldq, lo, V, c->ldq, np, R, kMaxCols, stat, done,
+                                                    0, o.arith);
             } else {
                 if (e == cudaSuccess)
                     e = launch_pip_gram_chol(s, c->n, basis, c->ldq, lo, V, c->ldq, np, R, kMaxCols, w, stat, done,
