@@ -105,11 +105,12 @@ FP64_PEAK_TFLOPS = 152 * 2070e6 * 2 * 2 / 1e12   # 2 FP64 FMA/clk/SM x 152 SMs x
 
 # DRAM bytes per launch from one ncu capture at n = 1,048,576 (profiles/),
 # scaled by 4 to the benchmark's n (traffic grows with n): the last stage-1
-# block (k = 56) and the stage-2 panel.  Each equals the launch's algorithmic
-# bytes to within the writes still in L2 at the end of the capture.
+# block (k = 56) and the stage-2 panel.  The FP64 kernels and the stage-2
+# tensor-core kernels move their algorithmic bytes; the stage-1 tensor-core
+# kernels read 14-byte digits instead of 8-byte values (the digit basis).
 NCU_TRAFFIC = {
-    "tc": {"stage1_gram": 4 * (512.2 + 3.8) * 1e6, "stage1_update": 4 * (512.7 + 36.7) * 1e6,
-           "stage2_gram": 4 * (514.1 + 4.6) * 1e6, "stage2_update": 4 * (511.8 + 457.2) * 1e6},
+    "tc": {"stage1_gram": 4 * (986.4 + 3.9) * 1e6, "stage1_update": 4 * (985.7 + 117.4) * 1e6,
+           "stage2_update": 4 * (511.8 + 457.2) * 1e6},
     "fp64": {"stage1_gram": 4 * (511.8 + 3.2) * 1e6, "stage2_gram": 4 * (514.7 + 3.5) * 1e6},
 }
 
