@@ -196,12 +196,75 @@ def hessenberg_columns(Rfin, C, start_final, s, sigma, theta, c_lo, c_hi, H):
     return H
 
 
+def leja_order(z) -> np.ndarray:
+    """Leja ordering of real points (Reichel, BIT 30, 1990), the ordering that
+    the Newton-basis s-step GMRES of Bai, Hu and Reichel (1994) gives its
+    shifts so that the shifted products stay well conditioned: the first point
+    has the largest modulus, every later one maximizes the product of its
+    distances to the points already taken.  The candidates are scanned in
+    ascending order and a tie goes to the first maximum; the distances are
+    scaled by 2^-e with max|z| <= 2^e (exact) so that the products neither
+    overflow nor depend on the scale.  Returns all the points in Leja order."""
+    x = np.sort(np.asarray(z, dtype=np.float64).ravel())
+    if x.size == 0:
+        return x
+    top = float(np.max(np.abs(x)))
+    scale = 1.0 if top == 0.0 else 2.0 ** -math.frexp(top)[1]
+    order = [int(np.argmax(np.abs(x)))]
+    left = np.ones(x.size, dtype=bool)
+    left[order[0]] = False
+    prod = np.ones(x.size)
+    while left.any():
+        prod = prod * np.abs((x - x[order[-1]]) * scale)
+        cand = np.where(left, prod, -1.0)
+        i = int(np.argmax(cand))
+        order.append(i)
+        left[i] = False
+    return x[np.array(order)]
+
+
+def newton_shifts(H, s: int) -> np.ndarray:
+    """Shifts theta_0..theta_{s-1} of the Newton basis, from the Ritz values of
+    a first standard GMRES cycle (the eigenvalues of the square k x k
+    Hessenberg matrix H_k with A Q_k = Q_{k+1} H): their real parts in Leja
+    order, the first s of them (repeated cyclically when k < s).  The real
+    parts keep the basis recurrence real; a conjugate pair gives one real
+    shift twice, and the repeat has distance product 0, so it comes last."""
+    Hk = np.asarray(H, dtype=np.float64)
+    k = Hk.shape[0]
+    if k == 0:
+        return np.zeros(s)
+    ritz = np.linalg.eigvals(Hk)
+    pts = leja_order(ritz.real)
+    return np.array([pts[i % k] for i in range(s)])
+
+
+def newton_sigma(theta, fallback: float) -> float:
+    """Scale of the Newton basis: the power of two nearest (in log2) to the
+    capacity of the interval [min theta, max theta], a quarter of its length
+    (the logarithmic capacity of a real interval).  Dividing each shifted
+    product by it keeps the Newton basis columns of comparable norm, as
+    ||A||_inf does for the monomial basis.  ``fallback`` when the shifts span
+    no interval.  Nearest in log2: cap = f 2^e with f in [1/2, 1) rounds up to
+    2^e when f >= 2^-1/2, else down to 2^(e-1)."""
+    th = np.asarray(theta, dtype=np.float64)
+    cap = 0.25 * (float(th.max()) - float(th.min())) if th.size else 0.0
+    if not (cap > 0.0) or not math.isfinite(cap):
+        return float(fallback)
+    f, e = math.frexp(cap)
+    return math.ldexp(1.0, e if f >= math.sqrt(0.5) else e - 1)
+
+
 def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=1000,
                 ortho="two_stage", sigma=None, theta=None, return_basis=False, basis_dtype=np.float64):
     """s-step GMRES (Fig. 1, §III) with the chosen block orthogonalization.
 
     ``panel`` is the second step size s^ of the two-stage scheme (§V); it must
-    satisfy s | s^ | m.  ``ortho`` in {"two_stage", "bcgs_pip2", "bcgs2_cholqr2"}.
+    satisfy s | s^ | m.  ``theta`` is None (monomial basis), s Newton shifts,
+    or "auto": the first cycle runs with s = 1 (standard GMRES through the same
+    block machinery), ``newton_shifts`` turns its Hessenberg matrix into s
+    shifts, and every later cycle uses the Newton basis with them, scaled by
+    ``newton_sigma`` unless ``sigma`` is given.  ``ortho`` in {"two_stage", "bcgs_pip2", "bcgs2_cholqr2"}.
     ``basis_dtype=np.float32`` is the mixed-precision pattern: the basis is
     stored in FP32 and the MPK runs in FP32 on an FP32 copy of A, while every
     Gram product and sum, the Cholesky factors, the Hessenberg/Givens work, x
@@ -220,6 +283,11 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
     M = as_operator(A)
     n = b.shape[0]
     lowp = np.dtype(basis_dtype) == np.float32
+    auto = isinstance(theta, str)
+    if auto and theta != "auto":
+        raise ValueError("theta must be None, s shifts or 'auto'")
+    th = None if auto else theta
+    s_req = s
     Mb = M.astype(np.float32) if lowp else M
     f64 = np.float64
     if panel is None:
@@ -228,6 +296,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
         panel = s
     if m % s or panel % s or m % panel:
         raise ValueError("need s | panel | m")
+    panel_req = panel
     sig = mpk_sigma(A) if sigma is None else float(sigma)
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     bnorm = np.linalg.norm(b)
@@ -249,6 +318,10 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
             status = STATUS_OK
             break
         restarts += 1
+        # theta = "auto": the first cycle is standard GMRES (s = 1, one SpMV per
+        # block) whose Hessenberg matrix gives the Ritz values for the shifts
+        s = 1 if (auto and th is None) else s_req
+        panel = panel_req if ortho == "two_stage" else s
         Q = np.zeros((n, m + 1), dtype=basis_dtype)
         Q[:, 0] = r / beta
         Rhat = np.zeros((m + 1, m + 1))
@@ -273,7 +346,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
                 where_blk = j
                 st = s * j
                 start_final[st] = final[st]
-                W = mpk(Mb, Q[:, st], s, sig, theta)
+                W = mpk(Mb, Q[:, st], s, sig, th)
                 cols = slice(st + 1, st + s + 1)
                 if ortho == "two_stage":
                     st1 = bo.stage1_lowp if lowp else bo.stage1
@@ -308,7 +381,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
                     c_lo = st
                 if gv is None:
                     gv = Givens(m, beta * C[0, 0])
-                hessenberg_columns(Rfin, C, start_final, s, sig, theta, c_lo, t, H)
+                hessenberg_columns(Rfin, C, start_final, s, sig, th, c_lo, t, H)
                 for c in range(c_lo, t):
                     gv.add_column(H[: c + 2, c])
                 k_used = t
@@ -324,11 +397,16 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
         x = x + Q[:, :k_used].astype(f64) @ y
         iters += k_used
         last = dict(Q=Q, H=H, g0=beta * C[0, 0], k=k_used, Rfin=Rfin, C=C)
+        if auto and th is None:
+            th = newton_shifts(H[:k_used, :k_used], s_req)
+            if sigma is None:
+                sig = newton_sigma(th, sig)
     else:
         r = b - M @ x
         hist.append(np.linalg.norm(r) / bnorm)
     info = dict(status=status, iters=iters, restarts=restarts, relres=hist[-1], history=hist,
-                sigma=sig, where=err_where, breakdown_block=breakdown[0], breakdown_pivot=breakdown[1])
+                sigma=sig, where=err_where, breakdown_block=breakdown[0], breakdown_pivot=breakdown[1],
+                theta=None if th is None else np.asarray(th, dtype=np.float64))
     if return_basis:
         info.update(last)
     return x, info

@@ -363,3 +363,135 @@ def test_mixed_basis_keeps_fp32_orthogonality_after_stage2():
     Q, _, _, _ = bo.two_stage_panel(np.zeros((n, 0)), blocks)
     assert checks.orth_error(Q)[0] < 100 * EPS
     assert checks.orth_error(Q.astype(np.float32).astype(np.float64))[0] < 50 * np.finfo(np.float32).eps
+
+
+# ---------------------------------------------------------------- Newton basis (Leja-ordered Ritz shifts)
+def test_leja_order_of_five_points_by_hand():
+    """Greedy Leja ordering of {-1, -1/2, 0, 1/2, 1}, worked by hand: the
+    largest moduli tie (first in ascending order: -1); then |x + 1| is largest
+    at 1; |x^2 - 1| is largest at 0 (value 1 against 3/4); |x (x^2 - 1)| ties at
+    +-1/2 (3/8 each, first: -1/2); 1/2 is left."""
+    assert kr.leja_order([0.5, 1.0, -1.0, 0.0, -0.5]).tolist() == [-1.0, 1.0, 0.0, -0.5, 0.5]
+
+
+def test_leja_order_on_a_fine_grid_approaches_the_interval_leja_points():
+    """On [-1, 1] the continuous Leja sequence from -1 is -1, 1, 0, then the
+    maximizer of |x (x^2 - 1)|, x = +-1/sqrt(3) (zero of 3x^2 - 1); then the
+    maximizer of |x (x^2 - 1)(x + 1/sqrt(3))|, a root of its derivative, found
+    here with numpy's polynomial roots.  A grid of step h gets each within h."""
+    h = 1e-3
+    got = kr.leja_order(np.linspace(-1.0, 1.0, 2001))[:5]
+    r3 = 1.0 / math.sqrt(3.0)
+    assert got[:3].tolist() == [-1.0, 1.0, 0.0]
+    assert abs(got[3] + r3) <= h
+    p = np.poly1d([1.0, 0.0, -1.0, 0.0]) * np.poly1d([1.0, r3])
+    crit = [z.real for z in p.deriv().roots if abs(z.imag) < 1e-12 and -1 <= z.real <= 1]
+    best = max(crit, key=lambda z: abs(p(z)))
+    assert abs(got[4] - best) <= h
+
+
+def test_leja_order_is_a_permutation_and_scale_free():
+    g = synth.rng(31)
+    z = g.standard_normal(40) * 3.0
+    o = kr.leja_order(z)
+    assert sorted(o.tolist()) == sorted(z.tolist())
+    assert abs(o[0]) == np.abs(z).max()
+    assert np.array_equal(kr.leja_order(z * 2.0 ** 37), o * 2.0 ** 37)
+    # a repeated point has distance product 0 and comes after every other point
+    o2 = kr.leja_order(np.concatenate([z[:10], z[:1]]))
+    assert o2[-1] == z[0] and np.count_nonzero(o2 == z[0]) == 2
+
+
+def test_newton_shifts_of_a_hessenberg_form_are_the_leja_ordered_eigenvalues():
+    """An orthogonal similarity of diag(d) reduced to Hessenberg form by
+    scipy's Householder reduction has eigenvalues d, so the shifts are
+    leja_order(d)[:s] (to eigenvalue rounding), cycled when k < s."""
+    import scipy.linalg as sla
+    g = synth.rng(32)
+    d = np.array([0.5, 1.0, 2.5, 3.0, 4.75, 6.0, 7.5, 8.0])
+    Qo, _ = np.linalg.qr(g.standard_normal((8, 8)))
+    Hh = sla.hessenberg(Qo @ np.diag(d) @ Qo.T)
+    assert np.allclose(np.tril(Hh, -2), 0.0)
+    th = kr.newton_shifts(Hh, 6)
+    assert np.allclose(th, kr.leja_order(d)[:6], atol=1e-12)
+    assert th[0] == pytest.approx(8.0, abs=1e-12) and th[1] == pytest.approx(0.5, abs=1e-12)
+    th12 = kr.newton_shifts(Hh, 12)
+    assert np.allclose(th12[8:], th12[:4])
+    # a rotation block [[a, -b], [b, a]] gives the conjugate pair a +- ib: one real shift a, twice
+    R = np.array([[2.0, -3.0, 0.0], [3.0, 2.0, 1.0], [0.0, 0.5, -4.0]])
+    ev = np.linalg.eigvals(R)
+    assert np.allclose(sorted(kr.newton_shifts(R, 3)), sorted(ev.real), atol=1e-12)
+
+
+def test_auto_shifts_are_the_ritz_values_of_the_first_cycle():
+    """The Ritz values are the eigenvalues of the Rayleigh quotient Q_m^T A Q_m
+    of the first cycle's orthonormal basis (computed here from the basis, not
+    from the recovered H); for symmetric A they lie inside [lambda_min,
+    lambda_max] (Cauchy interlacing)."""
+    A = synth.laplace2d(32)
+    M = kr.as_operator(A)
+    b = M @ synth.x_true(A.n, 0)
+    _, info = kr.sstep_gmres(A, b, m=60, s=10, tol=1e-30, max_restarts=1, theta="auto", return_basis=True)
+    assert info["k"] == 60
+    Q = info["Q"][:, :60]
+    rv = np.linalg.eigvalsh(Q.T @ (M @ Q))
+    assert np.allclose(info["theta"], kr.leja_order(rv)[:10], atol=1e-9)
+    lo, hi = checks.laplace2d_extreme_eigs(32)
+    assert lo - 1e-12 <= info["theta"].min() and info["theta"].max() <= hi + 1e-12
+
+
+def test_newton_sigma_is_the_power_of_two_nearest_the_capacity():
+    """Capacity of [a, b] is (b - a) / 4; the scale is the power of two nearest
+    it in log2 (the boundary 2^(e - 1/2) rounds up)."""
+    assert kr.newton_sigma([0.0, 8.0], 1.0) == 2.0
+    assert kr.newton_sigma([0.0, 4.0 * 3.0], 1.0) == 4.0        # cap 3 = 2^1.58 -> 4
+    assert kr.newton_sigma([0.0, 4.0 * 2.8], 1.0) == 2.0        # cap 2.8 = 2^1.49 -> 2
+    assert kr.newton_sigma([1.0, 1.0 + 4.0 * 2.0 ** 0.5], 1.0) == 2.0   # cap 2^0.5 is the boundary: up
+    assert kr.newton_sigma([5.0, 5.0], 16.0) == 16.0
+    assert kr.newton_sigma([], 16.0) == 16.0
+
+
+def test_newton_basis_is_better_conditioned_than_the_monomial_basis():
+    """The Newton basis with Leja-ordered Ritz shifts and the capacity scale
+    keeps an s = 10 MPK block of the 64x64 Laplacian far better conditioned
+    than the scaled monomial basis (the motivation for the Newton basis in the
+    paper's discussion of large s); column-equilibrated condition numbers."""
+    A = synth.laplace2d(64)
+    M = kr.as_operator(A)
+    b = M @ synth.x_true(A.n, 0)
+    _, info = kr.sstep_gmres(A, b, m=60, s=10, tol=1e-30, max_restarts=1, theta="auto")
+    th, sig_n = info["theta"], info["sigma"]
+    assert sig_n == 2.0     # the Ritz values fill (0, 8): capacity ~2
+    v = b / np.linalg.norm(b)
+
+    def econd(W):
+        W = np.column_stack([v, W])
+        return np.linalg.cond(W / np.linalg.norm(W, axis=0))
+    c_mono = econd(kr.mpk(M, v, 10, kr.mpk_sigma(A)))
+    c_newt = econd(kr.mpk(M, v, 10, sig_n, th))
+    assert c_mono > 1e7 and c_newt < 1e-4 * c_mono
+
+
+@pytest.mark.parametrize("ortho,s", [("two_stage", 10), ("two_stage", 15), ("bcgs_pip2", 15),
+                                     ("bcgs2_cholqr2", 15)])
+def test_auto_newton_basis_solves_where_the_monomial_basis_breaks_down(ortho, s):
+    """Large s on the 64x64 Laplacian: the monomial basis breaks down in the
+    first cycle (status -4); the auto Newton basis converges to 1e-8 with the
+    forward error within kappa(A) * relres (closed-form eigenvalues), and its
+    final cycle keeps the Arnoldi relation to 1e-12."""
+    N = 64
+    A = synth.laplace2d(N)
+    M = kr.as_operator(A)
+    xt = synth.x_true(A.n, 0)
+    b = M @ xt
+    _, mono = kr.sstep_gmres(A, b, m=60, s=s, tol=1e-8, ortho=ortho)
+    assert mono["status"] == kr.STATUS_BREAKDOWN
+    x, info = kr.sstep_gmres(A, b, m=60, s=s, tol=1e-8, ortho=ortho, theta="auto", return_basis=True)
+    assert info["status"] == 0 and info["restarts"] >= 2
+    rel = np.linalg.norm(M @ x - b) / np.linalg.norm(b)
+    assert rel <= 1e-8
+    lo, hi = checks.laplace2d_extreme_eigs(N)
+    assert np.linalg.norm(x - xt) / np.linalg.norm(xt) <= (hi / lo) * rel
+    assert lo - 1e-9 <= info["theta"].min() and info["theta"].max() <= hi + 1e-9
+    k = info["k"]
+    assert checks.arnoldi_residual(M, info["Q"], info["H"], k) < 1e-12
