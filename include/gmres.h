@@ -39,6 +39,7 @@ extern "C" {
 #define GMRES_ERR_NAN        -5   /* non-finite residual                                   */
 #define GMRES_ERR_TIMEOUT    -6   /* a bounded device wait ran out                         */
 #define GMRES_ERR_WORKSPACE  -7   /* d_work smaller than ortho_workspace_bytes()          */
+#define GMRES_ERR_EIG        -8   /* the QR iteration for the Ritz values did not converge */
 
 /* ---------------------------------------------------------------- options */
 #define GMRES_ORTHO_TWO_STAGE      0  /* §V, Fig. 5: BCGS-PIP per block + BCGS-PIP per big panel   */
@@ -50,6 +51,17 @@ extern "C" {
 #define GMRES_PREC_MIXED           1  /* FP32 basis + MPK, FP64 Gram/Cholesky/Hessenberg, FP64 IR */
 #define GMRES_BASIS_MONOMIAL       0  /* §VI: monomial basis (scaled by a power of two)           */
 #define GMRES_BASIS_NEWTON         1  /* shifted products (A - theta_i I) v, shifts in opts.theta  */
+#define GMRES_BASIS_NEWTON_AUTO    2  /* Newton basis with shifts from the solve itself: the first  */
+                                      /* restart cycle is standard GMRES (s = panel = 1: each      */
+                                      /* vector orthogonalized twice, same kernels); the           */
+                                      /* real parts of its Ritz values (eigenvalues of its k x k    */
+                                      /* Hessenberg matrix) in Leja order give theta_0..theta_{s-1} */
+                                      /* (gmres_newton_shifts) for every later cycle, whose MPK     */
+                                      /* scale is the power of two nearest the shifts' capacity     */
+                                      /* unless opts.sigma > 0.  Per solve: a context that solves   */
+                                      /* again starts again from s = 1.  A breakdown in the first   */
+                                      /* cycle is numbered in its own blocks (m stage-1 blocks of   */
+                                      /* s = 1, then m panels).  Not in the batched engine.          */
 #define GMRES_ARITH_FP64           0  /* native FP64 pipe (default)                                 */
 #define GMRES_ARITH_DD             1  /* opt-in: double-float (hi + lo FP32) on the FP32 pipe:      */
                                       /* error-free products, renormalized sums, ~2^-48 relative;   */
@@ -99,6 +111,10 @@ typedef struct gmres_result {
     double  relres_implicit;   /* |g_{k+1}| / ||b|| of the last least-squares solve        */
     double  relres_true;       /* ||b - A x|| / ||b|| recomputed in FP64 at exit           */
     double  t_mpk_ms, t_stage1_ms, t_stage2_ms, t_ls_ms, t_total_ms;  /* opts.timing = 1  */
+    double  sigma;             /* MPK scale of the last restart cycle                      */
+    double  theta[16];         /* its MPK shifts theta_0..theta_{s-1} (0: monomial); with  */
+                               /* GMRES_BASIS_NEWTON_AUTO the shifts the solve chose, which */
+                               /* a later solve can pass as opts.theta (basis = NEWTON)     */
 } gmres_result;
 
 typedef struct gmres_ctx gmres_ctx;   /* opaque: device CSR copy, Krylov basis, workspace */
@@ -356,6 +372,25 @@ int gmres_server_stop(gmres_server* s);
  * Asynchronous on the context's stream. */
 int gmres_mpk(gmres_ctx* c, const double* v, double* W, int64_t ldw, int32_t s,
               double sigma, const double* theta);
+
+/* ------------------------------------------------ Newton-basis shifts
+ * The shifts GMRES_BASIS_NEWTON_AUTO takes after its first cycle (host code,
+ * no device work; the Newton basis is the better-conditioned alternative to
+ * the monomial basis for large s that the paper names, with Leja-ordered Ritz
+ * values as in Bai, Hu and Reichel 1994).
+ *   H, ldh   HOST k x k upper Hessenberg matrix, column-major (entries below the
+ *            subdiagonal are not read); k = 0 gives theta = 0
+ *   theta    HOST out, s values: the real parts of the eigenvalues of H
+ *            (Francis double-shift QR) in Leja order, the first s, cycled when
+ *            k < s.  Leja order: start at the largest modulus, then the largest
+ *            product of distances to the points taken; candidates scanned in
+ *            ascending order, ties to the first
+ *   sigma    HOST in/out, may be NULL: the power of two nearest (in log2) to the
+ *            capacity (max theta - min theta) / 4 of the shifts' interval;
+ *            unchanged when the shifts span no interval
+ * Returns GMRES_ERR_ARG (0 <= k <= 256, 1 <= s <= 16, ldh >= k) or
+ * GMRES_ERR_EIG (non-finite H, or an eigenvalue took more than 60 sweeps). */
+int gmres_newton_shifts(const double* H, int32_t ldh, int32_t k, int32_t s, double* theta, double* sigma);
 
 #ifdef __cplusplus
 }

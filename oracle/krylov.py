@@ -261,8 +261,8 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
 
     ``panel`` is the second step size s^ of the two-stage scheme (§V); it must
     satisfy s | s^ | m.  ``theta`` is None (monomial basis), s Newton shifts,
-    or "auto": the first cycle runs with s = 1 (standard GMRES through the same
-    block machinery), ``newton_shifts`` turns its Hessenberg matrix into s
+    or "auto": the first cycle runs with s = s^ = 1 (standard GMRES through the
+    same block machinery), ``newton_shifts`` turns its Hessenberg matrix into s
     shifts, and every later cycle uses the Newton basis with them, scaled by
     ``newton_sigma`` unless ``sigma`` is given.  ``ortho`` in {"two_stage", "bcgs_pip2", "bcgs2_cholqr2"}.
     ``basis_dtype=np.float32`` is the mixed-precision pattern: the basis is
@@ -319,9 +319,14 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
             break
         restarts += 1
         # theta = "auto": the first cycle is standard GMRES (s = 1, one SpMV per
-        # block) whose Hessenberg matrix gives the Ritz values for the shifts
-        s = 1 if (auto and th is None) else s_req
-        panel = panel_req if ortho == "two_stage" else s
+        # block) whose Hessenberg matrix gives the Ritz values for the shifts.
+        # For the two-stage scheme it also takes s^ = 1, i.e. every vector is
+        # re-orthogonalized at once (CGS-P twice, the BCGS-PIP2 form): with
+        # s = 1 and a wide big panel the single Pythagorean pass loses
+        # orthogonality as the residual falls and breaks down near convergence.
+        first = auto and th is None
+        s = 1 if first else s_req
+        panel = (1 if first else panel_req) if ortho == "two_stage" else s
         Q = np.zeros((n, m + 1), dtype=basis_dtype)
         Q[:, 0] = r / beta
         Rhat = np.zeros((m + 1, m + 1))

@@ -23,6 +23,7 @@ GMRES_ERR_BREAKDOWN = -4
 GMRES_ERR_NAN = -5
 GMRES_ERR_TIMEOUT = -6
 GMRES_ERR_WORKSPACE = -7
+GMRES_ERR_EIG = -8
 
 GMRES_ORTHO_TWO_STAGE = 0
 GMRES_ORTHO_BCGS_PIP2 = 1
@@ -31,6 +32,7 @@ GMRES_PREC_FP64 = 0
 GMRES_PREC_MIXED = 1
 GMRES_BASIS_MONOMIAL = 0
 GMRES_BASIS_NEWTON = 1
+GMRES_BASIS_NEWTON_AUTO = 2
 GMRES_ARITH_FP64 = 0
 GMRES_ARITH_DD = 1
 GMRES_ARITH_TC = 2
@@ -60,10 +62,13 @@ class gmres_result(C.Structure):
                 ("breakdown_block", C.c_int32), ("breakdown_pivot", C.c_int32),
                 ("relres_implicit", C.c_double), ("relres_true", C.c_double),
                 ("t_mpk_ms", C.c_double), ("t_stage1_ms", C.c_double), ("t_stage2_ms", C.c_double),
-                ("t_ls_ms", C.c_double), ("t_total_ms", C.c_double)]
+                ("t_ls_ms", C.c_double), ("t_total_ms", C.c_double),
+                ("sigma", C.c_double), ("theta", C.c_double * 16)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["theta"] = list(self.theta)
+        return d
 
 
 _vp, _i32, _i64, _sz, _dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t, C.c_double
@@ -104,6 +109,7 @@ SIGNATURES = {
     "gmres_server_poll": (_i32, [_vp, _i64, _vp, C.POINTER(gmres_result)]),
     "gmres_server_get_stats": (_i32, [_vp, C.POINTER(gmres_server_stats)]),
     "gmres_server_stop": (_i32, [_vp]),
+    "gmres_newton_shifts": (_i32, [_vp, _i32, _i32, _i32, C.POINTER(_dbl), C.POINTER(_dbl)]),
     "ortho_stage1_noalloc": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp]),
 }
 
@@ -450,3 +456,20 @@ def ortho_stage2(Q, V, R, work, status, k=None, stream=None):
     """BCGS-PIP of the big panel V against the first k columns of Q (stage 2 of §V)."""
     k = (Q.shape[1] if Q is not None else 0) if k is None else k
     return check(_ortho(load().ortho_stage2, Q, V, R, work, status, k, stream))
+
+
+def newton_shifts(H, s, sigma=None):
+    """gmres_newton_shifts: the Newton-basis shifts from the k x k upper
+    Hessenberg matrix H (host array-like) and, when ``sigma`` is given, the
+    capacity scale (``sigma`` returned unchanged when the shifts span no
+    interval).  Returns (theta[s] as a numpy array, sigma or None)."""
+    import numpy as np
+    Hh = np.asfortranarray(np.asarray(H, dtype=np.float64))
+    k = Hh.shape[0]
+    if Hh.ndim != 2 or Hh.shape[1] != k:
+        raise ValueError("H must be square")
+    th = (C.c_double * int(s))()
+    sg = C.c_double(float(sigma)) if sigma is not None else None
+    hp = Hh.ctypes.data if k else None
+    check(load().gmres_newton_shifts(hp, max(k, 1), int(k), int(s), th, C.byref(sg) if sg is not None else None))
+    return np.array(th[:], dtype=np.float64), (sg.value if sg is not None else None)

@@ -550,6 +550,8 @@ int gmres_batch_create(gmres_batch** out, int32_t nsys, const int64_t* n, const 
            "arith must be GMRES_ARITH_FP64 or GMRES_ARITH_DD for batches");
     GM_ARG(o.ortho == GMRES_ORTHO_TWO_STAGE || o.ortho == GMRES_ORTHO_BCGS_PIP2,
            "ortho must be GMRES_ORTHO_TWO_STAGE or GMRES_ORTHO_BCGS_PIP2 for batches");
+    GM_ARG(o.basis == GMRES_BASIS_MONOMIAL || o.basis == GMRES_BASIS_NEWTON,
+           "basis must be GMRES_BASIS_MONOMIAL or GMRES_BASIS_NEWTON for batches (pass the shifts in opts.theta)");
     gmres_batch* c = new gmres_batch();
     c->opts = o;
     c->nsys = nsys;

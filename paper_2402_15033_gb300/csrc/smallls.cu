@@ -5,7 +5,15 @@ namespace gm {
 
 namespace {
 
-__global__ void cycle_begin_kernel(DevState* st) { cycle_begin_body(st, 0); }
+__global__ void cycle_begin_kernel(DevState* st, CycleBasis cb) {
+    if (threadIdx.x == 0) {
+        st->s = cb.s;
+        st->panel = cb.panel;
+        st->sigma = cb.sigma;
+    }
+    if (threadIdx.x < 16) st->theta[threadIdx.x] = cb.theta[threadIdx.x];
+    cycle_begin_body(st, 0);
+}
 
 __global__ void __launch_bounds__(256) hessenberg_ls_kernel(DevState* st, int lo, int t) {
     hessenberg_ls_body(st, lo, t);
@@ -20,8 +28,8 @@ __global__ void __launch_bounds__(256) eye_panel_kernel(DevState* st, int lo, in
 
 }  // namespace
 
-cudaError_t launch_cycle_begin(cudaStream_t st, DevState* ds) {
-    cycle_begin_kernel<<<1, 64, 0, st>>>(ds);
+cudaError_t launch_cycle_begin(cudaStream_t st, DevState* ds, const CycleBasis& cb) {
+    cycle_begin_kernel<<<1, 64, 0, st>>>(ds, cb);
     return cudaGetLastError();
 }
 

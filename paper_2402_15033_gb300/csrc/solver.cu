@@ -91,6 +91,7 @@ namespace gm {
 
 enum { PH_MPK = 0, PH_S1 = 1, PH_S2 = 2, PH_LS = 3 };
 
+CycleBasis first_cycle_basis(const gmres_opts& o, double sigma);
 size_t pip_bytes_for(int64_t n, const gmres_opts& o);
 size_t ctx_bytes(int64_t n, int64_t nnz, const gmres_opts& o);
 bool uses_digits(const gmres_opts& o);
@@ -128,16 +129,35 @@ size_t ortho_workspace_bytes(int64_t n, int32_t k, int32_t nb) {
 
 namespace gm {
 
+// Basis of a solve's first restart cycle: the options' own, or for
+// GMRES_BASIS_NEWTON_AUTO standard GMRES, s = 1 with the two-stage panel also
+// 1 (each vector re-orthogonalized at once; a single Pythagorean pass over a
+// wide panel of s = 1 blocks loses orthogonality as the residual falls).
+CycleBasis first_cycle_basis(const gmres_opts& o, double sigma) {
+    CycleBasis cb;
+    const bool aut = o.basis == GMRES_BASIS_NEWTON_AUTO;
+    cb.s = aut ? 1 : o.s;
+    cb.panel = (o.ortho == GMRES_ORTHO_TWO_STAGE && !aut) ? o.panel : cb.s;
+    cb.sigma = sigma;
+    for (int i = 0; i < 16; ++i) cb.theta[i] = (o.basis == GMRES_BASIS_NEWTON && i < o.s) ? o.theta[i] : 0.0;
+    return cb;
+}
+
 size_t pip_bytes_for(int64_t n, const gmres_opts& o) {
     size_t wb = 0;
-    for (int st0 = 0; st0 < o.m; st0 += o.s) {
-        wb = std::max(wb, ortho_workspace_bytes(n, st0 + 1, o.s));
-        const int t = st0 + o.s;
-        if (t % o.panel == 0) {
-            const int lo = (t == o.panel) ? 0 : t - o.panel + 1;
-            wb = std::max(wb, ortho_workspace_bytes(n, lo, t - lo + 1));
+    auto cover = [&](int s, int panel) {
+        for (int st0 = 0; st0 < o.m; st0 += s) {
+            wb = std::max(wb, ortho_workspace_bytes(n, st0 + 1, s));
+            const int t = st0 + s;
+            if (t % panel == 0) {
+                const int lo = (t == panel) ? 0 : t - panel + 1;
+                wb = std::max(wb, ortho_workspace_bytes(n, lo, t - lo + 1));
+            }
         }
-    }
+    };
+    cover(o.s, o.panel);
+    const CycleBasis f = first_cycle_basis(o, 1.0);
+    if (f.s != o.s) cover(f.s, f.panel);
     return wb;
 }
 
@@ -177,7 +197,8 @@ static int check_opts(const gmres_opts* o) {
                o->ortho == GMRES_ORTHO_BCGS2_CHOLQR2,
            "unknown ortho");
     GM_ARG(o->precision == GMRES_PREC_FP64 || o->precision == GMRES_PREC_MIXED, "unknown precision");
-    GM_ARG(o->basis == GMRES_BASIS_MONOMIAL || o->basis == GMRES_BASIS_NEWTON, "unknown basis");
+    GM_ARG(o->basis == GMRES_BASIS_MONOMIAL || o->basis == GMRES_BASIS_NEWTON || o->basis == GMRES_BASIS_NEWTON_AUTO,
+           "unknown basis");
     const int panel = o->ortho != GMRES_ORTHO_TWO_STAGE ? o->s : o->panel;
     GM_ARG(panel >= o->s && panel % o->s == 0 && o->m % panel == 0, "need s | panel | m");
     GM_ARG(o->sigma >= 0.0 && std::isfinite(o->sigma), "sigma must be >= 0");
@@ -351,7 +372,8 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
     CK(cuda_rc(cudaMemcpyAsync(c->st, c->hst, sizeof(DevState), cudaMemcpyHostToDevice, s), "state upload"));
     CK(cuda_rc(cudaStreamSynchronize(s), "sync"));
     if (o.timing) {
-        const int per_cycle = 2 * (2 * (o.m / o.s) + 2 * (o.m / o.panel)) + 2;
+        const CycleBasis f = first_cycle_basis(o, c->sigma);
+        const int per_cycle = 2 * (2 * (o.m / std::min(o.s, f.s)) + 2 * (o.m / std::min(o.panel, f.panel))) + 2;
         c->ev.resize(per_cycle);
         for (auto& e : c->ev) CK(cuda_rc(cudaEventCreate(&e), "cudaEventCreate"));
     }
@@ -363,13 +385,13 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
 }  // extern "C"
 
 template <typename T>
-static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
+static int run_cycle(gmres_ctx* c, const CycleBasis& cb, std::vector<std::pair<int, int>>* marks) {
     const gmres_opts& o = c->opts;
     cudaStream_t s = c->stream;
     DevState* ds = c->st;
     int32_t* done = &ds->done;
     T* basis = static_cast<T*>(c->basis);
-    const double sinv = 1.0 / c->sigma;
+    const double sinv = 1.0 / cb.sigma;
     PipWork w{};
     int evi = 0;
     auto mark = [&](int phase) -> cudaError_t {
@@ -377,19 +399,19 @@ static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
         marks->push_back({phase, evi});
         return cudaEventRecord(c->ev[evi++], s);
     };
-    const int nblk = o.m / o.s;
+    const int nblk = o.m / cb.s;
     int panel_idx = 0;
-    cudaError_t e = launch_cycle_begin(s, ds);
+    cudaError_t e = launch_cycle_begin(s, ds, cb);
     if (e == cudaSuccess) e = launch_scale(s, c->n, c->r ? c->r : static_cast<double*>(c->basis), basis, ds);
     const int capc = o.m + 1;
     void* dig = (sizeof(T) == sizeof(double)) ? c->digits : nullptr;   // the digit basis (tensor-core arithmetic)
     if (e == cudaSuccess && dig)
         e = launch_digits_fill_cols(s, c->n, reinterpret_cast<const double*>(basis), c->ldq, 0, 1, dig, capc);
     for (int j = 0; j < nblk && e == cudaSuccess; ++j) {
-        const int st0 = j * o.s;
+        const int st0 = j * cb.s;
         e = mark(PH_MPK);
-        for (int i = 0; i < o.s && e == cudaSuccess; ++i) {
-            const double th = c->hst->theta[i];
+        for (int i = 0; i < cb.s && e == cudaSuccess; ++i) {
+            const double th = cb.theta[i];
             e = launch_spmv(s, c->A, basis + (size_t)(st0 + i) * c->ldq, basis + (size_t)(st0 + i + 1) * c->ldq,
                             th, sinv, done);
         }
@@ -397,7 +419,7 @@ static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
         if (e == cudaSuccess) e = mark(PH_S1);
         if (e == cudaSuccess) {
             const int k = st0 + 1;
-            w = pip_work_layout(c->pip_work, c->n, k, o.s);
+            w = pip_work_layout(c->pip_work, c->n, k, cb.s);
             T* V = basis + (size_t)k * c->ldq;
             double* R = ds->Rhat + (size_t)k * kMaxCols;
             int32_t* stat = &ds->blkstat[j];
@@ -407,7 +429,7 @@ static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
                 const int grid = reduction_grid(c->n);
                 const size_t SB = (size_t)kMaxCols * kMaxCols;
                 double* S = c->bscr;
-                PipWork w0 = pip_work_layout(c->pip_work, c->n, 0, o.s);
+                PipWork w0 = pip_work_layout(c->pip_work, c->n, 0, cb.s);
                 struct Step { int kk; double* R; int gmode; int umode; };
                 const Step steps[5] = {{k, S, kPipGramOnly, kPipNoTrsm},     // P1, V <- V - Q P1
                                        {0, S + SB, 0, 0},                    // T1a, V <- V T1a^{-1}
@@ -417,52 +439,52 @@ static int run_cycle(gmres_ctx* c, std::vector<std::pair<int, int>>* marks) {
                 for (int q = 0; q < 5 && e == cudaSuccess; ++q) {
                     const Step& st_ = steps[q];
                     const PipWork& wq = st_.kk ? w : w0;
-                    e = launch_pip_gram_chol(s, c->n, basis, c->ldq, st_.kk, V, c->ldq, o.s, st_.R, kMaxCols, wq, stat,
+                    e = launch_pip_gram_chol(s, c->n, basis, c->ldq, st_.kk, V, c->ldq, cb.s, st_.R, kMaxCols, wq, stat,
                                              done, grid, st_.gmode, o.arith);
                     if (e == cudaSuccess)
-                        e = launch_pip_update(s, c->n, basis, c->ldq, st_.kk, V, c->ldq, o.s, st_.R, kMaxCols, stat,
+                        e = launch_pip_update(s, c->n, basis, c->ldq, st_.kk, V, c->ldq, cb.s, st_.R, kMaxCols, stat,
                                               done, st_.umode, o.arith);
                 }
-                if (e == cudaSuccess) e = launch_bcgs2_combine(s, ds, k, o.s, S, R);
+                if (e == cudaSuccess) e = launch_bcgs2_combine(s, ds, k, cb.s, S, R);
             } else if (sizeof(T) == sizeof(double) && dig) {
                 // BCGS-PIP (Fig. 4a) on the tensor cores, the accumulated columns'
                 // digits read from the digit basis, the block's written back
                 const double* Bd = reinterpret_cast<const double*>(basis);
-                e = launch_gram_tc_digits(s, c->n, Bd, c->ldq, k, reinterpret_cast<const double*>(V), c->ldq, o.s, R,
+                e = launch_gram_tc_digits(s, c->n, Bd, c->ldq, k, reinterpret_cast<const double*>(V), c->ldq, cb.s, R,
                                           kMaxCols, w, stat, reduction_grid(c->n), dig, capc, k, done);
                 if (e == cudaSuccess)
-                    e = launch_update_tc_digits(s, c->n, Bd, c->ldq, k, reinterpret_cast<double*>(V), c->ldq, o.s, R,
+                    e = launch_update_tc_digits(s, c->n, Bd, c->ldq, k, reinterpret_cast<double*>(V), c->ldq, cb.s, R,
                                                 kMaxCols, stat, dig, capc, done);
             } else if (sizeof(T) == sizeof(double)) {
                 // BCGS-PIP (Fig. 4a): one reduction, Pythagorean Gram
-                e = launch_pip_gram_chol(s, c->n, basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, w, stat, done,
+                e = launch_pip_gram_chol(s, c->n, basis, c->ldq, k, V, c->ldq, cb.s, R, kMaxCols, w, stat, done,
                                          reduction_grid(c->n), 0, o.arith);
                 if (e == cudaSuccess)
-                    e = launch_pip_update(s, c->n, basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, stat, done, 0,
+                    e = launch_pip_update(s, c->n, basis, c->ldq, k, V, c->ldq, cb.s, R, kMaxCols, stat, done, 0,
                                           o.arith);
             } else {
                 // FP32 basis: project, then CholQR of the projected block with an
                 // explicit FP64 Gram (the Pythagorean identity needs an
                 // orthonormal stored basis, which FP32 storage is only to ~1e-7)
-                e = launch_pip_gram_chol(s, c->n, basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, w, stat, done,
+                e = launch_pip_gram_chol(s, c->n, basis, c->ldq, k, V, c->ldq, cb.s, R, kMaxCols, w, stat, done,
                                          reduction_grid(c->n), kPipGramOnly, o.arith);
                 if (e == cudaSuccess)
-                    e = launch_pip_update(s, c->n, basis, c->ldq, k, V, c->ldq, o.s, R, kMaxCols, stat, done,
+                    e = launch_pip_update(s, c->n, basis, c->ldq, k, V, c->ldq, cb.s, R, kMaxCols, stat, done,
                                           kPipNoTrsm, o.arith);
                 if (e == cudaSuccess) {
-                    PipWork w0 = pip_work_layout(c->pip_work, c->n, 0, o.s);
-                    e = launch_pip_gram_chol(s, c->n, basis, c->ldq, 0, V, c->ldq, o.s, R + k, kMaxCols, w0, stat,
+                    PipWork w0 = pip_work_layout(c->pip_work, c->n, 0, cb.s);
+                    e = launch_pip_gram_chol(s, c->n, basis, c->ldq, 0, V, c->ldq, cb.s, R + k, kMaxCols, w0, stat,
                                              done, reduction_grid(c->n), 0, o.arith);
                 }
                 if (e == cudaSuccess)
-                    e = launch_pip_update(s, c->n, basis, c->ldq, 0, V, c->ldq, o.s, R + k, kMaxCols, stat, done, 0,
+                    e = launch_pip_update(s, c->n, basis, c->ldq, 0, V, c->ldq, cb.s, R + k, kMaxCols, stat, done, 0,
                                           o.arith);
             }
         }
         if (e == cudaSuccess) e = mark(PH_S1);
-        const int t = st0 + o.s;
-        if (e == cudaSuccess && t % o.panel == 0) {
-            const int lo = (t == o.panel) ? 0 : t - o.panel + 1;
+        const int t = st0 + cb.s;
+        if (e == cudaSuccess && t % cb.panel == 0) {
+            const int lo = (t == cb.panel) ? 0 : t - cb.panel + 1;
             const int np = t - lo + 1;
             e = mark(PH_S2);
             w = pip_work_layout(c->pip_work, c->n, lo, np);
@@ -526,6 +548,10 @@ int run_begin(gmres_ctx* c, SolveRun* R, const double* b, const double* x, int o
     if (cudaSetDevice(c->device) != cudaSuccess) return cuda_rc(cudaGetLastError(), "cudaSetDevice");
     cudaStream_t s = c->stream;
     const gmres_opts& o = c->opts;
+    R->cb = R->ran = first_cycle_basis(o, c->sigma);
+    R->auto_pending = o.basis == GMRES_BASIS_NEWTON_AUTO;
+    R->r.sigma = R->cb.sigma;
+    for (int i = 0; i < 16; ++i) R->r.theta[i] = R->cb.theta[i];
     const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const size_t vb = c->n * sizeof(double);
     if (o.timing) {
@@ -591,14 +617,14 @@ int run_decide(SolveRun* R) {
     r.restarts = cyc;
     r.relres_true = h.beta / R->bnorm;
     if (cyc > 0) r.relres_implicit = h.resid / R->bnorm;
-    const int nstat = o.m / o.s + o.m / o.panel;
+    const int nb1 = o.m / R->ran.s;
+    const int nstat = nb1 + o.m / R->ran.panel;
     for (int i = 0; i < nstat; ++i) {
         if (h.blkstat[i]) {
             r.breakdown_block = i;
             r.breakdown_pivot = h.blkstat[i];
             set_error("Cholesky breakdown in %s %d at pivot %d (restart cycle %d)",
-                      i < o.m / o.s ? "stage-1 block" : "stage-2 panel",
-                      i < o.m / o.s ? i : i - o.m / o.s, h.blkstat[i], cyc - 1);
+                      i < nb1 ? "stage-1 block" : "stage-2 panel", i < nb1 ? i : i - nb1, h.blkstat[i], cyc - 1);
             R->status = GMRES_ERR_BREAKDOWN;
             return (R->finished = true), 1;
         }
@@ -607,6 +633,23 @@ int run_decide(SolveRun* R) {
         set_error("non-finite residual norm");
         R->status = GMRES_ERR_NAN;
         return (R->finished = true), 1;
+    }
+    if (cyc > 0 && R->auto_pending) {
+        // the first cycle was standard GMRES: its k x k Hessenberg matrix gives
+        // the Ritz values; the Newton basis takes them as shifts from now on
+        CycleBasis& nb = R->cb;
+        nb.s = o.s;
+        nb.panel = o.ortho == GMRES_ORTHO_TWO_STAGE ? o.panel : o.s;
+        for (int i = 0; i < 16; ++i) nb.theta[i] = 0.0;
+        const int rc = newton_shifts(h.H, kMaxCols, h.k_used, o.s, nb.theta);
+        if (rc) {
+            R->status = rc;
+            return (R->finished = true), 1;
+        }
+        nb.sigma = o.sigma > 0.0 ? c->sigma : newton_sigma(nb.theta, o.s, c->sigma);
+        R->auto_pending = false;
+        r.sigma = nb.sigma;
+        for (int i = 0; i < 16; ++i) r.theta[i] = nb.theta[i];
     }
     if (h.beta <= o.tol * R->bnorm) { R->status = GMRES_OK; return (R->finished = true), 1; }
     if (cyc >= o.max_restarts) { R->status = GMRES_WARN_MAXIT; return (R->finished = true), 1; }
@@ -617,8 +660,9 @@ int run_enqueue_cycle(SolveRun* R) {
     gmres_ctx* c = R->c;
     const gmres_opts& o = c->opts;
     R->marks.clear();
-    const int rc = o.precision == GMRES_PREC_MIXED ? run_cycle<float>(c, o.timing ? &R->marks : nullptr)
-                                                   : run_cycle<double>(c, o.timing ? &R->marks : nullptr);
+    R->ran = R->cb;
+    const int rc = o.precision == GMRES_PREC_MIXED ? run_cycle<float>(c, R->cb, o.timing ? &R->marks : nullptr)
+                                                   : run_cycle<double>(c, R->cb, o.timing ? &R->marks : nullptr);
     if (o.precision == GMRES_PREC_MIXED) ++R->r.ir_steps;
     ++R->cyc;
     return rc;

@@ -14,6 +14,9 @@ struct SolveRun {
     int status = GMRES_WARN_MAXIT;
     int on_device = 0;
     bool finished = false;
+    CycleBasis cb;               // basis of the next restart cycle
+    CycleBasis ran;              // basis of the last cycle enqueued
+    bool auto_pending = false;   // GMRES_BASIS_NEWTON_AUTO before its shifts are chosen
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     std::vector<std::pair<int, int>> marks;
 };

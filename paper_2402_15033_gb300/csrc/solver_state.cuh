@@ -43,6 +43,19 @@ struct DevState {
     double Rg[kMaxCols * kMaxCols];    // H after the Givens rotations
 };
 
+// Basis of one restart cycle: step size, panel, MPK scale and shifts.  The
+// cycle-begin kernel writes it into DevState, so cycles of one solve may
+// differ (GMRES_BASIS_NEWTON_AUTO runs its first cycle with s = 1).
+struct CycleBasis {
+    int32_t s = 1, panel = 1;
+    double sigma = 1.0;
+    double theta[16] = {};
+};
+
+// Newton-basis shifts and scale from a k x k Hessenberg matrix (newton.cu, host)
+int newton_shifts(const double* H, int ldh, int k, int s, double* theta);
+double newton_sigma(const double* theta, int s, double fallback);
+
 int norm_grid(int64_t n);
 cudaError_t launch_spmv(cudaStream_t st, const DevCSR& A, const double* x, double* y, double theta,
                         double sinv, const int32_t* d_skip);
@@ -59,7 +72,7 @@ cudaError_t launch_validate_csr(cudaStream_t st, int64_t n, int64_t nnz, const i
                                 const int32_t* colind, int32_t* bad);
 cudaError_t launch_rowabs(cudaStream_t st, const DevCSR& A, unsigned long long* out);
 cudaError_t launch_rowptr_narrow(cudaStream_t st, int64_t m, const int64_t* in, int32_t* out);
-cudaError_t launch_cycle_begin(cudaStream_t st, DevState* ds);
+cudaError_t launch_cycle_begin(cudaStream_t st, DevState* ds, const CycleBasis& cb);
 cudaError_t launch_hessenberg_ls(cudaStream_t st, DevState* ds, int lo, int t);
 // BCGS2-CholQR2 block factor from the five reductions' factors (S: 5 blocks of kMaxCols^2)
 cudaError_t launch_bcgs2_combine(cudaStream_t st, const DevState* ds, int k, int s, const double* S, double* R);

@@ -40,7 +40,8 @@ def test_library_exports_every_declared_symbol(capi):
 
 def test_struct_layouts_match_the_header(capi):
     assert C.sizeof(capi.gmres_opts) == 216
-    assert C.sizeof(capi.gmres_result) == 80
+    assert C.sizeof(capi.gmres_result) == 216      # 6 int32, 8 doubles, theta[16]
+    assert capi.gmres_result.sigma.offset == 80 and capi.gmres_result.theta.offset == 88
     assert capi.gmres_opts.tol.offset == 16
     assert capi.gmres_opts.theta.offset == 48
     assert capi.gmres_result.relres_implicit.offset == 24
