@@ -554,6 +554,23 @@ def solver_numbers(capi, dev, args):
     S1.close()
     out["laplace64_tc"] = {"time_to_solution_ms": round(1e3 * statistics.median(times), 3), "status": rc,
                            "iters": res["iters"], "relres": res["relres_true"]}
+    # s = 10: the monomial basis breaks down on this system; the Newton basis with
+    # automatic shifts (first cycle standard GMRES) solves it
+    for aname, arith in (("fp64", capi.GMRES_ARITH_FP64), ("tc", capi.GMRES_ARITH_TC)):
+        S1 = capi.Solver.from_csr(A, capi.default_opts(m=60, s=10, panel=60, tol=1e-8, arith=arith,
+                                                       basis=capi.GMRES_BASIS_NEWTON_AUTO))
+        S1.solve(bd, xd)
+        times = []
+        for _ in range(5):
+            xd.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, res = S1.solve(bd, xd)
+            times.append(time.perf_counter() - t0)
+        S1.close()
+        out[f"laplace64_s10_newton_auto_{aname}"] = {
+            "time_to_solution_ms": round(1e3 * statistics.median(times), 3), "status": rc, "iters": res["iters"],
+            "restarts": res["restarts"], "relres": res["relres_true"], "sigma": res["sigma"]}
     # 2048 x 2048 Laplace: one restart cycle (60 iterations), per-phase times, for
     # the two-stage scheme and the paper's one-stage comparisons (BCGS-PIP2 and the
     # BCGS2-CholQR2 baseline of §VIII), FP64 and tensor-core arithmetic
@@ -604,9 +621,16 @@ def mixed_numbers(capi, dev):
     bd = torch.tensor(b, device=dev)
     out = {"grid": "160^3", "n": A.n}
     xs = {}
-    for name, prec in (("mixed", capi.GMRES_PREC_MIXED), ("fp64", capi.GMRES_PREC_FP64)):
+    auto = capi.GMRES_BASIS_NEWTON_AUTO
+    runs = (("mixed", capi.GMRES_PREC_MIXED, 0, 0), ("fp64", capi.GMRES_PREC_FP64, 0, 0),
+            # the Newton basis with automatic Leja-ordered Ritz shifts, where the
+            # monomial basis breaks down at s = 10
+            ("mixed_newton_auto", capi.GMRES_PREC_MIXED, auto, 0),
+            ("fp64_newton_auto", capi.GMRES_PREC_FP64, auto, capi.GMRES_ARITH_FP64),
+            ("tc_newton_auto", capi.GMRES_PREC_FP64, auto, capi.GMRES_ARITH_TC))
+    for name, prec, basis, arith in runs:
         S = capi.Solver.from_csr(A, capi.default_opts(m=60, s=10, panel=60, tol=1e-8, precision=prec,
-                                                      max_restarts=2000))
+                                                      max_restarts=2000, basis=basis, arith=arith))
         xd = torch.zeros(A.n, dtype=torch.float64, device=dev)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -619,9 +643,15 @@ def mixed_numbers(capi, dev):
                      "restarts": res["restarts"], "ir_steps": res["ir_steps"], "relres": res["relres_true"],
                      "err_vs_x_true": float(np.linalg.norm(x - xt) / np.linalg.norm(xt)),
                      "breakdown_block": res["breakdown_block"]}
-    if xs["mixed"][0] == 0 and xs["fp64"][0] == 0:
-        out["mixed"]["err_vs_fp64"] = float(np.linalg.norm(xs["mixed"][1] - xs["fp64"][1]) /
-                                            np.linalg.norm(xs["fp64"][1]))
+        if basis == auto:
+            out[name]["sigma"] = res["sigma"]
+            out[name]["theta"] = [round(t, 6) for t in res["theta"][:10]]
+    ref = "fp64" if xs["fp64"][0] == 0 else ("fp64_newton_auto" if xs["fp64_newton_auto"][0] == 0 else None)
+    if ref:
+        for name in out:
+            if isinstance(out[name], dict) and name != ref and xs.get(name, (1,))[0] == 0:
+                out[name]["err_vs_" + ref] = float(np.linalg.norm(xs[name][1] - xs[ref][1]) /
+                                                   np.linalg.norm(xs[ref][1]))
     return out
 
 
