@@ -260,13 +260,16 @@ int ortho_update_tc(void* stream, int64_t n, const double* Q, int64_t ldq, int32
  * every FP64 value (per 64-row chunk of a column), kept in device memory so that
  * a basis column is sliced once however many blocks later read it (stage 1
  * projects every block against all accumulated columns, §V).  No counterpart in
- * the paper; results are bit-identical to the ortho_*_tc calls.
+ * the paper.
  *   ortho_digits_bytes: size of a digit basis of capc columns for n rows
  *                       (about 14 bytes per value); capc <= 64.
  *   ortho_digits_fill:  slice X(:, 0:nc) into digit columns c0 .. c0+nc-1.
  *   ortho_gram_chol_tcd: ortho_gram_chol_tc whose first kc columns of [Q, V]
  *                       (kc <= k + nb) are read from digit columns 0 .. kc-1,
- *                       which must hold exactly those columns' current values.
+ *                       which must hold exactly those columns' current values;
+ *                       bit-identical to ortho_gram_chol_tc, except that with
+ *                       kc = k and nb <= 8 a pipelined kernel (bulk copies of
+ *                       the chunks' digit columns) runs and agrees to rounding.
  *   ortho_update_tcd:   ortho_update_tc that also writes the digits of the new V
  *                       into digit columns k .. k+nb-1; for nb <= 8 it reads Q's
  *                       digits from digit columns 0 .. k-1 (which must hold Q)

@@ -117,7 +117,7 @@ __device__ void gram_tc_part(int64_t n, const double* __restrict__ Q, int64_t ld
                 cp_async16(sl + (size_t)(c * 2 + (u >> 5)) * kTcWp + (u & 31), src + e, 16);
             }
             cp_async_commit();
-            for (int c = threadIdx.x; c < kc; c += blockDim.x) ex[c] = dex[(size_t)ci * capc + c];
+            for (int c = threadIdx.x; c < kc; c += blockDim.x) ex[c] = dex[(size_t)ci * tc_dex_stride(capc) + c];
         }
         // 1. per other column (one warp): exponent of the chunk maximum, then the
         //    digit slices; lane l holds rows 2l and 2l + 1

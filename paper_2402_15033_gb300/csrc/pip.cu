@@ -24,6 +24,7 @@
 #include <type_traits>
 #include "pip_body.cuh"
 #include "gram_tc.cuh"
+#include "gram_tcq.cuh"
 #include "update_tc.cuh"
 #include "update_tcd.cuh"
 
@@ -74,6 +75,39 @@ gram_tc_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
     const size_t ps = (size_t)kMaxNB * nb;
     gram_tc_part(n, Q, ldq, k, V, ldv, nb, blockIdx.x, G, partial + blockIdx.x * ps, smem, dig, dex, capc, kc);
     pip_finish(k, nb, 0, 1, G, R, ldr, partial, ps, counter, gram, d_status, d_skip, smem, mode);
+}
+
+// Narrow Gram with every Q column from the digit basis (gram_tcq.cuh): one CTA
+// per SM, a producer warp bulk-copying the chunks, slicer and MMA warps.
+__global__ void __launch_bounds__(kGqThreads, 1)
+gram_tcq_kernel(int64_t n, const double* __restrict__ V, int64_t ldv, int k, int nb, double* __restrict__ R, int ldr,
+                double* partial, unsigned* counter, double* gram, int32_t* d_status, int32_t* d_skip, int mode,
+                const uint4* dig, const int* dex, int capc) {
+    extern __shared__ __align__(16) char gq_smem[];
+    if (d_skip && *d_skip) return;
+    const int G = gridDim.x;
+    const size_t ps = (size_t)kMaxNB * nb;
+    gram_tcq_part(n, V, ldv, k, nb, blockIdx.x, G, partial + blockIdx.x * ps, gq_smem, dig, dex, capc);
+    pip_finish(k, nb, 0, 1, G, R, ldr, partial, ps, counter, gram, d_status, d_skip,
+               reinterpret_cast<double*>(gq_smem), mode);
+}
+
+cudaError_t launch_gram_tcq(cudaStream_t st, int64_t n, int k, const double* V, int64_t ldv, int nb, double* R,
+                            int ldr, const PipWork& w, int32_t* d_status, int32_t* d_skip, int grid, int mode,
+                            const void* digits, int capc) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(gram_tcq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)gram_tcq_smem(kGqMaxKX - 1));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const uint4* dig = static_cast<const uint4*>(digits);
+    const int* dex = reinterpret_cast<const int*>(dig + tc_digits_units(n, capc));
+    const int G = std::min(grid, num_sms());
+    gram_tcq_kernel<<<G, kGqThreads, gram_tcq_smem(k), st>>>(n, V, ldv, k, nb, R, ldr, w.partial, w.counter,
+                                                             w.gram, d_status, d_skip, mode, dig, dex, capc);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gram_tc(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k,
@@ -480,6 +514,9 @@ cudaError_t launch_pip_update(cudaStream_t st, int64_t n, const float* Q, int64_
 cudaError_t launch_gram_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, const double* V,
                                   int64_t ldv, int nb, double* R, int ldr, const PipWork& w, int32_t* d_status,
                                   int grid, const void* digits, int capc, int kc, int32_t* d_skip) {
+    // narrow blocks against a Q held entirely in the digit basis: per-warp streaming
+    if (nb <= kGqMaxNB && kc == k && k + nb <= kGqMaxKX)
+        return launch_gram_tcq(st, n, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, 0, digits, capc);
     return launch_gram_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, 0, digits, capc, kc);
 }
 cudaError_t launch_update_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, double* V,

@@ -178,14 +178,16 @@ __device__ __forceinline__ void tc_stage64(const double* Q, int64_t ldq, int k, 
 // a column is sliced once however often it is read.  For 64-row chunk ch and
 // column c, units [(ch * capc + c) * 64, +64) hold the 32 row pairs' digits
 // 0-3 (units 0-31) and 4-6 (units 32-63) in the shared-memory unit format of the
-// Gram kernel (without its padding), and exps[ch * capc + c] the chunk column's
-// unbiased exponent (kTcBadExp for a NaN or infinity).  The exponents follow
-// the units in one buffer.
+// Gram kernel (without its padding), and exps[ch * tc_dex_stride(capc) + c] the
+// chunk column's unbiased exponent (kTcBadExp for a NaN or infinity).  The
+// exponents follow the units in one buffer; a chunk's row of exponents starts
+// on a 16-byte boundary, so that one bulk copy can fetch it.
 __host__ __device__ inline size_t tc_digits_units(int64_t n, int capc) {
     return (size_t)((n + 63) / 64) * (size_t)capc * 64;
 }
+__host__ __device__ inline int tc_dex_stride(int capc) { return (capc + 3) & ~3; }
 __host__ __device__ inline size_t tc_digits_bytes(int64_t n, int capc) {
-    return tc_digits_units(n, capc) * 16 + (size_t)((n + 63) / 64) * (size_t)capc * sizeof(int) + 256;
+    return tc_digits_units(n, capc) * 16 + (size_t)((n + 63) / 64) * (size_t)tc_dex_stride(capc) * sizeof(int) + 256;
 }
 
 // Slice column c of a 64-row chunk (lane l holds rows 2l, 2l+1: x0, x1) into
@@ -206,7 +208,7 @@ __device__ __forceinline__ void tc_digits_store(double x0, double x1, int64_t ch
     uint4* u = units + ((size_t)ch * capc + c) * 64;
     u[lane] = lo;
     u[32 + lane] = hi;
-    if (lane == 0) exps[(size_t)ch * capc + c] = bad ? kTcBadExp : eb - 1023;
+    if (lane == 0) exps[(size_t)ch * tc_dex_stride(capc) + c] = bad ? kTcBadExp : eb - 1023;
 }
 
 }  // namespace gm

@@ -126,7 +126,7 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
             const uint4* src = dig + (size_t)ci * capc * 64;
             for (int e = tid; e < k * 64; e += blockDim.x) cp_async16(xu + (e >> 6) * kUdXs + (e & 63), src + e, 16);
             cp_async_commit();
-            for (int c = tid; c < k; c += blockDim.x) ec[c] = dex[(size_t)ci * capc + c];
+            for (int c = tid; c < k; c += blockDim.x) ec[c] = dex[(size_t)ci * tc_dex_stride(capc) + c];
         }
         if (warp < nb) {
             const int c = k + warp;
