@@ -627,7 +627,9 @@ def mixed_numbers(capi, dev):
             # monomial basis breaks down at s = 10
             ("mixed_newton_auto", capi.GMRES_PREC_MIXED, auto, 0),
             ("fp64_newton_auto", capi.GMRES_PREC_FP64, auto, capi.GMRES_ARITH_FP64),
-            ("tc_newton_auto", capi.GMRES_PREC_FP64, auto, capi.GMRES_ARITH_TC))
+            ("tc_newton_auto", capi.GMRES_PREC_FP64, auto, capi.GMRES_ARITH_TC),
+            # mixed precision with the Gram accumulated in double-float on the FP32 pipe
+            ("mixed_dd_newton_auto", capi.GMRES_PREC_MIXED, auto, capi.GMRES_ARITH_DD))
     for name, prec, basis, arith in runs:
         S = capi.Solver.from_csr(A, capi.default_opts(m=60, s=10, panel=60, tol=1e-8, precision=prec,
                                                       max_restarts=2000, basis=basis, arith=arith))
@@ -696,6 +698,19 @@ def batched_numbers(capi, args):
     B.close()
     ok = sum(1 for r in res if r["status"] == 0)
     relres = [r["relres_true"] for r in res if r["status"] == 0]
+    # the same batch with the Gram accumulated in double-float (FP32 pipe) instead of FP64
+    odd = capi.default_opts(m=40, s=5, panel=40, tol=1e-8, precision=capi.GMRES_PREC_MIXED, max_restarts=500,
+                            arith=capi.GMRES_ARITH_DD)
+    Bd = capi.Batch(mats, odd)
+    Bd.autotune()
+    xd = [np.zeros(A.n) for A in mats]
+    Bd.solve(bs, [np.zeros(A.n) for A in mats])
+    t0 = time.perf_counter()
+    rcd, resd = Bd.solve(bs, xd)
+    btd = time.perf_counter() - t0
+    Bd.close()
+    okd = sum(1 for r in resd if r["status"] == 0)
+    relresd = [r["relres_true"] for r in resd if r["status"] == 0]
     # plain FP64, one system at a time
     o64 = capi.default_opts(m=40, s=5, panel=40, tol=1e-8, max_restarts=500)
     t0 = time.perf_counter()
@@ -711,6 +726,9 @@ def batched_numbers(capi, args):
             "mixed_batched": {"solves_per_s": round(ok / bt, 3), "converged": ok, "wall_s": round(bt, 3),
                               "max_relres": max(relres) if relres else None,
                               "iters_median": int(np.median([r["iters"] for r in res]))},
+            "mixed_batched_dd_gram": {"solves_per_s": round(okd / btd, 3), "converged": okd, "wall_s": round(btd, 3),
+                                      "max_relres": max(relresd) if relresd else None,
+                                      "iters_median": int(np.median([r["iters"] for r in resd]))},
             "fp64_one_at_a_time": {"solves_per_s": round(ok64 / t64, 3), "converged": int(ok64),
                                    "wall_s": round(t64, 3),
                                    "note": "includes per-system create/destroy; FP64 BCGS-PIP breaks down on "
@@ -746,7 +764,18 @@ def serving_numbers(capi, args):
         m = int(g.choice([30, 60]))
         b = csr_matrix((A.vals, A.colind, A.rowptr), shape=(A.n, A.n)) @ synth.x_true(A.n, i)
         reqs.append((A, b, s, m))
-    out = {"requests": len(reqs), "max_restarts": args.serve_restarts, "rates": []}
+    # served: FP32 basis and MPK, Gram accumulated in double-float (about 2^-48, on the
+    # FP32 pipe), FP64 Cholesky / Hessenberg / refinement, Newton basis with automatic
+    # shifts (s = 10 requests keep converging)
+    def served_opts(s, m, **kw):
+        o = dict(precision=capi.GMRES_PREC_MIXED, arith=capi.GMRES_ARITH_DD, basis=capi.GMRES_BASIS_NEWTON_AUTO)
+        o.update(kw)
+        return capi.default_opts(m=m, s=s, panel=m, tol=1e-8, max_restarts=args.serve_restarts, **o)
+
+    out = {"requests": len(reqs), "max_restarts": args.serve_restarts,
+           "served": "mixed precision (FP32 basis/MPK), double-float Gram accumulation, FP64 Cholesky, Hessenberg "
+                     "and refinement, Newton basis with Leja-ordered Ritz shifts",
+           "rates": []}
     for rate in list(args.serve_rates) + [0.0]:
         # rate 0: every request arrives at t = 0 (saturated server, peak solves/s)
         arr = np.cumsum(g.exponential(1.0 / rate, size=len(reqs))) if rate > 0 else np.zeros(len(reqs))
@@ -756,9 +785,7 @@ def serving_numbers(capi, args):
         for (A, b, s, m), ta in zip(reqs, arr):
             while time.perf_counter() - t0 < ta:
                 time.sleep(0.001)
-            ids.append(srv.submit(A, b, opts=capi.default_opts(m=m, s=s, panel=m, tol=1e-8,
-                                                               precision=capi.GMRES_PREC_MIXED,
-                                                               max_restarts=args.serve_restarts)))
+            ids.append(srv.submit(A, b, opts=served_opts(s, m)))
         res = [srv.wait(i) for i in ids]
         st = srv.stats()
         srv.stop()
@@ -768,6 +795,18 @@ def serving_numbers(capi, args):
                              "converged_per_s": round(conv / st["busy_s"], 3) if st["busy_s"] > 0 else None,
                              "converged": conv,
                              "statuses": sorted(set(r["status"] for _, r in res))})
+    # the previous served configuration (FP64 Gram accumulation, monomial basis), saturated
+    srv = capi.Server(max_active=32)
+    t0 = time.perf_counter()
+    ids = [srv.submit(A, b, opts=served_opts(s, m, arith=capi.GMRES_ARITH_FP64, basis=capi.GMRES_BASIS_MONOMIAL))
+           for A, b, s, m in reqs]
+    res = [srv.wait(i) for i in ids]
+    st = srv.stats()
+    srv.stop()
+    conv = sum(1 for _, r in res if r["status"] == 0)
+    out["served_fp64_gram_monomial_saturated"] = {
+        "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2), "solves_per_s": round(st["solves_per_s"], 3),
+        "converged_per_s": round(conv / st["busy_s"], 3) if st["busy_s"] > 0 else None, "converged": conv}
     t0 = time.perf_counter()
     conv64 = 0
     for A, b, s, m in reqs:

@@ -99,3 +99,30 @@ def test_mixed_convection_diffusion(lib):
     A = synth.convdiff2d(50, 3)
     b = kr.as_operator(A) @ synth.x_true(A.n, 4)
     mixed_vs_oracle(capi, A, b, 30, 5, 30)
+
+
+@pytest.mark.parametrize("gen,N,s,m", [("laplace2d", 64, 10, 60), ("laplace3d", 24, 10, 60), ("convdiff2d", 50, 5, 30),
+                                       ("laplace2d", 48, 15, 60)])
+def test_mixed_double_float_gram_newton_auto(lib, gen, N, s, m):
+    """The served configuration: FP32 basis and MPK, every Gram accumulated in
+    double-float (about 2^-48, on the FP32 pipe) instead of FP64, FP64 Cholesky,
+    Hessenberg and refinement, Newton basis with automatic shifts.  Converges to
+    1e-8, x within 1e-6 of the FP64 oracle's, iterations within m of the
+    oracle's mixed-precision arm (FP64 Gram accumulation, same shifts rule)."""
+    from paper_2402_15033_gb300 import capi
+    A = getattr(synth, gen)(N) if gen != "convdiff2d" else synth.convdiff2d(N, 3)
+    M = kr.as_operator(A)
+    b = M @ synth.x_true(A.n, 0)
+    S = capi.Solver.from_csr(A, capi.default_opts(m=m, s=s, panel=m, tol=1e-8, precision=capi.GMRES_PREC_MIXED,
+                                                  arith=capi.GMRES_ARITH_DD, basis=capi.GMRES_BASIS_NEWTON_AUTO))
+    x = np.zeros(A.n)
+    rc, res = S.solve(b, x)
+    S.close()
+    assert rc == capi.GMRES_OK, (res, capi.last_error())
+    assert np.linalg.norm(b - M @ x) / np.linalg.norm(b) <= 1e-8
+    xm, im = kr.sstep_gmres(A, b, m=m, s=s, panel=m, tol=1e-8, basis_dtype=np.float32, theta="auto")
+    x64, i64 = kr.sstep_gmres(A, b, m=m, s=s, panel=m, tol=1e-8, theta="auto")
+    assert im["status"] == 0 and i64["status"] == 0
+    assert abs(res["iters"] - im["iters"]) <= m, (res["iters"], im["iters"])
+    assert np.linalg.norm(x - x64) / np.linalg.norm(x64) <= 1e-6
+    assert np.allclose(res["theta"][:s], im["theta"], atol=1e-5 * np.abs(im["theta"]).max())

@@ -101,3 +101,30 @@ def test_late_small_request_overtakes_a_running_long_one(lib):
     assert r_small["status"] == 0
     assert r_big["status"] in (capi.GMRES_OK, capi.GMRES_WARN_MAXIT)
     assert r_big["restarts"] > r_small["restarts"]
+
+
+def test_served_mixed_double_float_newton_requests_equal_lone_solves(lib):
+    """The benchmark's served configuration (FP32 basis, double-float Gram,
+    Newton basis with automatic shifts) gives every request the same result in
+    the mix as alone, bit for bit."""
+    from paper_2402_15033_gb300 import capi
+    reqs = []
+    for i, A in enumerate([synth.laplace2d(40), synth.convdiff3d(14, 5), synth.laplace2d(64), synth.convdiff3d(12, 9)]):
+        b = kr.as_operator(A) @ synth.x_true(A.n, i)
+        o = capi.default_opts(m=30 if i % 2 else 60, s=10 if i < 2 else 5, panel=30 if i % 2 else 60, tol=1e-8,
+                              precision=capi.GMRES_PREC_MIXED, arith=capi.GMRES_ARITH_DD,
+                              basis=capi.GMRES_BASIS_NEWTON_AUTO, max_restarts=400)
+        reqs.append((A, b, o))
+    srv = capi.Server(max_active=8)
+    ids = [srv.submit(A, b, opts=o) for A, b, o in reqs]
+    got = [srv.wait(i) for i in ids]
+    srv.stop()
+    for (A, b, o), (x, r) in zip(reqs, got):
+        S = capi.Solver.from_csr(A, o)
+        x1 = np.zeros(A.n)
+        rc1, r1 = S.solve(b, x1)
+        S.close()
+        assert r["status"] == rc1 == 0, (A.name, r["status"], rc1)
+        assert r["iters"] == r1["iters"] and r["theta"] == r1["theta"]
+        assert np.array_equal(x, x1), A.name
+        assert np.linalg.norm(b - kr.as_operator(A) @ x) / np.linalg.norm(b) <= 1e-8
