@@ -85,6 +85,18 @@ struct gmres_ctx {
     DevState* st = nullptr;      // device
     DevState* hst = nullptr;     // pinned host mirror
     std::vector<cudaEvent_t> ev;
+    // restart cycles as CUDA graphs, one per cycle basis in use (captured on a
+    // private stream, launched on `stream`); a basis runs eagerly once first
+    struct CycleGraph {
+        gm::CycleBasis cb{};
+        int runs = 0;
+        unsigned long long last = 0;
+        cudaGraphExec_t exec = nullptr;
+    };
+    cudaStream_t cap = nullptr;
+    CycleGraph graphs[2];
+    unsigned long long graph_tick = 0;
+    bool no_graphs = false;
 };
 
 namespace gm {
@@ -227,6 +239,9 @@ int gmres_destroy(gmres_ctx* c) {
     cudaFree(c->digits);
     cudaFree(c->st);
     cudaFreeHost(c->hst);
+    for (auto& g : c->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (c->cap) cudaStreamDestroy(c->cap);
     delete c;
     return GMRES_OK;
 }
@@ -385,9 +400,8 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
 }  // extern "C"
 
 template <typename T>
-static int run_cycle(gmres_ctx* c, const CycleBasis& cb, std::vector<std::pair<int, int>>* marks) {
+static int run_cycle(gmres_ctx* c, const CycleBasis& cb, std::vector<std::pair<int, int>>* marks, cudaStream_t s) {
     const gmres_opts& o = c->opts;
-    cudaStream_t s = c->stream;
     DevState* ds = c->st;
     int32_t* done = &ds->done;
     T* basis = static_cast<T*>(c->basis);
@@ -656,13 +670,71 @@ int run_decide(SolveRun* R) {
     return 0;
 }
 
+static bool same_basis(const CycleBasis& a, const CycleBasis& b) {
+    return a.s == b.s && a.panel == b.panel && std::memcmp(&a.sigma, &b.sigma, sizeof(double)) == 0 &&
+           std::memcmp(a.theta, b.theta, sizeof(a.theta)) == 0;
+}
+
+static int enqueue_eager(gmres_ctx* c, const CycleBasis& cb, std::vector<std::pair<int, int>>* marks,
+                         cudaStream_t s) {
+    return c->opts.precision == GMRES_PREC_MIXED ? run_cycle<float>(c, cb, marks, s)
+                                                 : run_cycle<double>(c, cb, marks, s);
+}
+
+// One restart cycle: replayed from its CUDA graph when the context has run this
+// basis before (a cycle is some 50 kernel launches, so small systems are bound
+// by launch latency), else enqueued kernel by kernel.  Timed runs stay eager
+// (their phase events sit between the kernels).
+static int enqueue_cycle(gmres_ctx* c, const CycleBasis& cb, std::vector<std::pair<int, int>>* marks) {
+    if (marks || c->no_graphs) return enqueue_eager(c, cb, marks, c->stream);
+    gmres_ctx::CycleGraph* g = nullptr;
+    for (auto& x : c->graphs)
+        if (x.runs > 0 && same_basis(x.cb, cb)) g = &x;
+    if (!g) {
+        // a free slot, else the least recently used one
+        g = &c->graphs[0];
+        for (auto& x : c->graphs)
+            if (x.runs == 0 || x.last < g->last) g = &x;
+        if (g->exec) {
+            cudaStreamSynchronize(c->stream);   // no replay of it is still running
+            cudaGraphExecDestroy(g->exec);
+        }
+        *g = gmres_ctx::CycleGraph{};
+        g->cb = cb;
+    }
+    g->last = ++c->graph_tick;
+    if (!g->exec && g->runs > 0) {
+        // second use of this basis: capture the cycle on the private stream
+        cudaError_t e = c->cap ? cudaSuccess : cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+        cudaGraph_t graph = nullptr;
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const int rc = enqueue_eager(c, cb, nullptr, c->cap);
+            const cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
+            e = rc ? cudaErrorUnknown : e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            // capture is not available here: stay eager for this context
+            cudaGetLastError();
+            clear_error();
+            g->exec = nullptr;
+            c->no_graphs = true;
+            return enqueue_eager(c, cb, nullptr, c->stream);
+        }
+    }
+    ++g->runs;
+    if (g->exec) return cuda_rc(cudaGraphLaunch(g->exec, c->stream), "cycle graph launch");
+    return enqueue_eager(c, cb, nullptr, c->stream);
+}
+
 int run_enqueue_cycle(SolveRun* R) {
     gmres_ctx* c = R->c;
     const gmres_opts& o = c->opts;
     R->marks.clear();
     R->ran = R->cb;
-    const int rc = o.precision == GMRES_PREC_MIXED ? run_cycle<float>(c, R->cb, o.timing ? &R->marks : nullptr)
-                                                   : run_cycle<double>(c, R->cb, o.timing ? &R->marks : nullptr);
+    const int rc = enqueue_cycle(c, R->cb, o.timing ? &R->marks : nullptr);
     if (o.precision == GMRES_PREC_MIXED) ++R->r.ir_steps;
     ++R->cyc;
     return rc;

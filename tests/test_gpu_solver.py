@@ -226,3 +226,33 @@ def test_both_arithmetics_match_oracle(lib, arith):
     assert info["status"] == 0 and rc == 0
     assert abs(res["iters"] - info["iters"]) <= 5
     assert np.linalg.norm(x - xr) / np.linalg.norm(xr) <= 1e-6
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(arith=2), dict(basis=2, s=10), dict(precision=1, arith=1, basis=2, s=10),
+                                dict(ortho=2), dict(precision=1)])
+def test_cycle_graph_replay_equals_eager_launches(lib, kw):
+    """From the second use of a cycle basis on a context, restart cycles are
+    replayed from a captured CUDA graph.  A context that solves twice (the
+    second solve entirely from graphs) gives the same x and iteration count,
+    bit for bit, as kernel-by-kernel launches (timing mode stays eager)."""
+    from paper_2402_15033_gb300 import capi
+    A = synth.laplace2d(48)
+    b = kr.as_operator(A) @ synth.x_true(A.n, 3)
+    o = dict(m=60, s=5, panel=60, tol=1e-8)
+    o.update(kw)
+    outs = []
+    S = capi.Solver.from_csr(A, capi.default_opts(**o))
+    for _ in range(2):
+        x = np.zeros(A.n)
+        rc, res = S.solve(b, x)
+        assert rc == 0, res
+        outs.append((x, res["iters"]))
+    S.close()
+    E = capi.Solver.from_csr(A, capi.default_opts(timing=1, **o))
+    xe = np.zeros(A.n)
+    rc, rese = E.solve(b, xe)
+    E.close()
+    assert rc == 0
+    for x, it in outs:
+        assert it == rese["iters"]
+        assert np.array_equal(x, xe)
