@@ -296,8 +296,9 @@ __global__ void bcycle_begin_kernel(BatchDev B) {
     cycle_begin_body(B.st + s, B.active[s] ? 0 : 1);
 }
 
-__global__ void __launch_bounds__(256) bhess_kernel(BatchDev B, int lo, int t) {
-    hessenberg_ls_body(B.st + blockIdx.x, lo, t);
+__global__ void __launch_bounds__(kLsThreads) bhess_kernel(BatchDev B, int lo, int t) {
+    extern __shared__ __align__(16) double bh_dyn[];
+    hessenberg_ls_body(B.st + blockIdx.x, lo, t, bh_dyn);
 }
 
 }  // namespace
@@ -475,7 +476,7 @@ cudaError_t enqueue_cycle(gmres_batch* c) {
             e = launch_bgram<T>(c, basis, lo, np, lo, 1, 0, sidx, 0);
             if (e == cudaSuccess) e = launch_bupdate<T>(c, basis, lo, np, lo, 1, 0, sidx, 0);
             if (e == cudaSuccess) {
-                bhess_kernel<<<c->nsys, 256, 0, s>>>(B, lo, t);
+                bhess_kernel<<<c->nsys, kLsThreads, hessenberg_ls_smem(), s>>>(B, lo, t);
                 e = cudaGetLastError();
             }
             ++panel_idx;
@@ -557,6 +558,11 @@ int gmres_batch_create(gmres_batch** out, int32_t nsys, const int64_t* n, const 
     c->nsys = nsys;
     auto fail = [&](int rc) { gmres_batch_destroy(c); return rc; };
     if (cudaGetDevice(&c->device) != cudaSuccess) return fail(cuda_rc_b(cudaGetLastError(), "cudaGetDevice"));
+    // the least-squares kernel stages its matrices in dynamic shared memory (set
+    // here, before any cycle is captured into a graph)
+    if (cudaFuncSetAttribute(bhess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hessenberg_ls_smem()) !=
+        cudaSuccess)
+        return fail(cuda_rc_b(cudaGetLastError(), "cudaFuncSetAttribute"));
     if (stream) {
         c->stream = static_cast<cudaStream_t>(stream);
     } else {

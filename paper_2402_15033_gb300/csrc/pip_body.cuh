@@ -234,9 +234,22 @@ __device__ inline void pip_finish(int k, int nb, int g, int groups, int G, doubl
     for (int e = tid; e < nb * nb; e += blockDim.x) {
         const int i = e % nb, j = e / nb;
         if (i > j) continue;
+        // the k terms subtracted in order; eight terms' loads are issued together
+        const double* gi = gram + (size_t)i * kx;
+        const double* gj = gram + (size_t)j * kx;
         double acc = __ldcg(gram + (k + i) + (size_t)j * kx);
-        for (int l = 0; l < k; ++l)
-            acc -= __ldcg(gram + l + (size_t)i * kx) * __ldcg(gram + l + (size_t)j * kx);
+        int l = 0;
+        for (; l + 8 <= k; l += 8) {
+            double x[8], y[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                x[q] = __ldcg(gi + l + q);
+                y[q] = __ldcg(gj + l + q);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc -= x[q] * y[q];
+        }
+        for (; l < k; ++l) acc -= __ldcg(gi + l) * __ldcg(gj + l);
         S[i + j * kSLd] = acc;
     }
     if (tid == 0) s_info = 0;

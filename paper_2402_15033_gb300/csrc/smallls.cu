@@ -15,8 +15,9 @@ __global__ void cycle_begin_kernel(DevState* st, CycleBasis cb) {
     cycle_begin_body(st, 0);
 }
 
-__global__ void __launch_bounds__(256) hessenberg_ls_kernel(DevState* st, int lo, int t) {
-    hessenberg_ls_body(st, lo, t);
+__global__ void __launch_bounds__(kLsThreads) hessenberg_ls_kernel(DevState* st, int lo, int t) {
+    extern __shared__ __align__(16) double ls_dyn[];
+    hessenberg_ls_body(st, lo, t, ls_dyn);
 }
 
 __global__ void __launch_bounds__(256) bcgs2_combine_kernel(const DevState* st, int k, int s, const double* S,
@@ -34,7 +35,14 @@ cudaError_t launch_cycle_begin(cudaStream_t st, DevState* ds, const CycleBasis& 
 }
 
 cudaError_t launch_hessenberg_ls(cudaStream_t st, DevState* ds, int lo, int t) {
-    hessenberg_ls_kernel<<<1, 256, 0, st>>>(ds, lo, t);
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(hessenberg_ls_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)hessenberg_ls_smem());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    hessenberg_ls_kernel<<<1, kLsThreads, hessenberg_ls_smem(), st>>>(ds, lo, t);
     return cudaGetLastError();
 }
 

@@ -35,91 +35,169 @@ __device__ inline void cycle_begin_body(DevState* st, int stand_down) {
 }
 
 // Hessenberg recovery and Givens update for the big panel [lo, t] (one CTA).
-__device__ inline void hessenberg_ls_body(DevState* st, int lo, int t) {
+// Everything runs on shared copies (dynamic shared memory of
+// hessenberg_ls_smem() bytes): the panel's blocks of Cm and Rhat, the final
+// coordinates Rfin they give, H's columns (each row's previous entries feed its
+// next one), the rotations, g, and, once the cycle ends, the rotated H for the
+// back substitution; the results go back to the state.  The arithmetic and its
+// order are those of the plain recurrences.
+constexpr int kLsThreads = 512;
+__host__ __device__ constexpr size_t hessenberg_ls_smem() { return (size_t)4 * kLsLd * kLsLd * sizeof(double); }
+
+__device__ inline void hessenberg_ls_body(DevState* st, int lo, int t, double* dyn) {
     __shared__ double a[kLsLd];
+    __shared__ double sg[kLsLd + 1];
+    __shared__ double scs[kLsLd], ssn[kLsLd];
+    __shared__ double sy[kLsLd];
+    __shared__ int s_done;
     if (st->done) return;   // a breakdown earlier in the cycle
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int m = st->m, s = st->s, panel = st->panel;
     const double sigma = st->sigma;
     const double* Rhat = st->Rhat;
     const double* Cm = st->Cm;
     double* Rfin = st->Rfin;
     double* H = st->H;
+    double* Rg = st->Rg;
+    const int c_lo = lo > 0 ? lo - 1 : 0;
+    double* sH = dyn;                        // H columns, then their rotated form [i + c ld]
+    double* sRf = dyn + kLsLd * kLsLd;       // Rfin columns c_lo .. t           [i + (c - c_lo) ld]
+    double* sCm = dyn + 2 * kLsLd * kLsLd;   // Cm columns c_lo .. t             [i + (p - c_lo) ld]
+    double* sRh = dyn + 3 * kLsLd * kLsLd;   // Rhat rows and columns lo .. t    [(p - lo) + (c - lo) ld]
+
+    // 0. stage the panel's factors, the earlier H columns, rotations and g
+    const int nc = t - c_lo + 1, ncol = t - lo + 1;
+    for (int e = tid; e < (m + 1) * nc; e += blockDim.x) {
+        const int i = e % (m + 1), p = c_lo + e / (m + 1);
+        sCm[i + (p - c_lo) * kLsLd] = Cm[i + p * kLsLd];
+        if (p < lo) sRf[i + (p - c_lo) * kLsLd] = Rfin[i + p * kLsLd];
+    }
+    for (int e = tid; e < ncol * ncol; e += blockDim.x) {
+        const int p = lo + e % ncol, c = lo + e / ncol;
+        sRh[(p - lo) + (c - lo) * kLsLd] = Rhat[p + c * kLsLd];
+    }
+    for (int e = tid; e < (m + 1) * c_lo; e += blockDim.x) {
+        const int i = e % (m + 1), p = e / (m + 1);
+        sH[i + p * kLsLd] = H[i + p * kLsLd];
+    }
+    for (int i = tid; i < c_lo; i += blockDim.x) {
+        scs[i] = st->cs[i];
+        ssn[i] = st->sn[i];
+    }
+    for (int i = tid; i <= m; i += blockDim.x) sg[i] = lo == 0 ? (i == 0 ? st->beta * Cm[0] : 0.0) : st->g[i];
+    __syncthreads();
 
     // 1. final coordinates of the panel's raw columns
-    const int ncol = t - lo + 1;
     for (int e = tid; e < ncol * (m + 1); e += blockDim.x) {
         const int c = lo + e / (m + 1), i = e % (m + 1);
         double acc;
         if (c == 0) {
-            acc = Cm[i];
+            acc = sCm[i];
         } else {
             acc = (i < lo) ? Rhat[i + c * kLsLd] : 0.0;
             const int pe = c < t ? c : t;
-            for (int p = lo; p <= pe; ++p) acc = fma(Cm[i + p * kLsLd], Rhat[p + c * kLsLd], acc);
+            for (int p = lo; p <= pe; ++p)
+                acc = fma(sCm[i + (p - c_lo) * kLsLd], sRh[(p - lo) + (c - lo) * kLsLd], acc);
         }
+        sRf[i + (c - c_lo) * kLsLd] = acc;
         Rfin[i + c * kLsLd] = acc;
     }
     __syncthreads();
 
     // 2. Hessenberg columns c_lo .. t-1 from H a_c = b_c
-    const int c_lo = lo > 0 ? lo - 1 : 0;
     for (int c = c_lo; c < t; ++c) {
         const bool bstart = (c % s) == 0;
         const bool sfinal = bstart && c > 0 && (c % panel) == 0;
         for (int i = tid; i <= m; i += blockDim.x)
-            a[i] = bstart ? (sfinal ? (i == c ? 1.0 : 0.0) : Cm[i + c * kLsLd]) : Rfin[i + c * kLsLd];
+            a[i] = bstart ? (sfinal ? (i == c ? 1.0 : 0.0) : sCm[i + (c - c_lo) * kLsLd]) : sRf[i + (c - c_lo) * kLsLd];
         __syncthreads();
         const double th = st->theta[c % s];
         const double inv_ac = 1.0 / a[c];
         for (int i = tid; i <= m; i += blockDim.x) {
-            double acc = sigma * Rfin[i + (c + 1) * kLsLd];
+            double acc = sigma * sRf[i + (c + 1 - c_lo) * kLsLd];
             if (th != 0.0) acc = fma(th, a[i], acc);
-            for (int p = 0; p < c; ++p) acc = fma(-H[i + p * kLsLd], a[p], acc);
-            H[i + c * kLsLd] = acc * inv_ac;
+            for (int p = 0; p < c; ++p) acc = fma(-sH[i + p * kLsLd], a[p], acc);
+            sH[i + c * kLsLd] = acc * inv_ac;
         }
         __syncthreads();
     }
+    for (int e = tid; e < (m + 1) * (t - c_lo); e += blockDim.x) {
+        const int i = e % (m + 1), c = c_lo + e / (m + 1);
+        H[i + c * kLsLd] = sH[i + c * kLsLd];
+    }
+    __syncthreads();
 
-    // 3. Givens rotations of the new columns and the residual estimate
-    if (tid == 0) {
-        double* g = st->g;
-        double* Rg = st->Rg;
-        if (lo == 0) {
-            g[0] = st->beta * Cm[0];
-            for (int i = 1; i <= m; ++i) g[i] = 0.0;
-        }
-        for (int c = c_lo; c < t; ++c) {
-            for (int i = 0; i <= c + 1; ++i) Rg[i + c * kLsLd] = H[i + c * kLsLd];
-            for (int i = 0; i < c; ++i) {
-                const double x0 = Rg[i + c * kLsLd], x1 = Rg[i + 1 + c * kLsLd];
-                Rg[i + c * kLsLd] = st->cs[i] * x0 + st->sn[i] * x1;
-                Rg[i + 1 + c * kLsLd] = -st->sn[i] * x0 + st->cs[i] * x1;
-            }
-            const double x0 = Rg[c + c * kLsLd], x1 = Rg[c + 1 + c * kLsLd];
+    // 3. Givens rotations of the new columns (in place) and the residual estimate.
+    //    Column c takes rotations 0 .. c-1 in order, then defines rotation c; here
+    //    rotation i is applied to every later new column at once (one thread per
+    //    column), so each column sees the same operations in the same order.
+    const int cfirst = c_lo;
+    for (int i = 0; i < t; ++i) {
+        if (i >= cfirst && tid == 0) {
+            // rotation i from column i, which has all of rotations 0 .. i-1
+            double* col = sH + i * kLsLd;
+            const double x0 = col[i], x1 = col[i + 1];
             const double r = hypot(x0, x1);
             double cc = 1.0, ss = 0.0;
             if (r != 0.0) { cc = x0 / r; ss = x1 / r; }
-            st->cs[c] = cc;
-            st->sn[c] = ss;
-            Rg[c + c * kLsLd] = r;
-            Rg[c + 1 + c * kLsLd] = 0.0;
-            const double gk = g[c];
-            g[c] = cc * gk;
-            g[c + 1] = -ss * gk;
+            scs[i] = cc;
+            ssn[i] = ss;
+            col[i] = r;
+            col[i + 1] = 0.0;
+            const double gk = sg[i];
+            sg[i] = cc * gk;
+            sg[i + 1] = -ss * gk;
         }
+        if (i >= cfirst) __syncthreads();
+        // rotation i on the new columns after it
+        for (int c = max(cfirst, i + 1) + tid; c < t; c += blockDim.x) {
+            double* col = sH + c * kLsLd;
+            const double x0 = col[i], x1 = col[i + 1];
+            col[i] = scs[i] * x0 + ssn[i] * x1;
+            col[i + 1] = -ssn[i] * x0 + scs[i] * x1;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
         st->nrot = t;
-        const double res = fabs(g[t]);
+        const double res = fabs(sg[t]);
         st->resid = res;
-        if (res <= st->tol_abs || t == m) {
-            for (int i = t - 1; i >= 0; --i) {
-                double acc = g[i];
-                for (int j = i + 1; j < t; ++j) acc -= Rg[i + j * kLsLd] * st->y[j];
-                st->y[i] = acc / Rg[i + i * kLsLd];
-            }
-            st->k_used = t;
-            st->done = 1;
+        s_done = (res <= st->tol_abs || t == m) ? 1 : 0;
+    }
+    __syncthreads();
+    for (int c = c_lo + tid; c < t; c += blockDim.x) {
+        st->cs[c] = scs[c];
+        st->sn[c] = ssn[c];
+    }
+    for (int i = tid; i <= m; i += blockDim.x) st->g[i] = sg[i];
+    for (int e = tid; e < (m + 1) * (t - c_lo); e += blockDim.x) {
+        const int i = e % (m + 1), c = c_lo + e / (m + 1);
+        if (i <= c + 1) Rg[i + c * kLsLd] = sH[i + c * kLsLd];
+    }
+    if (!s_done) return;
+
+    // 4. the cycle ends here: y from R y = g (R the rotated H, upper triangular);
+    //    the earlier panels' rotated columns come back from the state
+    for (int e = tid; e < t * c_lo; e += blockDim.x) {
+        const int i = e % t, p = e / t;
+        if (i <= p) sH[i + p * kLsLd] = Rg[i + p * kLsLd];
+    }
+    __syncthreads();
+    if (tid < 32) {
+        for (int i = t - 1; i >= 0; --i) {
+            double part = 0.0;
+            for (int j = i + 1 + lane; j < t; j += 32) part = fma(sH[i + j * kLsLd], sy[j], part);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+            if (lane == 0) sy[i] = (sg[i] - part) / sH[i + i * kLsLd];
+            __syncwarp();
         }
+    }
+    __syncthreads();
+    for (int i = tid; i < t; i += blockDim.x) st->y[i] = sy[i];
+    if (tid == 0) {
+        st->k_used = t;
+        st->done = 1;
     }
 }
 
