@@ -50,6 +50,7 @@ __device__ inline void hessenberg_ls_body(DevState* st, int lo, int t, double* d
     __shared__ double scs[kLsLd], ssn[kLsLd];
     __shared__ double sy[kLsLd];
     __shared__ int s_done;
+    __shared__ double s_inv;
     if (st->done) return;   // a breakdown earlier in the cycle
     const int tid = threadIdx.x, lane = tid & 31;
     const int m = st->m, s = st->s, panel = st->panel;
@@ -108,11 +109,15 @@ __device__ inline void hessenberg_ls_body(DevState* st, int lo, int t, double* d
     for (int c = c_lo; c < t; ++c) {
         const bool bstart = (c % s) == 0;
         const bool sfinal = bstart && c > 0 && (c % panel) == 0;
-        for (int i = tid; i <= m; i += blockDim.x)
-            a[i] = bstart ? (sfinal ? (i == c ? 1.0 : 0.0) : sCm[i + (c - c_lo) * kLsLd]) : sRf[i + (c - c_lo) * kLsLd];
+        for (int i = tid; i <= m; i += blockDim.x) {
+            const double ai = bstart ? (sfinal ? (i == c ? 1.0 : 0.0) : sCm[i + (c - c_lo) * kLsLd])
+                                     : sRf[i + (c - c_lo) * kLsLd];
+            a[i] = ai;
+            if (i == c) s_inv = 1.0 / ai;   // one FP64 division per column, not one per thread
+        }
         __syncthreads();
         const double th = st->theta[c % s];
-        const double inv_ac = 1.0 / a[c];
+        const double inv_ac = s_inv;
         for (int i = tid; i <= m; i += blockDim.x) {
             double acc = sigma * sRf[i + (c + 1 - c_lo) * kLsLd];
             if (th != 0.0) acc = fma(th, a[i], acc);
