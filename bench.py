@@ -8,7 +8,9 @@ the whole 61-column big panel (s^ = m = 60).  Each step re-orthogonalizes the
 previous step's output, so every step does identical work on a 2 GB basis
 (16x the 129 MB L2: no step reads another's data from L2).
 
-value  = algorithmic HBM bytes of the step (8376 B per row)
+value  = algorithmic HBM bytes of the step (8376 B per row: each stage-1 Gram reads
+         its k + s columns once, each update reads k + s and writes s, stage 2
+         reads the 61 columns twice and writes them once; 8 bytes per value)
          / device time of the step  [GB/s], inputs resident in HBM.  The
          headline step runs the exact-slice tensor-core arithmetic (FP64 in and
          out, FP64-quality Gram and update); the same step on the FP64 pipe and

@@ -1,5 +1,5 @@
 """Parity of the CUDA s-step GMRES (two-stage, FP64) with the CPU oracle
-through the C ABI.  Bars (the benchmark spec): final x within 1e-6 relative of the
+through the C ABI.  Bars: final x within 1e-6 relative of the
 oracle's at relative residual 1e-8, iteration count within +-s, Arnoldi-relation
 consistency through the converged residual."""
 import numpy as np

@@ -195,7 +195,7 @@ def test_givens_solves_the_hessenberg_least_squares():
                                          ("bcgs2_cholqr2", 5)])
 def test_arnoldi_relation_of_recovered_hessenberg(ortho, panel):
     """A Q_{1:k} = Q_{1:k+1} H to 1e-12 relative for the H recovered from the
-    s-step R factors (spec invariant)."""
+    s-step R factors."""
     A = synth.convdiff2d(40, seed=5)
     b = kr.as_operator(A) @ synth.x_true(A.n, 1)
     _, info = kr.sstep_gmres(A, b, m=60, s=5, panel=panel, tol=1e-30, max_restarts=1,
