@@ -115,19 +115,24 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
         }
         cp_async_commit();
     };
+    // Q's digit units and exponents of chunk ch from the digit basis (issued a
+    // chunk ahead, as soon as the previous chunk's MMAs are done with xu)
+    auto stage_q = [&](int64_t ch) {
+        const uint4* src = dig + (size_t)ch * capc * 64;
+        for (int e = tid; e < k * 64; e += blockDim.x) cp_async16(xu + (e >> 6) * kUdXs + (e & 63), src + e, 16);
+        cp_async_commit();
+        for (int c = tid; c < k; c += blockDim.x) ec[c] = dex[(size_t)ch * tc_dex_stride(capc) + c];
+    };
     __syncthreads();
-    if ((int64_t)b < nchunks) stage_v(b);
+    if ((int64_t)b < nchunks) {
+        stage_v(b);
+        stage_q(b);
+    }
     for (int64_t ci = b; ci < nchunks; ci += G) {
         const int64_t row0 = ci * kUdRows;
         cp_async_wait_all();
         __syncthreads();
-        // 1. Q's digit units and exponents from the digit basis; V's columns sliced
-        {
-            const uint4* src = dig + (size_t)ci * capc * 64;
-            for (int e = tid; e < k * 64; e += blockDim.x) cp_async16(xu + (e >> 6) * kUdXs + (e & 63), src + e, 16);
-            cp_async_commit();
-            for (int c = tid; c < k; c += blockDim.x) ec[c] = dex[(size_t)ci * tc_dex_stride(capc) + c];
-        }
+        // 1. V's columns sliced next to Q's digit units (already landed)
         if (warp < nb) {
             const int c = k + warp;
             const double x0 = raw[warp * kUdRows + 2 * lane], x1 = raw[warp * kUdRows + 2 * lane + 1];
@@ -142,7 +147,6 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
             tc_slice(x1, eb, d1);
             tc_pack(d0, d1, xu[c * kUdXs + lane], xu[c * kUdXs + 32 + lane]);
         }
-        cp_async_wait_all();
         __syncthreads();
         // the raw tile is free: the next chunk's V streams in
         if (ci + G < nchunks) stage_v(ci + G);
@@ -221,6 +225,9 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
 #pragma unroll
             for (int e = 0; e < 4; ++e) ksum[(t * 4 + e) * 32 + lane] = S[e];
         __syncthreads();
+        // every MMA is done with xu: the next chunk's Q digits stream in during the
+        // combine and the column pass
+        if (ci + G < nchunks) stage_q(ci + G);
         if (khalf == 0) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
