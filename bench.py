@@ -111,7 +111,7 @@ FP64_PEAK_TFLOPS = 152 * 2070e6 * 2 * 2 / 1e12   # 2 FP64 FMA/clk/SM x 152 SMs x
 # tensor-core kernels move their algorithmic bytes; the stage-1 tensor-core
 # kernels read 14-byte digits instead of 8-byte values (the digit basis).
 NCU_TRAFFIC = {
-    "tc": {"stage1_gram": 4 * (998.5 + 24.7) * 1e6, "stage1_update": 4 * (985.7 + 117.4) * 1e6,
+    "tc": {"stage1_gram": 4 * (998.1 + 24.9) * 1e6, "stage1_update": 4 * (985.8 + 116.1) * 1e6,
            "stage2_update": 4 * (511.8 + 457.2) * 1e6},
     "fp64": {"stage1_gram": 4 * (511.8 + 3.2) * 1e6, "stage2_gram": 4 * (514.7 + 3.5) * 1e6},
 }
