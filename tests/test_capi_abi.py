@@ -87,3 +87,13 @@ def test_bad_arguments_are_rejected_before_any_launch(capi):
                           vv.ctypes.data_as(C.c_void_p), 0, C.byref(o), None)
     assert rc == capi.GMRES_ERR_ARG and "panel" in capi.last_error()
     assert lib.gmres_destroy(None) == capi.GMRES_OK
+
+
+def test_digit_basis_size_formula(capi):
+    """ortho_digits_bytes (host code): per 64-row chunk, capc columns of 64
+    16-byte digit units, then each chunk's row of int32 exponents padded to a
+    multiple of four columns (16-byte aligned rows), plus 256 bytes."""
+    for n, capc in [(1, 1), (64, 5), (65, 61), (4194304, 64), (1000, 63), (129, 62)]:
+        chunks = (n + 63) // 64
+        expect = chunks * capc * 64 * 16 + chunks * ((capc + 3) // 4 * 4) * 4 + 256
+        assert capi.digits_bytes(n, capc) == expect, (n, capc)
