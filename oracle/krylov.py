@@ -6,7 +6,7 @@
                    ``two_stage`` (§V, Fig. 5), ``bcgs_pip2`` (§IV-C, Fig. 4b) or
                    ``bcgs2_cholqr2`` (§IV-B, Fig. 2b).
 
-The paper's Fig. 1 pseudocode is not in its source; the driver below restates
+The paper's Fig. 1 pseudocode is not in its source; the solver loop below restates
 the method from §III and §V:
 
 * A restart cycle starts from q_1 = r / ||r||, r = b - A x.

@@ -275,9 +275,10 @@ def test_digit_basis_gram_is_bit_identical(lib, n, k, nb):
         assert np.array_equal(outs[0], outs[1])
 
 
-def run_gram_stream(capi, Q, V, ld_pad=0, update=True, capc=64):
+def run_gram_stream(capi, Q, V, ld_pad=0, update=True, capc=64, cached_v=False):
     """Gram through the streaming kernel (Q from the digit basis, nb <= 8) and
-    the FP64 update."""
+    the FP64 update.  cached_v: V's digits are in the basis too (every column
+    cached, as for the stage-2 panel)."""
     n, nb = V.shape
     k = 0 if Q is None else Q.shape[1]
     buf = torch.zeros(k + nb, n + ld_pad, dtype=torch.float64, device="cuda")
@@ -287,12 +288,14 @@ def run_gram_stream(capi, Q, V, ld_pad=0, update=True, capc=64):
     Qd = buf[:k].T[:n] if k else None
     Vd = buf[k:].T[:n]
     dig = torch.zeros(capi.digits_bytes(n, capc), dtype=torch.uint8, device="cuda")
-    if k:
+    if cached_v:
+        capi.digits_fill(buf.T[:n], 0, dig, capc)
+    elif k:
         capi.digits_fill(Qd, 0, dig, capc)
     R = torch.full((nb, k + nb + 3), np.nan, dtype=torch.float64, device="cuda").T
     work = torch.empty(capi.workspace_bytes(n, k, nb), dtype=torch.uint8, device="cuda")
     st = torch.full((1,), -7, dtype=torch.int32, device="cuda")
-    capi.ortho_gram_chol_tcd(Qd, Vd, R, work, st, dig, capc, k, k=k)
+    capi.ortho_gram_chol_tcd(Qd, Vd, R, work, st, dig, capc, k + nb if cached_v else k, k=k)
     if update:
         capi.ortho_update(Qd, Vd, R, st, k=k)
     torch.cuda.synchronize()
@@ -367,6 +370,49 @@ def test_streaming_digit_gram_nan_zero_and_repeatability(lib):
     Qn = Q.copy()
     Qn[12345, 7] = np.inf    # row 7 of P is NaN, so is every entry of G - P^T P: the first pivot fails
     assert run_gram_stream(capi, Qn, V, update=False)[2] == 1
+
+
+@pytest.mark.parametrize("n,k,nb", [(64, 0, 9), (65, 0, 16), (127, 3, 9), (4099, 0, 61), (4099, 15, 17),
+                                    (20001, 16, 48), (3001, 40, 24), (100003, 0, 64), (777, 31, 33), (5000, 55, 9)])
+def test_all_cached_digit_gram_matches_oracle(lib, n, k, nb):
+    """The Gram over columns that are all in the digit basis (the stage-2
+    panel; output tiles on and off the diagonal, ragged tile columns and last
+    chunks) meets the FP64 parity bars against the oracle."""
+    from paper_2402_15033_gb300 import capi
+    g = synth.rng(2600 + n + k + nb)
+    Q = bo.hhqr(g.standard_normal((n, k)))[0] if k else None
+    V = g.standard_normal((n, nb)) / np.sqrt(n) + (Q @ g.standard_normal((k, nb)) / 4 if k else 0.0)
+    Vg, Rg, st = run_gram_stream(capi, Q, V, ld_pad=n % 2, cached_v=True)
+    assert_parity(Q, V, Vg, Rg, st)
+
+
+def test_all_cached_digit_gram_exact_rationals_scaling_nan(lib):
+    """Gram entries within 2^-48 of exact rational sums on hard digits; a
+    power-of-two scale of V scales R exactly; a NaN in V fails its pivot; two
+    runs agree bit for bit."""
+    from paper_2402_15033_gb300 import capi
+    g = synth.rng(4411)
+    n, k, nb = 1000, 12, 20
+    Q = _hard_digits(g, n, k)
+    Q *= 2.0 ** -(np.ceil(np.log2(np.linalg.norm(Q))) + 1)
+    V = _hard_digits(g, n, nb)
+    _, Rg, st = run_gram_stream(capi, Q, V, ld_pad=0, update=False, cached_v=True)
+    assert st == 0
+    err = np.abs(Rg[:k] - checks.exact_gram(Q, V)) / np.outer(np.linalg.norm(Q, axis=0), np.linalg.norm(V, axis=0))
+    assert err.max() <= 2.0 ** -48, err.max()
+    nv = np.linalg.norm(V, axis=0)
+    G_rec = Rg[k:].T @ Rg[k:] + Rg[:k].T @ Rg[:k]
+    assert np.max(np.abs(G_rec - checks.exact_gram(V, V)) / np.outer(nv, nv)) <= 1e-13
+    n, k, nb = 20011, 27, 17
+    Qo = bo.hhqr(g.standard_normal((n, k)))[0]
+    Vn = g.standard_normal((n, nb))
+    _, R0, s0 = run_gram_stream(capi, Qo, Vn, ld_pad=1, update=False, cached_v=True)
+    _, R1, s1 = run_gram_stream(capi, Qo, Vn * 2.0 ** -300, ld_pad=1, update=False, cached_v=True)
+    _, R2, s2 = run_gram_stream(capi, Qo, Vn, ld_pad=1, update=False, cached_v=True)
+    assert s0 == s1 == s2 == 0
+    assert np.array_equal(R1, R0 * 2.0 ** -300) and np.array_equal(R2, R0)
+    Vn[17000, 11] = np.nan
+    assert run_gram_stream(capi, Qo, Vn, ld_pad=1, update=False, cached_v=True)[2] == 12
 
 
 @pytest.mark.parametrize("n,k,nb", [(4099, 6, 5), (777, 20, 21), (20001, 56, 5), (1000, 0, 8), (131, 3, 1)])
