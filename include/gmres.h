@@ -356,7 +356,8 @@ int gmres_server_submit(gmres_server* s, int64_t n, const int64_t* rowptr, const
                         int64_t* id);
 
 /* 1 = finished (x[n] and *res filled, the request released), 0 = not yet
- * (timeout_s < 0 waits forever; poll = wait with timeout 0). */
+ * (timeout_s < 0 waits forever; poll = wait with timeout 0), GMRES_ERR_ARG for
+ * an id that was never submitted or has already been collected. */
 int gmres_server_wait(gmres_server* s, int64_t id, double* x, gmres_result* res, double timeout_s);
 int gmres_server_poll(gmres_server* s, int64_t id, double* x, gmres_result* res);
 

@@ -372,14 +372,9 @@ cudaError_t launch_bgram_t(gmres_batch* c, T* basis, int k, int nb, int vcol, in
     switch (nb) {
 #define GM_CASE(NBV)                                                                                       \
     case NBV: {                                                                                            \
-        static bool attr = false;                                                                          \
-        if (!attr) {                                                                                       \
-            cudaError_t e = cudaFuncSetAttribute(bgram_skinny_kernel<T, NBV, true>,                        \
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,              \
-                                                 (int)gram_skinny_df_smem(kMaxNB + NBV));                  \
-            if (e != cudaSuccess) return e;                                                                \
-            attr = true;                                                                                   \
-        }                                                                                                  \
+        static const cudaError_t attr =                                                                    \
+            smem_limit(bgram_skinny_kernel<T, NBV, true>, gram_skinny_df_smem(kMaxNB + NBV));              \
+        if (attr != cudaSuccess) return attr;                                                              \
         bgram_skinny_kernel<T, NBV, true><<<c->grid_gram, kGramThreads, gram_skinny_df_smem(k + NBV + NBV), \
                                             c->stream>>>(B, basis, k, vcol, which, rrow, statidx, mode);   \
         return cudaGetLastError();                                                                         \
@@ -413,13 +408,8 @@ cudaError_t launch_bupdate_t(gmres_batch* c, T* basis, int k, int nb, int vcol, 
 #undef GM_CASE
         default: break;
     }
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(bupdate_wide_kernel<T, DDA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kBWideSmem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static const cudaError_t attr = smem_limit(bupdate_wide_kernel<T, DDA>, kBWideSmem);
+    if (attr != cudaSuccess) return attr;
     bupdate_wide_kernel<T, DDA><<<c->grid_rows, DDA ? 256 : 128, kBWideSmem, c->stream>>>(B, basis, k, nb, vcol, which,
                                                                                         rrow, statidx, mode);
     return cudaGetLastError();
@@ -575,10 +565,18 @@ int gmres_batch_create(gmres_batch** out, int32_t nsys, const int64_t* n, const 
     // system table, tiles, virtual CTAs, concatenated block-diagonal CSR
     int64_t row0 = 0, nnz_tot = 0;
     int32_t v0 = 0, t0 = 0;
+    // argument errors from here on release the context (and its stream)
+#define BARG(cond, ...)                        \
+    do {                                       \
+        if (!(cond)) {                         \
+            set_error(__VA_ARGS__);            \
+            return fail(GMRES_ERR_ARG);        \
+        }                                      \
+    } while (0)
     for (int i = 0; i < nsys; ++i) {
-        GM_ARG(n[i] >= 1, "system %d: n must be >= 1", i);
+        BARG(n[i] >= 1, "system %d: n must be >= 1", i);
         const int64_t nz = rowptr[i][n[i]];
-        GM_ARG(rowptr[i][0] == 0 && nz >= 0, "system %d: rowptr must start at 0", i);
+        BARG(rowptr[i][0] == 0 && nz >= 0, "system %d: rowptr must start at 0", i);
         BSys S;
         S.n = n[i];
         S.row0 = row0;
@@ -594,7 +592,8 @@ int gmres_batch_create(gmres_batch** out, int32_t nsys, const int64_t* n, const 
         row0 += (n[i] + 31) / 32 * 32;
         nnz_tot += nz;
     }
-    GM_ARG(nnz_tot < (int64_t(1) << 31) && row0 < (int64_t(1) << 31), "batch too large for 32-bit CSR indices");
+    BARG(nnz_tot < (int64_t(1) << 31) && row0 < (int64_t(1) << 31), "batch too large for 32-bit CSR indices");
+#undef BARG
     c->ntot = row0;
     std::vector<int32_t> rp(row0 + 1), ci(nnz_tot > 0 ? nnz_tot : 1);
     std::vector<double> vv(nnz_tot > 0 ? nnz_tot : 1);

@@ -20,6 +20,14 @@ constexpr int kGramThreads = 256;
 int reduction_grid(int64_t n);
 int num_sms();
 
+// Raises kernel f's dynamic shared-memory limit to `bytes`.  Callers keep the
+// result in a function-local static, whose initialization C++ runs once even
+// when several host threads launch.
+template <class F>
+inline cudaError_t smem_limit(F* f, size_t bytes) {
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 // Layout of the scratch space of one BCGS-PIP call (bytes, 256-aligned pieces).
 struct PipWork {
     double* partial;     // [grid][groups][64*64] per-CTA partial Gram blocks

@@ -95,13 +95,8 @@ gram_tcq_kernel(int64_t n, const double* __restrict__ V, int64_t ldv, int k, int
 cudaError_t launch_gram_tcq(cudaStream_t st, int64_t n, int k, const double* V, int64_t ldv, int nb, double* R,
                             int ldr, const PipWork& w, int32_t* d_status, int32_t* d_skip, int grid, int mode,
                             const void* digits, int capc) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gram_tcq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)gram_tcq_smem(kGqMaxKX - 1));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static const cudaError_t attr = smem_limit(gram_tcq_kernel, gram_tcq_smem(kGqMaxKX - 1));
+    if (attr != cudaSuccess) return attr;
     const uint4* dig = static_cast<const uint4*>(digits);
     const int* dex = reinterpret_cast<const int*>(dig + tc_digits_units(n, capc));
     const int G = std::min(grid, num_sms());
@@ -114,13 +109,8 @@ cudaError_t launch_gram_tc(cudaStream_t st, int64_t n, const double* Q, int64_t 
                            const double* V, int64_t ldv, int nb, double* R, int ldr, const PipWork& w,
                            int32_t* d_status, int32_t* d_skip, int grid, int mode,
                            const void* digits = nullptr, int capc = 0, int kc = 0) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)gram_tc_smem(kTcMaxKX));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static const cudaError_t attr = smem_limit(gram_tc_kernel, gram_tc_smem(kTcMaxKX));
+    if (attr != cudaSuccess) return attr;
     const uint4* dig = static_cast<const uint4*>(digits);
     const int* dex = digits ? reinterpret_cast<const int*>(dig + tc_digits_units(n, capc)) : nullptr;
     // two CTAs per SM (the chunk tiles take most of the shared memory)
@@ -179,16 +169,12 @@ update_tc_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k, do
 cudaError_t launch_update_tc(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, double* V,
                              int64_t ldv, int nb, const double* R, int ldr, const int32_t* d_status,
                              const int32_t* d_skip, int mode, void* digits = nullptr, int capc = 0) {
-    static bool attr[2] = {false, false};
     const bool dg = digits != nullptr;
-    if (!attr[dg]) {
-        cudaError_t e = dg ? cudaFuncSetAttribute(update_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)update_tc_smem(kTuMaxKX, kTuMaxKX, true))
-                           : cudaFuncSetAttribute(update_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)update_tc_smem(kTuMaxKX, kTuMaxKX, false));
-        if (e != cudaSuccess) return e;
-        attr[dg] = true;
-    }
+    static const cudaError_t attr_dg = smem_limit(update_tc_kernel<true>, update_tc_smem(kTuMaxKX, kTuMaxKX, true));
+    static const cudaError_t attr_fp =
+        smem_limit(update_tc_kernel<false>, update_tc_smem(kTuMaxKX, kTuMaxKX, false));
+    const cudaError_t attr = dg ? attr_dg : attr_fp;
+    if (attr != cudaSuccess) return attr;
     // wide blocks: one 16-warp CTA per SM (the W slices take a third of the
     // shared memory); narrow ones: 8-warp CTAs, two per SM where they fit
     const int threads = nb > 32 ? 512 : 256;
@@ -219,13 +205,8 @@ update_tcd_kernel(int64_t n, int k, double* V, int64_t ldv, int nb, const double
 cudaError_t launch_update_tcd(cudaStream_t st, int64_t n, int k, double* V, int64_t ldv, int nb, const double* R,
                               int ldr, const int32_t* d_status, const int32_t* d_skip, int mode, void* digits,
                               int capc) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(update_tcd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)update_tcd_smem(kTuMaxKX, kUdMaxNB));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static const cudaError_t attr = smem_limit(update_tcd_kernel, update_tcd_smem(kTuMaxKX, kUdMaxNB));
+    if (attr != cudaSuccess) return attr;
     const int64_t chunks = (n + kUdRows - 1) / kUdRows;
     const int G = (int)std::min<int64_t>(chunks, 2 * (int64_t)num_sms());
     uint4* dig = static_cast<uint4*>(digits);
@@ -362,13 +343,8 @@ cudaError_t launch_skinny_df(cudaStream_t st, int64_t n, const T* Q, int64_t ldq
     const int kx = k + NB;
     const dim3 g(grid, (kx + kMaxNB - 1) / kMaxNB);
     const size_t sm = gram_skinny_df_smem(std::min(kx, kMaxNB) + NB);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gram_skinny_df_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)gram_skinny_df_smem(kMaxNB + NB));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static const cudaError_t attr = smem_limit(gram_skinny_df_kernel<T, NB>, gram_skinny_df_smem(kMaxNB + NB));
+    if (attr != cudaSuccess) return attr;
     gram_skinny_df_kernel<T, NB><<<g, kGramThreads, sm, st>>>(n, Q, ldq, k, V, ldv, R, ldr, w.partial,
                                                               w.counter, w.gram, d_status, d_skip, mode);
     return cudaGetLastError();
@@ -458,14 +434,8 @@ cudaError_t pip_update_t(cudaStream_t st, int64_t n, const T* Q, int64_t ldq, in
             default: break;
         }
         if (k + nb <= kMaxNB) {
-            static bool attr_set[2] = {false, false};
-            bool& done = attr_set[sizeof(T) == sizeof(float)];
-            if (!done) {
-                cudaError_t e = cudaFuncSetAttribute(update_wide_df_kernel<T>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWideDfSmem);
-                if (e != cudaSuccess) return e;
-                done = true;
-            }
+            static const cudaError_t attr = smem_limit(update_wide_df_kernel<T>, kWideDfSmem);
+            if (attr != cudaSuccess) return attr;
             const int64_t tiles = (n + kDfWideRows - 1) / kDfWideRows;
             const int grid = (int)(tiles < 4 * (int64_t)num_sms() ? tiles : 4 * (int64_t)num_sms());
             update_wide_df_kernel<T><<<grid, 256, kWideDfSmem, st>>>(n, Q, ldq, k, V, ldv, nb, R, ldr, d_status,

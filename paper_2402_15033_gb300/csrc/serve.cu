@@ -22,6 +22,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <set>
 #include <thread>
 #include <vector>
 #include "solver_run.cuh"
@@ -62,6 +63,7 @@ struct gmres_server {
     std::deque<Request*> pending;
     std::vector<Request*> active;
     std::map<int64_t, Request*> finished;
+    std::set<int64_t> live;          // ids submitted and not yet collected by wait / poll
     std::vector<double> latencies;   // seconds, completed requests
     size_t budget = 0, used = 0;
     int max_active = 0;
@@ -224,6 +226,10 @@ int gmres_server_submit(gmres_server* S, int64_t n, const int64_t* rowptr, const
     if (opts) o = *opts; else gmres_default_opts(&o);
     const size_t bytes = gmres_footprint(n, nnz, &o);
     GM_ARG(bytes > 0, "invalid options for this request");
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        GM_ARG(!S->stopping, "server is stopping");
+    }
     Request* q = new Request();
     q->n = n;
     q->rowptr.assign(rowptr, rowptr + n + 1);
@@ -237,9 +243,14 @@ int gmres_server_submit(gmres_server* S, int64_t n, const int64_t* rowptr, const
     q->bytes = bytes;
     q->t_submit = now_s();
     std::lock_guard<std::mutex> lk(S->mu);
-    GM_ARG(!S->stopping, "server is stopping");
+    if (S->stopping) {
+        delete q;
+        set_error("server is stopping");
+        return GMRES_ERR_ARG;
+    }
     q->id = S->next_id++;
     *id = q->id;
+    S->live.insert(q->id);
     ++S->submitted;
     if (S->t_first_submit < 0) S->t_first_submit = q->t_submit;
     if (bytes > S->budget) {
@@ -262,11 +273,13 @@ int gmres_server_wait(gmres_server* S, int64_t id, double* x, gmres_result* res,
     clear_error();
     GM_ARG(S != nullptr, "NULL server");
     std::unique_lock<std::mutex> lk(S->mu);
+    GM_ARG(S->live.count(id) > 0, "request %lld was never submitted or is already collected", (long long)id);
     auto ready = [&] { return S->finished.count(id) > 0; };
     if (timeout_s < 0) S->cv_done.wait(lk, ready);
     else if (!S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready)) return 0;
     Request* q = S->finished[id];
     S->finished.erase(id);
+    S->live.erase(id);
     lk.unlock();
     if (x) std::memcpy(x, q->x.data(), q->n * sizeof(double));
     if (res) *res = q->res;

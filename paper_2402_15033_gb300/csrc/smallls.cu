@@ -35,13 +35,8 @@ cudaError_t launch_cycle_begin(cudaStream_t st, DevState* ds, const CycleBasis& 
 }
 
 cudaError_t launch_hessenberg_ls(cudaStream_t st, DevState* ds, int lo, int t) {
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(hessenberg_ls_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)hessenberg_ls_smem());
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static const cudaError_t attr = smem_limit(hessenberg_ls_kernel, hessenberg_ls_smem());
+    if (attr != cudaSuccess) return attr;
     hessenberg_ls_kernel<<<1, kLsThreads, hessenberg_ls_smem(), st>>>(ds, lo, t);
     return cudaGetLastError();
 }

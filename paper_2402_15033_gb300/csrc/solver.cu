@@ -42,15 +42,13 @@ void set_error(const char* fmt, ...) {
 void clear_error() { g_err[0] = 0; }
 
 int num_sms() {
-    static int cached = 0;
-    if (cached == 0) {
+    static const int cached = [] {
         int dev = 0, v = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
-            cached = v;
-        else
-            cached = 152;
-    }
+            return v;
+        return 152;
+    }();
     return cached;
 }
 
@@ -291,7 +289,7 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
         int64_t* tmp = nullptr;
         CK(cuda_rc(cudaMalloc(&tmp, (n + 1) * sizeof(int64_t)), "cudaMalloc tmp"));
         cudaError_t e = cudaMemcpyAsync(tmp, rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
-        if (e == cudaSuccess) e = launch_rowptr_narrow(s, n + 1, tmp, c->A.rowptr);
+        if (e == cudaSuccess) e = launch_rowptr_narrow(s, n + 1, tmp, c->A.rowptr, nnz);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         cudaFree(tmp);
         CK(cuda_rc(e, "rowptr copy"));

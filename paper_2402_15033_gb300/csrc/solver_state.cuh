@@ -71,7 +71,7 @@ cudaError_t launch_narrow_vals(cudaStream_t st, int64_t m, const double* in, flo
 cudaError_t launch_validate_csr(cudaStream_t st, int64_t n, int64_t nnz, const int32_t* rowptr,
                                 const int32_t* colind, int32_t* bad);
 cudaError_t launch_rowabs(cudaStream_t st, const DevCSR& A, unsigned long long* out);
-cudaError_t launch_rowptr_narrow(cudaStream_t st, int64_t m, const int64_t* in, int32_t* out);
+cudaError_t launch_rowptr_narrow(cudaStream_t st, int64_t m, const int64_t* in, int32_t* out, int64_t nnz);
 cudaError_t launch_cycle_begin(cudaStream_t st, DevState* ds, const CycleBasis& cb);
 cudaError_t launch_hessenberg_ls(cudaStream_t st, DevState* ds, int lo, int t);
 // BCGS2-CholQR2 block factor from the five reductions' factors (S: 5 blocks of kMaxCols^2)

@@ -157,10 +157,14 @@ __global__ void rowabs_kernel(int64_t n, const int32_t* __restrict__ rowptr, con
     if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
 }
 
-__global__ void rowptr_narrow_kernel(int64_t m, const int64_t* in, int32_t* out) {
+// Entries outside [0, nnz] become -1, which the CSR validation rejects (a plain
+// narrowing could wrap one into a valid-looking offset).
+__global__ void rowptr_narrow_kernel(int64_t m, const int64_t* in, int32_t* out, int64_t nnz) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = (int32_t)in[i];
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = in[i];
+        out[i] = (v < 0 || v > nnz) ? -1 : (int32_t)v;
+    }
 }
 
 int vec_grid(int64_t n) {
@@ -230,8 +234,8 @@ cudaError_t launch_rowabs(cudaStream_t st, const DevCSR& A, unsigned long long* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_rowptr_narrow(cudaStream_t st, int64_t m, const int64_t* in, int32_t* out) {
-    rowptr_narrow_kernel<<<vec_grid(m), kVecThreads, 0, st>>>(m, in, out);
+cudaError_t launch_rowptr_narrow(cudaStream_t st, int64_t m, const int64_t* in, int32_t* out, int64_t nnz) {
+    rowptr_narrow_kernel<<<vec_grid(m), kVecThreads, 0, st>>>(m, in, out, nnz);
     return cudaGetLastError();
 }
 

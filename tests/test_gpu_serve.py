@@ -81,6 +81,24 @@ def test_request_larger_than_the_budget_is_rejected(lib):
     assert r["status"] == capi.GMRES_ERR_OOM and st["rejected"] == 1
 
 
+def test_wait_on_an_unknown_or_collected_id_is_an_argument_error(lib):
+    """wait returns GMRES_ERR_ARG, without blocking, for an id the server never
+    issued and for one whose result was already collected."""
+    import ctypes as C
+    from paper_2402_15033_gb300 import capi
+    A = synth.laplace2d(16)
+    b = kr.as_operator(A) @ synth.x_true(A.n, 0)
+    srv = capi.Server(max_active=2)
+    rid = srv.submit(A, b, opts=capi.default_opts(m=30, s=5, panel=30))
+    x, r = srv.wait(rid)
+    assert r["status"] == 0
+    wait = capi.load().gmres_server_wait
+    res = capi.gmres_result()
+    assert wait(srv.h, rid, None, C.byref(res), -1.0) == capi.GMRES_ERR_ARG
+    assert wait(srv.h, rid + 1000, None, C.byref(res), -1.0) == capi.GMRES_ERR_ARG
+    srv.stop()
+
+
 def test_late_small_request_overtakes_a_running_long_one(lib):
     """Continuous batching, not a queue: a small request submitted after a long
     one has started is admitted alongside it and finishes first."""

@@ -145,6 +145,13 @@ def test_device_csr_input(lib):
     rc, res = S.solve(b, x)
     S.close()
     assert rc == 0 and res["relres_true"] <= 1e-8
+    # a 64-bit row offset that would wrap to a valid 32-bit one is rejected
+    assert rp.dtype == torch.int64
+    bad = rp.clone()
+    bad[5] += 1 << 32
+    with pytest.raises(capi.GmresError) as e:
+        capi.Solver(A.n, bad, ci, vv, capi.default_opts(m=20, s=5, panel=20))
+    assert e.value.code == capi.GMRES_ERR_ARG
 
 
 def test_zero_rhs_and_nan_rhs(lib):
