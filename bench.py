@@ -495,10 +495,10 @@ def run_ours(args):
     # ---- CPU oracle on a bounded sample of the same workload
     cpu = None
     if rank == 0 and not args.no_cpu:
-        rows = 2 * args.ref_rows
-        val, dt = cpu_oracle_rate(rows, 1)
+        rows, steps = n, 2
+        val, dt = cpu_oracle_rate(rows, steps)
         cpu = {"value": round(val, 3), "unit": "GB/s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"one step on {rows} of {n} rows (numpy FP64 oracle), {dt:.1f} s"}
+               "sample": f"{steps} steps on all {rows} rows (numpy FP64 oracle), {dt:.1f} s"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,

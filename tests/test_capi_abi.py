@@ -72,6 +72,11 @@ def test_bad_arguments_are_rejected_before_any_launch(capi):
     rc = lib.ortho_stage1(None, 100, None, 100, 0, C.c_void_p(8), 100, 5, C.c_void_p(256), 5,
                           C.c_void_p(256), 1 << 20, st)
     assert rc == capi.GMRES_ERR_ARG and "aligned" in capi.last_error()
+    # size limits: nb <= 64, k + nb <= 256 (dummy pointers, never read)
+    for k, nb in ((0, 65), (192, 65), (200, 57), (256, 1)):
+        rc = lib.ortho_stage2(None, 1000, C.c_void_p(256), 1000, k, C.c_void_p(256), 1000, nb, C.c_void_p(256),
+                              k + nb, C.c_void_p(256), 1 << 30, st)
+        assert rc == capi.GMRES_ERR_ARG and "k + nb <= 256" in capi.last_error(), (k, nb)
     # too small workspace
     rc = lib.ortho_stage2(None, 100, None, 100, 0, C.c_void_p(256), 100, 5, C.c_void_p(256), 5,
                           C.c_void_p(256), 8, st)

@@ -74,7 +74,7 @@ def test_stage1_matches_oracle(lib, n, k, nb):
 
 
 @pytest.mark.parametrize("n,k,nb", [(61, 0, 61), (2000, 0, 61), (70001, 0, 61), (3333, 20, 21),
-                                    (4000, 70, 40), (9000, 0, 17), (5000, 120, 64)])
+                                    (4000, 70, 40), (9000, 0, 17), (5000, 120, 64), (3001, 192, 64)])
 def test_stage2_matches_oracle(lib, n, k, nb):
     from paper_2402_15033_gb300 import capi
     g = synth.rng(200 + n + k)
