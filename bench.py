@@ -239,6 +239,24 @@ def cpu_threads():
         return os.cpu_count()
 
 
+def max_over_ranks(x, world, device=None):
+    """The slowest rank's x (a time in ms): an all-reduce MAX over the process
+    group (NCCL on GPUs, gloo on CPUs); x itself at N = 1."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(bytes_per_rank, ms, world):
+    """GB/s of the whole job: each of the world ranks moves bytes_per_rank, all
+    within ms (the slowest rank's time)."""
+    return bytes_per_rank / (ms * 1e-3) / 1e9 * world
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -389,14 +407,10 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    total_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), world, dev)
     ms_per_step = total_ms / args.steps
     bytes_step = BYTES_PER_ROW * n
-    value = bytes_step / (ms_per_step * 1e-3) / 1e9 * world
+    value = whole_job_gbs(bytes_step, ms_per_step, world)
 
     # per-kernel-family time; the dominant one carries the roofline
     fam, families = families_of(evs, args.arith, args.steps)
@@ -474,8 +488,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         if int(st.abs().sum().item()) != 0:
             raise RuntimeError("Cholesky breakdown in the end-to-end steps")
-        ems = a.elapsed_time(b) / ke
-        e2e = {"value": round(bytes_step / (ems * 1e-3) / 1e9 * world, 3), "unit": "GB/s",
+        ems = max_over_ranks(a.elapsed_time(b) / ke, world, dev)
+        e2e = {"value": round(whole_job_gbs(bytes_step, ems, world), 3), "unit": "GB/s",
                "h2d_bytes_per_step": int(hostin.numel() * 8),
                "d2h_bytes_per_step": int(hostq[0].numel() * 8 + hostr[0].numel() * 8),
                "ms_per_step": round(ems, 3), "steps": ke,
