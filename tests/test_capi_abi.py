@@ -102,3 +102,25 @@ def test_digit_basis_size_formula(capi):
         chunks = (n + 63) // 64
         expect = chunks * capc * 64 * 16 + chunks * ((capc + 3) // 4 * 4) * 4 + 256
         assert capi.digits_bytes(n, capc) == expect, (n, capc)
+
+
+def test_footprint_covers_the_resident_state(capi):
+    """gmres_footprint (host code; the serving loop admits requests by it): at
+    least the basis (m+1) x n in the basis precision plus the CSR, as the
+    admission rule states; the tensor-core arithmetic adds the digit basis
+    (16 bytes per basis entry); monotone in n and nnz; 0 for invalid input."""
+    n, nnz = 1 << 20, 5 << 20
+    ldq = (n + 31) // 32 * 32
+    csr = (n + 1) * 4 + nnz * 4 + nnz * 8
+    f64 = capi.footprint(n, nnz, capi.default_opts(m=60, s=5, panel=60))
+    mix = capi.footprint(n, nnz, capi.default_opts(m=60, s=5, panel=60, precision=capi.GMRES_PREC_MIXED))
+    tc = capi.footprint(n, nnz, capi.default_opts(m=60, s=5, panel=60, arith=capi.GMRES_ARITH_TC))
+    assert f64 >= 61 * ldq * 8 + csr
+    assert mix >= 61 * ldq * 4 + csr + nnz * 4     # FP32 basis, plus the FP32 copy of the values
+    assert mix < f64 - 61 * ldq * 3                 # the basis takes half the bytes
+    assert tc - f64 >= 61 * n * 16                  # seven bf16 digits (+ one spare) per entry
+    assert f64 - csr < 61 * ldq * 8 * 1.25          # and not much else
+    assert capi.footprint(2 * n, nnz, capi.default_opts(m=60, s=5, panel=60)) > f64
+    assert capi.footprint(n, 2 * nnz, capi.default_opts(m=60, s=5, panel=60)) > f64
+    assert capi.footprint(0, nnz, capi.default_opts()) == 0
+    assert capi.footprint(n, nnz, capi.default_opts(m=60, s=7, panel=60)) == 0
