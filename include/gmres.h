@@ -306,7 +306,8 @@ int ortho_update_tcd(void* stream, int64_t n, const double* Q, int64_t ldq, int3
  * system converged, else the most severe per-system status. */
 typedef struct gmres_batch gmres_batch;
 
-/* Device bytes a batch of these sizes would allocate (for admission control). */
+/* Device bytes a batch of these sizes would allocate (for admission control);
+ * 0 for options gmres_batch_create rejects, n[i] < 1 or nnz[i] < 0. */
 size_t gmres_batch_footprint(int32_t nsys, const int64_t* n, const int64_t* nnz, const gmres_opts* opts);
 
 int gmres_batch_create(gmres_batch** out, int32_t nsys, const int64_t* n, const int64_t* const* rowptr,

@@ -502,14 +502,31 @@ int gmres_batch_destroy(gmres_batch* c) {
     return GMRES_OK;
 }
 
+// The options a batch accepts (GMRES_ERR_ARG with the reason otherwise).
+static int check_batch_opts(const gmres_opts& o) {
+    GM_ARG(o.m >= 1 && o.m + 1 <= kMaxCols && o.s >= 1 && o.s <= 16 && o.panel % o.s == 0 && o.m % o.panel == 0,
+           "need s | panel | m, m + 1 <= 64, s <= 16");
+    GM_ARG(o.precision == GMRES_PREC_FP64 || o.precision == GMRES_PREC_MIXED, "unknown precision");
+    GM_ARG(o.tol > 0.0 && o.max_restarts >= 1, "bad tol / max_restarts");
+    GM_ARG(o.arith == GMRES_ARITH_FP64 || o.arith == GMRES_ARITH_DD,
+           "arith must be GMRES_ARITH_FP64 or GMRES_ARITH_DD for batches");
+    GM_ARG(o.ortho == GMRES_ORTHO_TWO_STAGE || o.ortho == GMRES_ORTHO_BCGS_PIP2,
+           "ortho must be GMRES_ORTHO_TWO_STAGE or GMRES_ORTHO_BCGS_PIP2 for batches");
+    GM_ARG(o.basis == GMRES_BASIS_MONOMIAL || o.basis == GMRES_BASIS_NEWTON,
+           "basis must be GMRES_BASIS_MONOMIAL or GMRES_BASIS_NEWTON for batches (pass the shifts in opts.theta)");
+    return GMRES_OK;
+}
+
 size_t gmres_batch_footprint(int32_t nsys, const int64_t* n, const int64_t* nnz, const gmres_opts* opts) {
     if (nsys <= 0 || !n || !nnz) return 0;
     gmres_opts o;
     if (opts) o = *opts; else gmres_default_opts(&o);
     if (o.ortho == GMRES_ORTHO_BCGS_PIP2) o.panel = o.s;
+    if (check_batch_opts(o)) return 0;
     const size_t esz = o.precision == GMRES_PREC_MIXED ? 4 : 8;
     size_t rows = 0, nz = 0, vt = 0;
     for (int i = 0; i < nsys; ++i) {
+        if (n[i] < 1 || nnz[i] < 0) return 0;
         rows += (size_t)((n[i] + 31) / 32 * 32);
         nz += (size_t)nnz[i];
         vt += (size_t)reduction_grid(n[i]);
@@ -533,16 +550,10 @@ int gmres_batch_create(gmres_batch** out, int32_t nsys, const int64_t* n, const 
     gmres_opts o;
     if (opts) o = *opts; else gmres_default_opts(&o);
     if (o.ortho == GMRES_ORTHO_BCGS_PIP2) o.panel = o.s;
-    GM_ARG(o.m >= 1 && o.m + 1 <= kMaxCols && o.s >= 1 && o.s <= 16 && o.panel % o.s == 0 && o.m % o.panel == 0,
-           "need s | panel | m, m + 1 <= 64, s <= 16");
-    GM_ARG(o.precision == GMRES_PREC_FP64 || o.precision == GMRES_PREC_MIXED, "unknown precision");
-    GM_ARG(o.tol > 0.0 && o.max_restarts >= 1, "bad tol / max_restarts");
-    GM_ARG(o.arith == GMRES_ARITH_FP64 || o.arith == GMRES_ARITH_DD,
-           "arith must be GMRES_ARITH_FP64 or GMRES_ARITH_DD for batches");
-    GM_ARG(o.ortho == GMRES_ORTHO_TWO_STAGE || o.ortho == GMRES_ORTHO_BCGS_PIP2,
-           "ortho must be GMRES_ORTHO_TWO_STAGE or GMRES_ORTHO_BCGS_PIP2 for batches");
-    GM_ARG(o.basis == GMRES_BASIS_MONOMIAL || o.basis == GMRES_BASIS_NEWTON,
-           "basis must be GMRES_BASIS_MONOMIAL or GMRES_BASIS_NEWTON for batches (pass the shifts in opts.theta)");
+    {
+        const int rc = check_batch_opts(o);
+        if (rc) return rc;
+    }
     gmres_batch* c = new gmres_batch();
     c->opts = o;
     c->nsys = nsys;

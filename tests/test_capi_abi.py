@@ -124,3 +124,29 @@ def test_footprint_covers_the_resident_state(capi):
     assert capi.footprint(n, 2 * nnz, capi.default_opts(m=60, s=5, panel=60)) > f64
     assert capi.footprint(0, nnz, capi.default_opts()) == 0
     assert capi.footprint(n, nnz, capi.default_opts(m=60, s=7, panel=60)) == 0
+
+
+def test_batch_footprint_covers_the_resident_state(capi):
+    """gmres_batch_footprint (host code): at least every system's basis rows
+    (padded to 32) x (m+1) in the basis precision plus the concatenated CSR;
+    0 for options a batch rejects and for empty systems."""
+    import ctypes as C2
+    ns = [1000, 4097, 250001]
+    nz = [5 * v for v in ns]
+    N = (C2.c_int64 * 3)(*ns)
+    Z = (C2.c_int64 * 3)(*nz)
+    lib = capi.load()
+    rows = sum((v + 31) // 32 * 32 for v in ns)
+    csr = (rows + 3) * 4 + sum(nz) * 12
+    f64 = lib.gmres_batch_footprint(3, N, Z, C2.byref(capi.default_opts(m=40, s=5, panel=40)))
+    mix = lib.gmres_batch_footprint(3, N, Z, C2.byref(capi.default_opts(m=40, s=5, panel=40,
+                                                                          precision=capi.GMRES_PREC_MIXED)))
+    assert f64 >= rows * 41 * 8 + csr
+    assert mix >= rows * 41 * 4 + csr + sum(nz) * 4
+    assert mix < f64
+    for bad in (dict(m=40, s=5, panel=15), dict(m=64, s=8, panel=64), dict(arith=capi.GMRES_ARITH_TC),
+                dict(ortho=2), dict(basis=capi.GMRES_BASIS_NEWTON_AUTO)):
+        o = capi.default_opts(**{**dict(m=40, s=5, panel=40), **bad})
+        assert lib.gmres_batch_footprint(3, N, Z, C2.byref(o)) == 0, bad
+    N0 = (C2.c_int64 * 3)(1000, 0, 5)
+    assert lib.gmres_batch_footprint(3, N0, Z, C2.byref(capi.default_opts(m=40, s=5, panel=40))) == 0
