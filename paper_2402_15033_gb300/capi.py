@@ -165,6 +165,23 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _vec(a, n, name, writable=False):
+    """Checks a solver vector before its pointer goes to the library: a
+    contiguous float64 numpy array (host) or CUDA tensor (device) of n entries.
+    Returns (pointer, on_device)."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64 or not a.is_cuda or not a.is_contiguous() or a.numel() != n:
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of {n} entries")
+        return C.c_void_p(a.data_ptr()), True
+    import numpy as np
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous or a.size != n:
+        raise ValueError(f"{name} must be a contiguous float64 numpy array of {n} entries")
+    if writable and not a.flags.writeable:
+        raise ValueError(f"{name} must be writable")
+    return a.ctypes.data_as(C.c_void_p), False
+
+
 class Solver:
     """gmres_create / gmres_solve / gmres_destroy around one CSR matrix.
 
@@ -196,11 +213,11 @@ class Solver:
         x holds x0 and receives the solution.  Returns (status, result dict)."""
         lib = load()
         res = gmres_result()
-        if hasattr(b, "data_ptr"):
-            rc = lib.gmres_solve(self.h, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), 1, C.byref(res))
-        else:
-            rc = lib.gmres_solve(self.h, b.ctypes.data_as(C.c_void_p), x.ctypes.data_as(C.c_void_p), 0,
-                                 C.byref(res))
+        bp, b_dev = _vec(b, self.n, "b")
+        xp, x_dev = _vec(x, self.n, "x", writable=True)
+        if b_dev != x_dev:
+            raise ValueError("b and x must both be on the host or both on the device")
+        rc = lib.gmres_solve(self.h, bp, xp, int(b_dev), C.byref(res))
         out = res.as_dict()
         out["error"] = last_error() if rc < 0 else ""
         return rc, out
@@ -256,6 +273,11 @@ class Batch:
         """bs, xs: lists of float64 numpy arrays (x holds x0, receives x).
         Returns (worst status, list of result dicts)."""
         ns = len(self.mats)
+        if len(bs) != ns or len(xs) != ns:
+            raise ValueError(f"need {ns} right-hand sides and {ns} solution vectors")
+        for i, (b, x) in enumerate(zip(bs, xs)):
+            if _vec(b, self.n[i], f"b[{i}]")[1] or _vec(x, self.n[i], f"x[{i}]", writable=True)[1]:
+                raise ValueError("batch vectors are host numpy arrays")
         res = (gmres_result * ns)()
         rc = load().gmres_batch_solve(self.h, _ptr_array(bs), _ptr_array(xs), res)
         if rc in (GMRES_ERR_ARG, GMRES_ERR_CUDA, GMRES_ERR_OOM):
@@ -296,6 +318,9 @@ class Server:
     def submit(self, A, b, x0=None, opts=None):
         rid = C.c_int64()
         o = opts if opts is not None else default_opts()
+        for v, name in ((b, "b"), (x0, "x0")):
+            if v is not None and _vec(v, int(A.n), name)[1]:
+                raise ValueError(f"{name} must be a host numpy array")
         check(load().gmres_server_submit(self.h, int(A.n), A.rowptr.ctypes.data_as(C.c_void_p),
                                          A.colind.ctypes.data_as(C.c_void_p), A.vals.ctypes.data_as(C.c_void_p),
                                          b.ctypes.data_as(C.c_void_p),
@@ -346,8 +371,8 @@ def _ortho(fn, Q, V, R, work, status, k, stream):
     ldq = Q.stride(1) if (Q is not None and k > 0) else n
     qp = C.c_void_p(Q.data_ptr()) if (Q is not None and k > 0) else None
     return fn(C.c_void_p(stream or 0), int(n), qp, int(ldq), int(k), C.c_void_p(V.data_ptr()), int(ldv), int(nb),
-              C.c_void_p(R.data_ptr()), int(R.stride(1)), C.c_void_p(work.data_ptr()), int(work.numel()),
-              C.c_void_p(status.data_ptr()))
+              C.c_void_p(R.data_ptr()), int(R.stride(1)), C.c_void_p(work.data_ptr()),
+              int(work.numel() * work.element_size()), C.c_void_p(status.data_ptr()))
 
 
 def ortho_gram_chol(Q, V, R, work, status, k=None, stream=None):
@@ -382,7 +407,8 @@ def ortho_update(Q, V, R, status, k=None, stream=None, dd=False, tc=False):
 
 
 def digits_bytes(n, capc):
-    """Bytes of a digit basis of capc columns for n rows (about 14 per value)."""
+    """Bytes of a digit basis of capc columns for n rows: 16 per value (seven
+    bf16 digits and a spare) plus an int32 exponent per 64-row chunk and column."""
     return int(load().ortho_digits_bytes(int(n), int(capc)))
 
 

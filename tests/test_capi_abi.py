@@ -150,3 +150,20 @@ def test_batch_footprint_covers_the_resident_state(capi):
         assert lib.gmres_batch_footprint(3, N, Z, C2.byref(o)) == 0, bad
     N0 = (C2.c_int64 * 3)(1000, 0, 5)
     assert lib.gmres_batch_footprint(3, N0, Z, C2.byref(capi.default_opts(m=40, s=5, panel=40))) == 0
+
+
+def test_binding_rejects_bad_host_vectors(capi):
+    """The binding checks solver vectors before their pointers reach the
+    library: float64, contiguous, the system's length, x writable."""
+    import numpy as np
+    ok = np.zeros(10)
+    p, dev = capi._vec(ok, 10, "b")
+    assert dev is False and p.value == ok.ctypes.data
+    for bad in (np.zeros(9), np.zeros(10, dtype=np.float32), np.zeros(20)[::2], [0.0] * 10):
+        with pytest.raises(ValueError):
+            capi._vec(bad, 10, "b")
+    ro = np.zeros(10)
+    ro.flags.writeable = False
+    capi._vec(ro, 10, "b")
+    with pytest.raises(ValueError):
+        capi._vec(ro, 10, "x", writable=True)
