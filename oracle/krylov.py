@@ -1,4 +1,4 @@
-"""GMRES drivers of the oracle, FP64, restated from the paper (test infrastructure only).
+"""GMRES solvers of the oracle, FP64, restated from the paper (test infrastructure only).
 
 * ``gmres_cgs2``   standard restarted GMRES(m), Arnoldi with classical
                    Gram-Schmidt twice (the "GMRES + CGS2" arm of Table 3, §I).

@@ -1,4 +1,4 @@
-// s-step GMRES driver (Fig. 1, §III) with two-stage block orthogonalization
+// s-step GMRES solver loop (Fig. 1, §III) with two-stage block orthogonalization
 // (§V, Fig. 5) and the C ABI of include/gmres.h.
 //
 // One restart cycle, all on the device, in stream order:
