@@ -214,9 +214,13 @@ def logscaled(n: int, c: int, kappa: float, seed: int) -> np.ndarray:
 
 
 def glued(n: int, c: int, panels: int, kappa_panel: float, seed: int, growth: float = 2.0) -> np.ndarray:
-    """Panels V_j = X_j diag(logspace) Y_j^T of condition ~kappa_panel each, with
-    V_j mixed with the previous panel so that the accumulated condition number
-    grows roughly by ``growth`` per panel."""
+    """Panels V_j = X_j diag(logspace) Y_j^T of condition kappa_panel, each one
+    after the first mixed with its predecessor: V_j += (1 - 1/growth) V_{j-1} W_j
+    (W_j Gaussian / sqrt(c)), so consecutive panels are far from orthogonal.
+    The first panel keeps condition kappa_panel; the mixing term dominates the
+    later panels' small singular values, so their own condition numbers fall
+    (to 10-1000 for kappa_panel = 1e5) and the accumulated condition number
+    grows only slowly (1e5 -> 1.4e5-2.8e5 over five panels of six columns)."""
     g = rng(seed)
     blocks = []
     for j in range(panels):

@@ -147,8 +147,8 @@ def test_cholqr_error_grows_like_kappa_squared_and_cholqr2_is_stable():
 
 
 def test_two_stage_on_glued_matrix_reaches_machine_precision():
-    """Theorem 3 (§V) on the glued matrix of §VI (panel kappa 1e5, growing
-    accumulated kappa): after stage 1 the big panel has O(1) condition number
+    """Theorem 3 (§V) on the glued matrix of §VI (first panel kappa 1e5, the
+    panels mixed with their predecessors): after stage 1 the big panel has O(1) condition number
     (Eq. 11); after stage 2 the orthogonality error is O(eps)."""
     n, s, panels = 5000, 5, 6
     V = synth.glued(n, s, panels, 1e5, seed=3)
