@@ -16,9 +16,12 @@ Workloads (shapes follow the paper's test problems, §VI and §VIII):
   per row, a stand-in for the wider SuiteSparse rows of Table 4.
 * ``logscaled(n, c, kappa)``  X diag(logspace) Y^T panels (the ``Logscaled``
   matrix of the CholQR2 experiment, §VI).
-* ``glued(...)``  panels of fixed condition number whose accumulated condition
-  number grows (the ``glued`` matrix of the BCGS-PIP2 and two-stage
-  experiments, §VI).
+* ``glued(...)``  panels mixed with their predecessors: the first of
+  condition kappa_panel, the later ones better conditioned, the accumulated
+  condition number growing slowly.
+* ``glued_sweep(...)``  panels of exactly kappa_panel each whose column spaces
+  draw closer as kappa_mix grows, so the total condition number is swept with
+  the panels' own fixed (the ``glued`` experiments of §VI).
 * ``tall_basis(n, c)``  N(0,1)/sqrt(n) columns for the standalone block
   orthogonalization benchmark.
 """
@@ -28,7 +31,7 @@ import numpy as np
 
 __all__ = [
     "CSR", "laplace2d", "laplace3d", "convdiff2d", "convdiff3d", "banded_random",
-    "x_true", "tall_basis", "logscaled", "glued", "rng",
+    "x_true", "tall_basis", "logscaled", "glued", "glued_sweep", "rng",
 ]
 
 
@@ -230,3 +233,34 @@ def glued(n: int, c: int, panels: int, kappa_panel: float, seed: int, growth: fl
             V = V + (1.0 - 1.0 / growth) * (blocks[-1] @ W)
         blocks.append(V)
     return np.asfortranarray(np.concatenate(blocks, axis=1))
+
+
+def glued_sweep(n: int, c: int, panels: int, kappa_panel: float, kappa_mix: float, seed: int) -> np.ndarray:
+    """Big panel of ``panels`` blocks of c columns: every block has 2-norm
+    condition number kappa_panel exactly, and the total condition number grows
+    with kappa_mix while the blocks' own stays fixed.
+
+    Y = logscaled(n, c * panels, kappa_mix) sets the geometry: block j is
+    Q_j diag(logspace(0, -log10 kappa_panel, c)) Z_j^T, with Q_j an orthonormal
+    basis of Y's block column j and Z_j a random c x c orthogonal matrix.  The
+    larger kappa_mix, the smaller the principal angles between the blocks'
+    column spaces.  For 6 blocks of 5 columns at kappa_panel = 1e3 the total
+    condition number is 10-300 times kappa_mix for kappa_mix from 1e2 to 1e10
+    (measured in the tests).
+    """
+    g = rng(seed)
+    Y = logscaled(n, c * panels, kappa_mix, int(g.integers(1 << 31)))
+    sig = np.logspace(0.0, -np.log10(kappa_panel), c)
+    out = np.empty((n, c * panels), order="F")
+    for j in range(panels):
+        Qj = _orthonormal_factor_of(Y[:, j * c:(j + 1) * c])
+        Z = _orthonormal_factor(g, c, c)
+        out[:, j * c:(j + 1) * c] = (Qj * sig) @ Z.T
+    return out
+
+
+def _orthonormal_factor_of(Y):
+    # Orthonormal basis of Y's columns (numpy's LAPACK QR, signs fixed); test
+    # inputs only.
+    q, r = np.linalg.qr(Y)
+    return q * np.sign(np.diag(r))

@@ -162,6 +162,32 @@ def test_two_stage_on_glued_matrix_reaches_machine_precision():
     assert np.all(np.diag(Rd) > 0)
 
 
+@pytest.mark.parametrize("seed", [1, 2])
+def test_two_stage_on_the_glued_sweep(seed):
+    """§V on the glued sweep of §VI (six blocks of condition 1e3 each, the
+    total condition number swept): after stage 1 the big panel's orthogonality
+    error grows like kappa^2 eps (Eq. 10) while its condition number stays O(1)
+    (Eq. 11); after stage 2 the error is O(eps) (Theorem 3) and V = Q R.  Far
+    beyond eps^(-1/2) the assumption of Eq. 9 fails: a stage-1 Cholesky breaks
+    down and is reported."""
+    n, c, p = 4000, 5, 6
+    for km in (1e2, 1e4, 1e6):
+        V = synth.glued_sweep(n, c, p, 1e3, km, seed)
+        kap = checks.cond2(V)
+        blocks = [V[:, i * c:(i + 1) * c] for i in range(p)]
+        Q, Rt, Rd, Qhat = bo.two_stage_panel(np.zeros((n, 0)), blocks)
+        e1 = checks.orth_error(Qhat)[0]
+        assert 0.01 * kap ** 2 * EPS <= e1 <= 10 * kap ** 2 * EPS, (km, kap, e1)
+        assert checks.cond2(Qhat) < 2.0
+        assert checks.orth_error(Q)[0] < 100 * EPS
+        assert np.abs(Q @ Rd - V).max() <= 1e-13 * np.abs(V).max()
+    V = synth.glued_sweep(n, c, p, 1e3, 1e10, seed)
+    assert checks.cond2(V) > 1e11
+    with pytest.raises(bo.Breakdown) as e:
+        bo.two_stage_panel(np.zeros((n, 0)), [V[:, i * c:(i + 1) * c] for i in range(p)])
+    assert "stage1" in str(e.value)
+
+
 def test_two_stage_panel_equals_householder_r():
     """The two-stage R factor of a well-conditioned big panel is the unique
     positive-diagonal R of its QR (Fig. 1 caption)."""

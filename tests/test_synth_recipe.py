@@ -129,3 +129,18 @@ def test_glued_panels_as_documented(growth):
         Qa = np.linalg.qr(V[:, c * (j - 1):c * j])[0]
         Qb = np.linalg.qr(V[:, c * j:c * (j + 1)])[0]
         assert np.linalg.svd(Qa.T @ Qb, compute_uv=False)[0] > 0.5
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_glued_sweep_fixes_the_panels_and_sweeps_the_total(seed):
+    n, c, p, kp = 4000, 5, 6, 1e3
+    prev = 0.0
+    for km in (1e2, 1e4, 1e6, 1e10):
+        V = synth.glued_sweep(n, c, p, kp, km, seed)
+        assert V.shape == (n, c * p) and V.flags.f_contiguous
+        for j in range(p):
+            assert np.linalg.cond(V[:, c * j:c * (j + 1)]) == pytest.approx(kp, rel=1e-6)
+        tot = np.linalg.cond(V)
+        assert 10 * km <= tot <= 300 * km
+        assert tot > prev
+        prev = tot
