@@ -792,6 +792,7 @@ int gmres_batch_autotune(gmres_batch* c, double* res_ms) {
 int gmres_batch_solve(gmres_batch* c, const double* const* b, double* const* x, gmres_result* res) {
     clear_error();
     GM_ARG(c != nullptr && b != nullptr && x != nullptr, "NULL argument");
+    for (int i = 0; i < c->nsys; ++i) GM_ARG(b[i] != nullptr && x[i] != nullptr, "system %d: NULL b or x", i);
     if (cudaSetDevice(c->device) != cudaSuccess) return cuda_rc_b(cudaGetLastError(), "cudaSetDevice");
     const gmres_opts& o = c->opts;
     cudaStream_t s = c->stream;
