@@ -321,6 +321,46 @@ def test_convergence_tests_fall_on_panel_boundaries():
         assert info["iters"] % step == 0
 
 
+def _krylov_minimizer(A, b, x0, m):
+    """x0 + argmin over K_m(A, r0) of ||b - A x||, by brute force: the power
+    vectors r0, A r0, ..., A^(m-1) r0 (each normalized), their LAPACK QR, and a
+    dense least-squares solve."""
+    r0 = b - A @ x0
+    K = np.empty((len(b), m))
+    v = r0 / np.linalg.norm(r0)
+    for j in range(m):
+        K[:, j] = v
+        v = A @ v
+        v /= np.linalg.norm(v)
+    Qk = np.linalg.qr(K)[0]
+    z = np.linalg.lstsq(A @ Qk, r0, rcond=None)[0]
+    return x0 + Qk @ z
+
+
+@pytest.mark.parametrize("ortho,s,panel,theta", [("two_stage", 5, 15, None), ("bcgs_pip2", 5, 5, None),
+                                                 ("bcgs2_cholqr2", 5, 5, None),
+                                                 ("two_stage", 5, 15, (2.3, 1.7, 2.0, 1.5, 2.5))])
+def test_one_cycle_is_the_minimal_residual_iterate(ortho, s, panel, theta):
+    """GMRES' defining property (§I, §III): one restart cycle of m steps from
+    x0 returns the minimizer of ||b - A x|| over x0 + K_m(A, r0), whatever the
+    block scheme and whether the basis is monomial or Newton (both span K_m).
+    A small nonsymmetric system whose residual after 15 steps is still 2.6e-2,
+    so that the 15-step and 10-step minimizers differ by 11%."""
+    import scipy.sparse as sp
+    g = synth.rng(77)
+    n, m = 60, 15
+    A = sp.csr_matrix(2.0 * np.eye(n) + 1.8 * g.standard_normal((n, n)) / np.sqrt(n))
+    b = g.standard_normal(n)
+    x0 = 0.1 * g.standard_normal(n)
+    xref = _krylov_minimizer(A, b, x0, m)
+    assert np.linalg.norm(xref - _krylov_minimizer(A, b, x0, m - 5)) > 0.1 * np.linalg.norm(xref)
+    th = None if theta is None else np.array(theta)
+    x, info = kr.sstep_gmres(A, b, x0=x0, m=m, s=s, panel=panel, tol=1e-30, max_restarts=1, ortho=ortho, theta=th)
+    assert info["iters"] == m and info["restarts"] == 1
+    assert np.linalg.norm(x - xref) <= 1e-8 * np.linalg.norm(xref)
+    assert np.linalg.norm(b - A @ x) <= (1 + 1e-8) * np.linalg.norm(b - A @ xref)
+
+
 def test_s_equal_one_is_standard_gmres():
     """§III: standard GMRES is s-step GMRES with step size one."""
     A = synth.convdiff2d(20, seed=7)
