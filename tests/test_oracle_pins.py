@@ -361,6 +361,23 @@ def test_one_cycle_is_the_minimal_residual_iterate(ortho, s, panel, theta):
     assert np.linalg.norm(b - A @ x) <= (1 + 1e-8) * np.linalg.norm(b - A @ xref)
 
 
+def test_restart_applies_the_minimal_residual_property_cycle_by_cycle():
+    """Restarted GMRES(m): the second cycle starts from the first cycle's x and
+    returns the minimizer over x1 + K_m(A, r1)."""
+    import scipy.sparse as sp
+    g = synth.rng(78)
+    n, m = 60, 10
+    A = sp.csr_matrix(2.0 * np.eye(n) + 1.8 * g.standard_normal((n, n)) / np.sqrt(n))
+    b = g.standard_normal(n)
+    x0 = np.zeros(n)
+    x1 = _krylov_minimizer(A, b, x0, m)
+    x2 = _krylov_minimizer(A, b, x1, m)
+    assert np.linalg.norm(x2 - x1) > 0.01 * np.linalg.norm(x2)
+    x, info = kr.sstep_gmres(A, b, x0=x0, m=m, s=5, panel=10, tol=1e-30, max_restarts=2)
+    assert info["iters"] == 2 * m and info["restarts"] == 2
+    assert np.linalg.norm(x - x2) <= 1e-8 * np.linalg.norm(x2)
+
+
 def test_s_equal_one_is_standard_gmres():
     """§III: standard GMRES is s-step GMRES with step size one."""
     A = synth.convdiff2d(20, seed=7)
