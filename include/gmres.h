@@ -212,9 +212,13 @@ int ortho_stage2_f32(void* stream, int64_t n, const float* Q, int64_t ldq, int32
  * cudaFree or allocating library routine.
  * Set-up: the first call on a device (with that device current) looks up the
  * array's device address once; make that first call before any stream
- * capture.  Every call shares the one array: calls that may overlap on the
- * GPU (different streams, or different host threads) race and must be
- * serialized by the caller.  Arguments otherwise as for ortho_stage1. */
+ * capture.  The address is kept for the life of the process: after
+ * cudaDeviceReset (or anything else that tears down the device's primary
+ * context) the array may live at another address, and this entry point must
+ * not be called on that device again.  Every call shares the one array: calls
+ * that may overlap on the GPU (different streams, or different host threads)
+ * race and must be serialized by the caller.  Arguments otherwise as for
+ * ortho_stage1. */
 int ortho_stage1_noalloc(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
                          double* V, int64_t ldv, int32_t nb, double* R, int32_t ldr,
                          int32_t* d_status);

@@ -18,12 +18,22 @@ class Breakdown(Exception):
     """Cholesky of a Gram matrix failed (the Gram is not numerically SPD).
 
     This is the failure mode excluded by the stability conditions Eq. (1),
-    Eq. (5) and Eq. (9) of the paper.  ``pivot`` is 1-based."""
+    Eq. (5) and Eq. (9) of the paper.  ``pivot`` is 1-based; ``value`` is the
+    failing pivot (the Schur complement that was not positive).  A breakdown of
+    BCGS-PIP also carries ``margin``: the smallest eigenvalue of the explicitly
+    projected block's Gram (V - Q P)^T (V - Q P) over the 2-norm of the
+    Pythagorean identity's error P^T (Q^T Q - I) P (§IV-C: G - P^T P equals the
+    projected Gram only for an orthonormal Q).  A margin below one means the
+    pivot's sign is decided by Q's loss of orthogonality, itself rounding
+    amplified by earlier blocks' condition numbers, not by the data."""
 
-    def __init__(self, pivot: int, where: str = ""):
+    def __init__(self, pivot: int, where: str = "", value: float = float("nan"),
+                 margin: float = float("inf")):
         super().__init__(f"Cholesky breakdown at pivot {pivot} {where}")
         self.pivot = pivot
         self.where = where
+        self.value = value
+        self.margin = margin
 
 
 def chol_upper(G: np.ndarray):
@@ -44,6 +54,28 @@ def chol_upper(G: np.ndarray):
     return R, 0
 
 
+def pivot_value(G: np.ndarray, R: np.ndarray, info: int) -> float:
+    """The failing pivot of ``chol_upper(G)`` that returned (R, info > 0):
+    G_jj minus the squares of the column's entries already computed."""
+    j = info - 1
+    return float(G[j, j] - np.dot(R[:j, j], R[:j, j]))
+
+
+def pip_margin(Q: np.ndarray, V: np.ndarray, P: np.ndarray) -> float:
+    """lambda_min((V - Q P)^T (V - Q P)) / ||P^T (Q^T Q - I) P||_2 (inf for an
+    exactly orthonormal or empty Q): how far the projected block is from
+    rank deficiency, in units of the error the Pythagorean shortcut of BCGS-PIP
+    makes when Q is not orthonormal (only computed on a breakdown)."""
+    k = Q.shape[1]
+    if k == 0:
+        return float("inf")
+    W = V - Q @ P
+    lmin = float(np.linalg.eigvalsh(W.T @ W)[0])
+    E = P.T @ (Q.T @ Q - np.eye(k)) @ P
+    en = float(np.linalg.norm(E, 2))
+    return float("inf") if en == 0.0 else lmin / en
+
+
 def right_trsm_upper(V: np.ndarray, R: np.ndarray) -> np.ndarray:
     """V R^{-1} for upper-triangular R (the TRSM of CholQR, §VII)."""
     return solve_triangular(R, V.T, trans="T", lower=False).T
@@ -54,7 +86,7 @@ def cholqr(V: np.ndarray, where: str = "cholqr"):
     G = V.T @ V
     R, info = chol_upper(G)
     if info:
-        raise Breakdown(info, where)
+        raise Breakdown(info, where, pivot_value(G, R, info))
     return right_trsm_upper(V, R), R
 
 
@@ -101,7 +133,7 @@ def bcgs_pip(Q: np.ndarray, V: np.ndarray, where: str = "bcgs_pip"):
     S = G - P.T @ P
     T, info = chol_upper(S)
     if info:
-        raise Breakdown(info, where)
+        raise Breakdown(info, where, pivot_value(S, T, info), pip_margin(Q, V, P))
     W = V - Q @ P
     return right_trsm_upper(W, T), P, T
 
@@ -140,7 +172,7 @@ def stage1_lowp(Qacc: np.ndarray, V: np.ndarray, where: str = "stage1", store=np
     G = W.T @ W
     T, info = chol_upper(G)
     if info:
-        raise Breakdown(info, where)
+        raise Breakdown(info, where, pivot_value(G, T, info))
     return right_trsm_upper(W, T).astype(store).astype(np.float64), P, T
 
 

@@ -278,7 +278,8 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
     Returns (x, info dict) with status, iteration count (SpMVs inside restart
     cycles), restarts, the explicit relative residual, the breakdown location
     (``breakdown_block``: s-step block j, or m/s + p for the stage 2 of big
-    panel p; ``breakdown_pivot``: 1-based), and, when
+    panel p; ``breakdown_pivot``: 1-based; ``breakdown_value``: the failing
+    pivot; ``breakdown_margin``: ``Breakdown.margin``), and, when
     ``return_basis``, the last cycle's Q, H and g0 (for Arnoldi-relation tests)."""
     M = as_operator(A)
     n = b.shape[0]
@@ -306,7 +307,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
     status = STATUS_MAXIT
     last = {}
     err_where = None
-    breakdown = (-1, 0)
+    breakdown = (-1, 0, float("nan"), float("inf"))
     for cyc in range(max_restarts):
         r = b - M @ x
         beta = np.linalg.norm(r)
@@ -396,7 +397,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
         except bo.Breakdown as e:
             status = STATUS_BREAKDOWN
             err_where = str(e)
-            breakdown = (where_blk, e.pivot)
+            breakdown = (where_blk, e.pivot, e.value, e.margin)
             break
         y = gv.solve()
         x = x + Q[:, :k_used].astype(f64) @ y
@@ -411,6 +412,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
         hist.append(np.linalg.norm(r) / bnorm)
     info = dict(status=status, iters=iters, restarts=restarts, relres=hist[-1], history=hist,
                 sigma=sig, where=err_where, breakdown_block=breakdown[0], breakdown_pivot=breakdown[1],
+                breakdown_value=breakdown[2], breakdown_margin=breakdown[3],
                 theta=None if th is None else np.asarray(th, dtype=np.float64))
     if return_basis:
         info.update(last)

@@ -32,10 +32,16 @@ def check_against_oracle(capi, A, b, m, s, panel, ortho="two_stage", tol=1e-8, a
     rc, res, x = solve_gpu(capi, A, b, **kw)
     xr, info = kr.sstep_gmres(A, b, m=m, s=s, panel=panel, tol=tol, ortho=ortho)
     if info["status"] == kr.STATUS_BREAKDOWN:
-        # The failing pivot is zero up to rounding, so which side of zero it
-        # lands on is a rounding tie.  Accept a breakdown no more than one block
-        # after the oracle's (earlier ones included), or a solve whose residual
-        # checks out on the host.
+        if (rc == capi.GMRES_ERR_BREAKDOWN and res["breakdown_block"] == info["breakdown_block"]
+                and res["breakdown_pivot"] == info["breakdown_pivot"]):
+            return rc, res, info
+        # Another outcome is allowed only where the oracle's failing pivot is
+        # decided by rounding: the projected block's smallest Gram eigenvalue is
+        # below the error of the Pythagorean shortcut, P^T (Q^T Q - I) P, which
+        # grows from the earlier blocks' rounding (margin < 1).  Then accept a
+        # breakdown no more than one block after the oracle's, or a solve whose
+        # residual checks out on the host.
+        assert info["breakdown_margin"] < 1.0, (res, info["where"], info["breakdown_margin"])
         if rc == capi.GMRES_ERR_BREAKDOWN:
             assert res["breakdown_block"] <= info["breakdown_block"] + 1, (res, info["where"])
         else:
@@ -103,9 +109,12 @@ def test_bcgs2_cholqr2_nonsymmetric_matches_oracle(lib):
                                                 ("convdiff3d", 4, 30, 5, 10), ("banded", 2, 30, 5, 10),
                                                 ("convdiff3d", 4, 60, 5, 60), ("banded", 2, 30, 5, 30)])
 def test_nonsymmetric_systems_match_oracle(lib, gen, seed, m, s, panel):
-    """Upwinded convection-diffusion and random banded systems; the s^ = m
-    cases of the last two rows break down in the oracle (the big panel
-    violates Eq. (9)) and must break down at the same block on the GPU."""
+    """Upwinded convection-diffusion and random banded systems.  The s^ = m
+    cases of the last two rows break down in the oracle's stage 1 (blocks 9 and
+    2): the accumulated pre-processed panel has lost orthogonality (Eq. 10),
+    and the Pythagorean shortcut's error is 1e5-1e7 times the projected
+    block's smallest Gram eigenvalue, so the pivot's sign is a rounding
+    outcome (margin < 1, asserted by check_against_oracle)."""
     from paper_2402_15033_gb300 import capi
     if gen == "convdiff2d":
         A = synth.convdiff2d(50, seed)

@@ -525,3 +525,57 @@ def test_digit_basis_two_stage_sequence_matches_oracle(lib):
     assert np.all(np.abs(R2g - T2) <= 1e-12 * sc[None, :])
     assert np.max(np.abs(Qg - Qf)) <= 1e-12
     assert checks.orth_error(Qg)[0] < 100 * np.finfo(float).eps
+
+
+@pytest.mark.slow
+def test_full_size_digit_basis_sequence_sampled(lib):
+    """The benchmark's headline sequence at its own size (n = 4,194,304 x 61:
+    column 0 into the digit basis, 12 blocks of 5 through the digit-basis
+    stage-1 Gram and update, k up to 56, then the all-cached stage-2 Gram and
+    the tensor-core stage-2 update), launched as the benchmark launches it,
+    against the oracle's stage 1 and stage 2 on the same input: every R entry
+    within 1e-12 of its column's norm and 4096 sampled rows of Q within 1e-12."""
+    from paper_2402_15033_gb300 import capi
+    n, s, nblk = 4194304, 5, 12
+    ncol = 1 + s * nblk
+    B0 = synth.tall_basis(n, ncol, seed=1)
+    buf = torch.tensor(B0.T.copy(), device="cuda")
+    B = buf.T
+    B[:, 0] /= torch.linalg.norm(B[:, 0])
+    capc = 64
+    Rh = torch.zeros(ncol, ncol, dtype=torch.float64, device="cuda").T
+    R2 = torch.zeros(ncol, ncol, dtype=torch.float64, device="cuda").T
+    work = torch.empty(capi.workspace_bytes(n, ncol, ncol), dtype=torch.uint8, device="cuda")
+    st = torch.zeros(nblk + 1, dtype=torch.int32, device="cuda")
+    dig = torch.empty(capi.digits_bytes(n, capc), dtype=torch.uint8, device="cuda")
+    capi.digits_fill(B[:, :1], 0, dig, capc)
+    for j in range(nblk):
+        k = 1 + s * j
+        Q, V, Rb = B[:, :k], B[:, k:k + s], Rh[:k + s, k:k + s]
+        capi.ortho_gram_chol_tcd(Q, V, Rb, work, st[j:j + 1], dig, capc, k, k=k)
+        capi.ortho_update_tcd(Q, V, Rb, st[j:j + 1], dig, capc, k=k)
+    capi.ortho_gram_chol_tcd(None, B, R2, work, st[nblk:], dig, capc, ncol, k=0)
+    capi.ortho_update(None, B, R2, st[nblk:], k=0, tc=True)
+    torch.cuda.synchronize()
+    assert int(st.abs().sum().item()) == 0
+    del dig, work
+    X = np.array(B0, copy=True)
+    X[:, 0] /= np.linalg.norm(X[:, 0])
+    Rh_ref = np.zeros((ncol, ncol))
+    for j in range(nblk):
+        k = 1 + s * j
+        Qh, P, T = bo.stage1(X[:, :k], X[:, k:k + s])
+        X[:, k:k + s] = Qh
+        Rh_ref[:k, k:k + s] = P
+        Rh_ref[k:k + s, k:k + s] = T
+    Qf, _, T2 = bo.stage2(np.zeros((n, 0)), X)
+    R2g, Rhg = R2.cpu().numpy(), Rh.cpu().numpy()
+    sc = np.linalg.norm(T2, axis=0)
+    assert np.all(np.abs(R2g - T2) <= 1e-12 * sc[None, :])
+    msk = np.triu(np.ones((ncol, ncol), bool), 1)
+    msk[:, 0] = False
+    scale = np.maximum(np.linalg.norm(Rh_ref, axis=0), 1e-300)
+    assert np.all(np.abs(Rhg - Rh_ref)[msk] <= (1e-12 * scale[None, :].repeat(ncol, 0))[msk])
+    rows = synth.rng(3).choice(n, 4096, replace=False)
+    Qs = B[torch.tensor(rows, device="cuda")].cpu().numpy()
+    assert np.max(np.abs(Qs - Qf[rows])) <= 1e-12

@@ -436,6 +436,91 @@ def test_mixed_precision_refinement_reaches_fp64_accuracy(N):
     assert i32["iters"] % 60 == 0
 
 
+def _round_f32(x):
+    """The float32 nearest to the rational x (ties to even), from the rational
+    itself: a double-rounding check guards float(x) -> float32."""
+    from fractions import Fraction
+    d = float(x)                       # correctly rounded to 53 bits
+    f = np.float32(d)
+    # the exact value must not sit within 2^-40 relative of a float32 midpoint,
+    # where rounding through the double could differ from rounding the rational
+    lo, hi = np.nextafter(f, np.float32(-np.inf)), np.nextafter(f, np.float32(np.inf))
+    for nb in (lo, hi):
+        mid = (Fraction(float(f)) + Fraction(float(nb))) / 2
+        assert mid == 0 or abs(Fraction(x) - mid) > abs(mid) * Fraction(1, 2 ** 40)
+    return float(f)
+
+
+def test_stage1_lowp_rounds_the_projected_block_and_the_result_to_fp32():
+    """The mixed-precision stage 1 (explicit projection for an FP32-stored
+    basis, the higher-precision-Gram CholQR of §II) on a tiny case, against an
+    independent exact-rational computation: W = V - Q (Q^T V) in exact
+    rationals, rounded once to float32; T = LAPACK Cholesky of the exactly
+    accumulated W^T W.  The oracle's T must agree to 1e-13 (dropping the FP32
+    rounding of W moves T by about 1e-8); its Q^ must be FP32 values (dropping
+    the final rounding leaves FP64 values) within one float32 ulp of W T^{-1}."""
+    from fractions import Fraction
+    g = synth.rng(4242)
+    n, k, nb = 9, 3, 2
+    Q = np.linalg.qr(g.standard_normal((n, k)))[0].astype(np.float32).astype(np.float64)
+    V = (g.standard_normal((n, nb)) + Q @ g.standard_normal((k, nb))).astype(np.float32).astype(np.float64)
+    Qf = [[Fraction(float(v)) for v in Q[:, c]] for c in range(k)]
+    Vf = [[Fraction(float(v)) for v in V[:, j]] for j in range(nb)]
+    Pf = [[sum(a * b for a, b in zip(Qf[c], Vf[j])) for j in range(nb)] for c in range(k)]
+    W32 = np.zeros((n, nb))
+    for j in range(nb):
+        for r in range(n):
+            w = Vf[j][r] - sum(Qf[c][r] * Pf[c][j] for c in range(k))
+            W32[r, j] = _round_f32(w)
+    Wf = [[Fraction(float(v)) for v in W32[:, j]] for j in range(nb)]
+    G = np.array([[float(sum(a * b for a, b in zip(Wf[i], Wf[j]))) for j in range(nb)] for i in range(nb)])
+    T_ref = np.linalg.cholesky(G).T
+    Qh, P, T = bo.stage1_lowp(Q, V)
+    assert np.allclose(P, np.array([[float(x) for x in row] for row in Pf]), rtol=0, atol=1e-15)
+    assert np.all(np.abs(T - T_ref) <= 1e-13 * np.abs(T_ref).max()), np.abs(T - T_ref).max()
+    # the unrounded W would have moved T by far more than that bar
+    W64 = V - Q @ (Q.T @ V)
+    T64 = np.linalg.cholesky(W64.T @ W64).T
+    assert np.abs(T64 - T_ref).max() > 1e-10 * np.abs(T_ref).max()
+    assert np.array_equal(Qh, Qh.astype(np.float32).astype(np.float64))
+    ref = np.linalg.solve(T_ref.T, W32.T).T
+    assert np.all(np.abs(Qh - ref) <= 2.0 ** -23 * np.abs(ref) + 1e-30)
+    assert np.abs(Qh - ref).max() > 0.0 or np.array_equal(ref, ref.astype(np.float32).astype(np.float64))
+
+
+def test_breakdown_reports_the_failing_pivot_and_the_pythagorean_margin():
+    """The failing pivot is the Schur complement that was not positive
+    (hand-worked: diag(4, 1, -1, 2) fails at pivot 3 with value -1; [[1, 2],
+    [2, 3]] at pivot 2 with 3 - 2^2 = -1).  BCGS-PIP's margin uses the exact
+    identity (V - Q P)^T (V - Q P) = G - P^T P + P^T (Q^T Q - I) P, checked
+    here on a non-orthonormal Q; for an orthonormal Q the error term vanishes
+    to rounding, so a rank-deficient projected block (V in span Q) has a
+    margin of rounding size, and a full-rank one never breaks down."""
+    _, info = bo.chol_upper(np.diag([4.0, 1.0, -1.0, 2.0]))
+    R, info = bo.chol_upper(np.diag([4.0, 1.0, -1.0, 2.0]))
+    assert info == 3 and bo.pivot_value(np.diag([4.0, 1.0, -1.0, 2.0]), R, info) == -1.0
+    G = np.array([[1.0, 2.0], [2.0, 3.0]])
+    R, info = bo.chol_upper(G)
+    assert info == 2 and bo.pivot_value(G, R, info) == -1.0
+    g = synth.rng(4343)
+    n, k, nb = 50, 4, 3
+    Q = g.standard_normal((n, k)) / np.sqrt(n)          # far from orthonormal
+    V = g.standard_normal((n, nb))
+    P = Q.T @ V
+    W = V - Q @ P
+    lhs = W.T @ W
+    rhs = V.T @ V - P.T @ P + P.T @ (Q.T @ Q - np.eye(k)) @ P
+    assert np.allclose(lhs, rhs, rtol=0, atol=1e-12 * np.abs(lhs).max())
+    E = P.T @ (Q.T @ Q - np.eye(k)) @ P
+    assert bo.pip_margin(Q, V, P) == pytest.approx(np.linalg.eigvalsh(lhs)[0] / np.linalg.norm(E, 2), rel=1e-12)
+    assert bo.pip_margin(np.zeros((n, 0)), V, np.zeros((0, nb))) == float("inf")
+    Qo, _ = _sign_fixed_qr(g.standard_normal((n, k)))
+    Vin = Qo @ g.standard_normal((k, nb))              # V in span(Q): rank-deficient projection
+    with pytest.raises(bo.Breakdown) as e:
+        bo.bcgs_pip(Qo, Vin)
+    assert e.value.margin < 1.0 and not (e.value.value > 0.0)
+
+
 def test_mixed_basis_keeps_fp32_orthogonality_after_stage2():
     """Stage 2 on an FP32-stored pre-processed panel: the FP64-computed Q has
     O(eps64) orthogonality before rounding and O(eps32) after (Theorem 3 with

@@ -30,9 +30,17 @@ def _to_dev(Q, V, n, k, nb):
     return (buf[:k].T if k else None), buf[k:].T
 
 
-@pytest.mark.parametrize("n,k,nb", [(100003, 26, 5), (4099, 0, 16)])
-def test_noalloc_matches_workspace_version_twice(lib, n, k, nb):
+@pytest.mark.parametrize("n,k,nb,on_stream", [(100003, 26, 5, False), (4099, 0, 16, False),
+                                               (65537, 48, 16, True)])
+def test_noalloc_matches_workspace_version_twice(lib, n, k, nb, on_stream):
+    """(65537, 48, 16) fills the array's largest layout: k + nb = 64 columns of
+    16 at the full reduction grid; it runs on a stream other than the default."""
     from paper_2402_15033_gb300 import capi
+    if on_stream:
+        side = torch.cuda.Stream()
+        stream = side.cuda_stream
+    else:
+        side, stream = None, None
     for call, seed in enumerate((31, 32)):
         Q, V = _inputs(n, k, nb, seed + n)
         Qa, Va = _to_dev(Q, V, n, k, nb)
@@ -43,7 +51,8 @@ def test_noalloc_matches_workspace_version_twice(lib, n, k, nb):
         sb = torch.full((1,), -1, dtype=torch.int32, device="cuda")
         work = torch.empty(capi.workspace_bytes(n, k, nb), dtype=torch.uint8, device="cuda")
         capi.ortho_stage1(Qa, Va, Ra, work, sa, k=k)
-        capi.ortho_stage1_noalloc(Qb, Vb, Rb, sb, k=k)
+        torch.cuda.synchronize()
+        capi.ortho_stage1_noalloc(Qb, Vb, Rb, sb, k=k, stream=stream)
         torch.cuda.synchronize()
         assert int(sa.item()) == 0 and int(sb.item()) == 0, call
         ra, rb = Ra.cpu().numpy(), Rb.cpu().numpy()
