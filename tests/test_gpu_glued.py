@@ -6,8 +6,11 @@ panel through stage 2, in the three arithmetics (FP64 pipe, exact-slice
 tensor cores, tensor cores with the digit basis).
 
 Bars, from the paper's bounds (eps = 2^-52):
-* after stage 1, ||I - Q^^T Q^|| within [0.01, 10] kappa^2 eps (Eq. 10) and
-  kappa(Q^) < 2 (Eq. 11), as the oracle's pin states for the same inputs;
+* after stage 1, ||I - Q^^T Q^|| at most 10 kappa^2 eps (Eq. 10, an upper
+  bound) and at least 1e-3 kappa^2 eps (not a bound of the paper: it shows the
+  sweep reaches the kappa^2 eps regime; the GPU's fixed-order FMA sums lose
+  somewhat less than the oracle's, about 0.008 kappa^2 eps at kappa 1.4e6),
+  and kappa(Q^) < 2 (Eq. 11);
 * after stage 2, ||I - Q^T Q|| < 100 eps (Theorem 3) and V = Q R to 1e-13;
 * R (stage 2 times stage 1) within 100 kappa eps ||R|| of the oracle's (the
   perturbation bound of a QR factor for a backward-stable method);
@@ -79,7 +82,7 @@ def test_glued_sweep_stage_bounds_on_the_gpu(lib, arith, seed):
         Qhat, Q, Rh, R2, st = gpu_two_stage(capi, V, arith)
         assert np.all(st == 0), (km, st)
         e1 = checks.orth_error(Qhat)[0]
-        assert 0.01 * kap ** 2 * EPS <= e1 <= 10 * kap ** 2 * EPS, (km, kap, e1)
+        assert 1e-3 * kap ** 2 * EPS <= e1 <= 10 * kap ** 2 * EPS, (km, kap, e1)
         assert checks.cond2(Qhat) < 2.0
         assert checks.orth_error(Q)[0] < 100 * EPS
         R = R2 @ Rh
