@@ -69,7 +69,7 @@ extern "C" {
                                       /* Pythagorean step (Eq. 5) breaks down sooner on marginal     */
                                       /* blocks; values must keep |x y| and partial sums inside the  */
                                       /* FP32 exponent range (|x| in [2^-50, 2^50] for unit-scale n) */
-#define GMRES_ARITH_TC             2  /* opt-in: Gram reductions on the bf16 tensor cores by exact    */
+#define GMRES_ARITH_TC             2  /* opt-in: Gram reductions on the f16 tensor cores by exact     */
                                       /* integer slicing (Ozaki et al.): seven 8-bit digits per      */
                                       /* value against a per-chunk column exponent, digit products    */
                                       /* summed exactly in FP32, combined in 64-bit integers; FP64    */
@@ -249,7 +249,7 @@ int ortho_update_dd(void* stream, int64_t n, const double* Q, int64_t ldq, int32
                     double* V, int64_t ldv, int32_t nb, const double* R, int32_t ldr,
                     const int32_t* d_status);
 
-/* The same two halves on the bf16 tensor cores by exact slicing
+/* The same two halves on the f16 tensor cores by exact slicing
  * (GMRES_ARITH_TC), for k + nb <= 64 (larger blocks run the FP64 kernels).
  * The update forms W = [-P T^{-1}; T^{-1}] and computes [Q, V] W. */
 int ortho_gram_chol_tc(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
@@ -266,14 +266,16 @@ int ortho_update_tc(void* stream, int64_t n, const double* Q, int64_t ldq, int32
  * projects every block against all accumulated columns, §V).  No counterpart in
  * the paper.
  *   ortho_digits_bytes: size of a digit basis of capc columns for n rows
- *                       (about 14 bytes per value); capc <= 64.
+ *                       (7 digit bytes per value plus one int32 exponent per
+ *                       64-row chunk and column); capc <= 64.
  *   ortho_digits_fill:  slice X(:, 0:nc) into digit columns c0 .. c0+nc-1.
  *   ortho_gram_chol_tcd: ortho_gram_chol_tc whose first kc columns of [Q, V]
  *                       (kc <= k + nb) are read from digit columns 0 .. kc-1,
  *                       which must hold exactly those columns' current values;
  *                       bit-identical to ortho_gram_chol_tc, except that with
- *                       kc = k and nb <= 8 a pipelined kernel (bulk copies of
- *                       the chunks' digit columns) runs and agrees to rounding.
+ *                       kc = k and nb <= 8 a streaming kernel (each warp copies
+ *                       the digit bytes of its own chunks) runs and agrees to
+ *                       rounding.
  *   ortho_update_tcd:   ortho_update_tc that also writes the digits of the new V
  *                       into digit columns k .. k+nb-1; for nb <= 8 it reads Q's
  *                       digits from digit columns 0 .. k-1 (which must hold Q)

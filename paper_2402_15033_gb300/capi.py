@@ -407,8 +407,8 @@ def ortho_update(Q, V, R, status, k=None, stream=None, dd=False, tc=False):
 
 
 def digits_bytes(n, capc):
-    """Bytes of a digit basis of capc columns for n rows: 16 per value (seven
-    bf16 digits and a spare) plus an int32 exponent per 64-row chunk and column."""
+    """Bytes of a digit basis of capc columns for n rows: 7 per value (seven
+    biased 8-bit digits) plus an int32 exponent per 64-row chunk and column."""
     return int(load().ortho_digits_bytes(int(n), int(capc)))
 
 

@@ -1,35 +1,37 @@
-// Tall-skinny Gram block [P; G] = [Q, V]^T V on the bf16 tensor cores with
+// Tall-skinny Gram block [P; G] = [Q, V]^T V on the f16 tensor cores with
 // exact integer slicing (the error-free splitting of Ozaki, Ogita, Oishi and
 // Rump, 2012): FP64 inputs, results of FP64 quality, for k + nb <= 64.
 //
-// Per 64-row chunk and column c let e_c be the largest binary exponent in the
-// chunk (|x| < 2^(e_c+1)).  Each value is truncated to the integer
-// F = trunc(|x| 2^(54 - e_c)) (< 2^55, 55 significant bits for the largest
-// entries) and written, signed like x, in balanced base 256:
-//     F = sum_{p=0..6} d_p 256^(6-p),  |d_p| <= 128,
-// so x = sum_p d_p 2^(e_c - 6 - 8p) within 2^(e_c - 54), and every digit is
-// exact in bf16.  For a column pair (i, j) the chunk's contribution is
-//     x_i^T y_j = 2^(e_i + e_j - 12) sum_{t=0..6} 2^(-8t) I_t,
+// Per 64-row chunk and column c let E_c be the largest binary exponent in the
+// chunk (|x| < 2^(E_c+1)).  Each value is truncated to the integer
+// F = trunc(|x| 2^(53 - E_c)) (< 2^54, 54 significant bits for the largest
+// entries) and written, signed like x, in balanced base 256 (tc_common.cuh):
+//     +-F = sum_{p=0..6} d_p 256^(6-p),  |d_p| <= 128,
+// so x = sum_p d_p 2^(E_c - 5 - 8p) within 2^(E_c - 53), and every digit is
+// exact in f16.  For a column pair (i, j) the chunk's contribution is
+//     x_i^T y_j = 2^(E_i + E_j - 10) sum_{t=0..6} 2^(-8t) I_t,
 //     I_t = sum_{p+q=t} sum_rows d_p d'_q,
-// and each I_t is accumulated by mma.sync m16n8k16 (bf16 inputs, FP32
+// and each I_t is accumulated by mma.sync m16n8k16 (f16 inputs, FP32
 // accumulators).  Every product is an integer of magnitude <= 2^14, and every
 // partial sum is bounded by (t+1) * 64 * 2^14 <= 7 * 2^20 < 2^24, so the FP32
 // accumulation is exact.  Pairs with p + q > 6 weigh less than 2^-51 of the
 // largest product and are not formed (28 products per output instead of 49).
 // After each chunk the seven exact sums are combined in 64-bit integers
-// (|S| < 2^61), converted to FP64 (one rounding) and added to the output, scaled
-// by 2^(e_i + e_j - 52), with one fused multiply-add.  The per-chunk error is a
+// (|S| < 2^59), converted to FP64 (one rounding) and added to the output, scaled
+// by 2^(E_i + E_j - 50), with one fused multiply-add.  The per-chunk error is a
 // few units of 2^-53 of the chunk's largest product, below the rounding error
 // of an FP64 dot product of the same rows.  Subnormal inputs count as zero; a
 // NaN or infinity in a column makes every entry of that column's row and
 // column of the block NaN, as FP64 arithmetic would.
 //
 // Two CTAs share an SM, so one slices while the other multiplies.  Within a
-// CTA, chunks arrive by asynchronous copies (cp.async) into a raw FP64 tile,
-// which is free once the chunk is sliced: the next chunk streams in during the
-// MMAs.  The slices of a column are stored as two 16-byte units per row pair
-// (digits 0-3 and 4-6), so a thread loads the seven digit words of an MMA
-// fragment position with two 128-bit shared loads, free of bank conflicts.
+// CTA, chunks arrive by asynchronous copies (cp.async) into a raw tile, which
+// is free once the chunk is sliced: the next chunk streams in during the MMAs.
+// Columns held in the digit basis arrive as their 448 digit bytes in the same
+// tile slot and are only widened.  The slices of a column are stored as two
+// 16-byte units per row pair (f16 digits 0-3 and 4-6), so a thread loads the
+// seven digit words of an MMA fragment position with two 128-bit shared
+// loads, free of bank conflicts.
 #pragma once
 #include "pip_body.cuh"
 #include "tc_common.cuh"
@@ -62,7 +64,7 @@ __host__ __device__ inline int tc_tile_count(int k, int nb) {
 // One virtual CTA's partial block of [Q(:, 0:k), V(:, 0:nb)]^T V(:, 0:nb) over
 // the 64-row chunks b, b+G, ...; entry (c, j) goes to slot[c * nb + j].  The
 // first kc columns of [Q, V] may come from a digit basis (dig, dex, capc:
-// tc_digits_store) instead of being staged and sliced.  256 threads (8 warps);
+// tc_b8_store) instead of being staged and sliced.  256 threads (8 warps);
 // k + nb <= 64; dynamic shared memory gram_tc_smem(k + nb).
 __device__ void gram_tc_part(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
                              const double* __restrict__ V, int64_t ldv, int nb, int b, int G,
@@ -102,23 +104,40 @@ __device__ void gram_tc_part(int64_t n, const double* __restrict__ Q, int64_t ld
         for (int i = 0; i < 4; ++i) out[q][i] = 0.0;
 
     const int64_t nchunks = (n + kTcRows - 1) / kTcRows;
-    if ((int64_t)b < nchunks && kc < kx) {
-        tc_stage64(Q, ldq, k, V, ldv, kx, (int64_t)b * kTcRows, n, raw, kc);
+    // the raw tile of chunk ch: FP64 rows of columns kc and up, and the 448
+    // digit bytes of each column below kc in that column's 512-byte slot
+    auto stage = [&](int64_t ch) {
+        if (kc < kx) tc_stage64(Q, ldq, k, V, ldv, kx, ch * kTcRows, n, raw, kc);
+        if (kc > 0) {
+            const uint4* src = dig + (size_t)ch * capc * kTcB8Units;
+            for (int e = threadIdx.x; e < kc * kTcB8Units; e += blockDim.x) {
+                const int c = e / kTcB8Units, u = e - c * kTcB8Units;
+                cp_async16(reinterpret_cast<uint4*>(raw + (size_t)c * kTcRows) + u, src + e, 16);
+            }
+        }
         cp_async_commit();
-    }
+    };
+    if ((int64_t)b < nchunks) stage(b);
     for (int64_t ci = b; ci < nchunks; ci += G) {
         cp_async_wait_all();
         __syncthreads();
-        // 0. columns held in the digit basis: their digit units and exponents
-        if (kc > 0) {
-            const uint4* src = dig + (size_t)ci * capc * 64;
-            for (int e = threadIdx.x; e < kc * 64; e += blockDim.x) {
-                const int c = e >> 6, u = e & 63;
-                cp_async16(sl + (size_t)(c * 2 + (u >> 5)) * kTcWp + (u & 31), src + e, 16);
-            }
-            cp_async_commit();
-            for (int c = threadIdx.x; c < kc; c += blockDim.x) ex[c] = dex[(size_t)ci * tc_dex_stride(capc) + c];
+        // 0. columns held in the digit basis: widen digit p of rows 16w + 2g,
+        //    +1 (pair 8w + g) and +8, +9 (pair 8w + g + 4) into the slice units
+        for (int e = threadIdx.x; e < kc * 16; e += blockDim.x) {
+            const int c = e >> 4, g = (e >> 2) & 3, w = e & 3;
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(raw + (size_t)c * kTcRows) + g * 4 + w;
+            uint32_t wd[kTcSlices];
+#pragma unroll
+            for (int p = 0; p < kTcSlices; ++p) wd[p] = src[p * 16];
+            uint4* u = sl + (size_t)c * 2 * kTcWp + 8 * w + g;
+            u[0] = make_uint4(tc_widen<0x4140>(wd[0]), tc_widen<0x4140>(wd[1]), tc_widen<0x4140>(wd[2]),
+                              tc_widen<0x4140>(wd[3]));
+            u[kTcWp] = make_uint4(tc_widen<0x4140>(wd[4]), tc_widen<0x4140>(wd[5]), tc_widen<0x4140>(wd[6]), 0u);
+            u[4] = make_uint4(tc_widen<0x4342>(wd[0]), tc_widen<0x4342>(wd[1]), tc_widen<0x4342>(wd[2]),
+                              tc_widen<0x4342>(wd[3]));
+            u[4 + kTcWp] = make_uint4(tc_widen<0x4342>(wd[4]), tc_widen<0x4342>(wd[5]), tc_widen<0x4342>(wd[6]), 0u);
         }
+        for (int c = threadIdx.x; c < kc; c += blockDim.x) ex[c] = dex[(size_t)ci * tc_dex_stride(capc) + c];
         // 1. per other column (one warp): exponent of the chunk maximum, then the
         //    digit slices; lane l holds rows 2l and 2l + 1
         for (int c = kc + warp; c < kx; c += 8) {
@@ -129,19 +148,12 @@ __device__ void gram_tc_part(int64_t n, const double* __restrict__ Q, int64_t ld
             const bool bad = eb == 0x7FF;          // NaN or infinity in the chunk
             if (bad || eb == 0) eb = 1023;         // all zero (or subnormal): every digit is zero
             if (lane == 0) ex[c] = bad ? kTcBadExp : eb - 1023;
-            uint32_t d0[kTcSlices], d1[kTcSlices];
-            tc_slice(v.x, eb, d0);
-            tc_slice(v.y, eb, d1);
             uint4* u = sl + (size_t)c * 2 * kTcWp + lane;
-            tc_pack(d0, d1, u[0], u[kTcWp]);
+            tc_pack(tc_slice(v.x, eb), tc_slice(v.y, eb), u[0], u[kTcWp]);
         }
-        if (kc > 0) cp_async_wait_all();
         __syncthreads();
         // the raw tile is free: the next chunk streams in during the MMAs
-        if (ci + G < nchunks && kc < kx) {
-            tc_stage64(Q, ldq, k, V, ldv, kx, (ci + G) * kTcRows, n, raw, kc);
-            cp_async_commit();
-        }
+        if (ci + G < nchunks) stage(ci + G);
         // 2. exact digit products on the tensor cores, one output tile at a time
 #pragma unroll
         for (int q = 0; q < kTcMaxTiles; ++q) {
@@ -174,7 +186,7 @@ __device__ void gram_tc_part(int64_t n, const double* __restrict__ Q, int64_t ld
                                                acc[6][i]);
                 const int ei = ex[row], ej = ex[k + col];
                 out[q][i] = max(ei, ej) == kTcBadExp ? __longlong_as_double(0x7FF8000000000000ll)
-                                                     : tc_accum(out[q][i], S, ei + ej - 52);
+                                                     : tc_accum(out[q][i], S, ei + ej - kTcShift);
             }
         }
     }

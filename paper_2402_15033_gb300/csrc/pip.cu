@@ -122,25 +122,38 @@ cudaError_t launch_gram_tc(cudaStream_t st, int64_t n, const double* Q, int64_t 
 }
 
 // Digit-basis fill: columns c0 .. c0+nc-1 of the digit basis from X(:, 0:nc).
+// One (chunk, column) item per half warp; a half warp without an item of its
+// own repeats its partner's (the same bytes to the same places) so that both
+// halves reach the exponent shuffles together.
 __global__ void __launch_bounds__(256)
 digits_fill_kernel(int64_t n, const double* __restrict__ X, int64_t ldx, int c0, int nc, uint4* dig, int* dex,
                    int capc) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int64_t nchunks = (n + 63) / 64;
-    for (int64_t e = (int64_t)blockIdx.x * nw + warp; e < nchunks * nc; e += (int64_t)gridDim.x * nw) {
+    const int hw = threadIdx.x >> 4, h = threadIdx.x & 15, nhw = blockDim.x >> 4;
+    const int w = h >> 2, g = h & 3;
+    const int64_t items = (n + 63) / 64 * nc;
+    for (int64_t base = (int64_t)blockIdx.x * nhw; base < items; base += (int64_t)gridDim.x * nhw) {
+        const int64_t e0 = base + (hw & ~1);             // the warp's first item
+        if (e0 >= items) continue;                        // warp-uniform
+        const int64_t e = base + hw < items ? base + hw : e0;
         const int64_t ch = e / nc;
         const int c = (int)(e % nc);
-        const int64_t r0 = ch * 64 + 2 * lane;
-        const double* p = X + (int64_t)c * ldx + r0;
-        double x0 = 0.0, x1 = 0.0;
-        if (r0 + 1 < n) {
-            const double2 v = __ldg(reinterpret_cast<const double2*>(p));
-            x0 = v.x;
-            x1 = v.y;
-        } else if (r0 < n) {
-            x0 = __ldg(p);
+        double x[4];
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int64_t r0 = ch * 64 + 16 * w + 2 * g + 8 * hh;
+            const double* p = X + (int64_t)c * ldx + r0;
+            x[2 * hh] = 0.0;
+            x[2 * hh + 1] = 0.0;
+            if (r0 + 1 < n) {
+                const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+                x[2 * hh] = v.x;
+                x[2 * hh + 1] = v.y;
+            } else if (r0 < n) {
+                x[2 * hh] = __ldg(p);
+            }
         }
-        tc_digits_store(x0, x1, ch, c0 + c, capc, dig, dex);
+        tc_b8_store(x, dig + ((size_t)ch * capc + c0 + c) * kTcB8Units,
+                    dex + (size_t)ch * tc_dex_stride(capc) + c0 + c);
     }
 }
 
@@ -149,7 +162,7 @@ cudaError_t launch_digits_fill(cudaStream_t st, int64_t n, const double* X, int6
     uint4* dig = static_cast<uint4*>(digits);
     int* dex = reinterpret_cast<int*>(dig + tc_digits_units(n, capc));
     const int64_t items = (n + 63) / 64 * nc;
-    const int grid = (int)std::min<int64_t>((items + 7) / 8, 8 * (int64_t)num_sms());
+    const int grid = (int)std::min<int64_t>((items + 15) / 16, 8 * (int64_t)num_sms());
     digits_fill_kernel<<<grid, 256, 0, st>>>(n, X, ldx, c0, nc, dig, dex, capc);
     return cudaGetLastError();
 }

@@ -1,19 +1,28 @@
-// Exact integer slicing of FP64 values for the bf16 tensor cores (the
+// Exact integer slicing of FP64 values for the f16 tensor cores (the
 // error-free splitting of Ozaki, Ogita, Oishi and Rump, 2012), shared by the
-// tensor-core Gram (gram_tc.cuh) and block update (update_tc.cuh).
+// tensor-core Gram (gram_tc.cuh, gram_tcq.cuh) and block update (update_tc.cuh,
+// update_tcd.cuh).
 //
 // A value x is sliced against a common biased exponent eb of its group (a
 // chunk column for the Gram, a row for the update), eb >= x's own exponent:
-// F = trunc(|x| 2^(54 - e)) (e = eb - 1023; F < 2^55) is written in balanced
-// base 256, F = sum_{p=0..6} d_p 256^(6-p) with |d_p| <= 128, signed like x, so
-// that x = sum_p d_p 2^(e - 6 - 8p) within 2^(e - 54) (55 bits for the
-// group's largest entries) and every digit is exact in bf16.  A dot product of two sliced vectors of at most
-// 64 terms is 2^(e_x + e_y - 12) sum_{t=0..6} 2^(-8t) I_t with
-// I_t = sum_{p+q=t} sum_terms d_p d'_q; every digit product is an integer of
-// magnitude <= 2^14 and every partial sum of I_t is at most (t+1) 64 2^14 < 2^24,
-// so mma.sync (bf16 inputs, FP32 accumulators) forms each I_t exactly.  Digit
-// pairs with p + q > 6 weigh less than 2^-51 of the largest product and are not
-// formed.
+// with E = eb - 1023 (so |x| < 2^(E+1) for the group's largest entries),
+// F = trunc(|x| 2^(53 - E)) < 2^54 keeps 54 significant bits of the largest
+// entries (53 of FP64 plus one).  The signed integer Fs = +-F is written in
+// balanced base 256,
+//     Fs = sum_{p=0..6} d_p 256^(6-p),  d_p in [-128, 127] for p >= 1,  |d_0| <= 64,
+// so that x = 2^(E-5) sum_p d_p 2^(-8p) within 2^(E-53), and every digit is an
+// integer exact in f16.  The digits come out of one 64-bit addition: the low
+// seven bytes of G = Fs + 0x0080808080808080 are d_p + 128 (byte 6 - p holds
+// digit p), each a biased byte in [0, 255]; a byte b becomes the f16 value
+// b - 128 by placing it under the f16 exponent of 1024 (bits 0x6400 | b, the
+// value 1024 + b exactly) and subtracting 1152 (exact).
+//
+// A dot product of two sliced vectors of at most 64 terms is
+//     2^(E_x + E_y - 10) sum_{t=0..6} 2^(-8t) I_t,   I_t = sum_{p+q=t} sum_terms d_p d'_q;
+// every digit product is an integer of magnitude <= 2^14 and every partial
+// sum of I_t is at most (t+1) 64 2^14 < 2^24, so mma.sync (f16 inputs, FP32
+// accumulators) forms each I_t exactly.  Digit pairs with p + q > 6 weigh less
+// than 2^-51 of the largest product and are not formed.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -23,11 +32,14 @@ namespace gm {
 constexpr int kTcSlices = 7;                  // balanced base-256 digits
 constexpr int kTcWp = 34;                     // 16-byte units per (column, digit half): 32 pairs + 2 pad
 constexpr int kTcBadExp = 1 << 20;            // exponent marking a NaN or infinity in the group
+constexpr int kTcShift = 50;                  // x_i x_j = S 2^(E_i + E_j - kTcShift), S from tc_combine
+constexpr uint32_t kTcF16Hi = 0x64646464u;    // f16 exponent byte of 1024, for the widening permutes
+constexpr uint32_t kTcF16Bias = 0x64806480u;  // f16x2 (1152, 1152)
 
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                               uint32_t b0, uint32_t b1) {
+__device__ __forceinline__ void mma_f16_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                              uint32_t b0, uint32_t b1) {
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};\n"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
@@ -36,35 +48,34 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], uint32_t a0, uint3
 // Biased FP64 exponent field of x.
 __device__ __forceinline__ int tc_bexp(double x) { return (__double2hiint(x) >> 20) & 0x7FF; }
 
-// The seven digits of x against the group's biased exponent eb (>= x's own),
-// as FP32 bit patterns whose high halves are the bf16 digits: F =
-// trunc(|x| 2^(54 - e)) (e = eb - 1023; zero and subnormals give 0) is shifted
-// into place with two 32-bit funnel shifts, 128 is added at every lower digit
-// position (each byte of the sum is then the balanced digit plus 128, the
-// carries included), and a byte b becomes the float +-(b - 128) by one byte
-// permute into the signed constant +-1.5 * 2^23 and one exact addition.
-__device__ __forceinline__ void tc_slice(double x, int eb, uint32_t (&dig)[kTcSlices]) {
+// The seven biased digit bytes of x against the group's biased exponent eb
+// (>= x's own): G = Fs + 0x0080808080808080 (low word .x: digits 6, 5, 4, 3 in
+// bytes 0-3; high word .y: digits 2, 1, 0 in bytes 0-2, byte 3 zero).  Zero
+// and subnormal inputs give Fs = 0.  F = (2m) >> (eb - e) for the 53-bit
+// significand m, by two 32-bit funnel shifts.
+__device__ __forceinline__ uint2 tc_slice(double x, int eb) {
     const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
     const int e = (int)(hi >> 20) & 0x7FF;
     const uint32_t mh = e ? ((hi & 0xFFFFFu) | 0x100000u) : 0u;
     const uint32_t ml = e ? lo : 0u;
     const int d = min(eb - e, 63);
-    const uint32_t h = (mh << 2) | (ml >> 30), l = ml << 2;          // the mantissa times 4 (55 bits)
+    const uint32_t h = (mh << 1) | (ml >> 31), l = ml << 1;          // twice the significand (54 bits)
     const uint32_t fl = __funnelshift_rc(l, h, d) >> max(d - 32, 0);
     const uint32_t fh = __funnelshift_rc(h, 0u, d);
-    const unsigned long long G = (((unsigned long long)fh << 32) | fl) + 0x808080808080ull;
-    const uint32_t gl = (uint32_t)G, gh = (uint32_t)(G >> 32);
-    const bool neg = (hi >> 31) != 0;
-    const uint32_t magic = neg ? 0xCB400000u : 0x4B400000u;
-    const float off = neg ? 12583040.0f : -12583040.0f;
-    const float off0 = neg ? 12582912.0f : -12582912.0f;
-    dig[6] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(gl, magic, 0x7650)), off));
-    dig[5] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(gl, magic, 0x7651)), off));
-    dig[4] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(gl, magic, 0x7652)), off));
-    dig[3] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(gl, magic, 0x7653)), off));
-    dig[2] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(gh, magic, 0x7650)), off));
-    dig[1] = __float_as_uint(__fadd_rn(__uint_as_float(__byte_perm(gh, magic, 0x7651)), off));
-    dig[0] = __float_as_uint(__fadd_rn(__uint_as_float(magic + (gh >> 16)), off0));
+    unsigned long long F = ((unsigned long long)fh << 32) | fl;
+    if (hi >> 31) F = 0ull - F;
+    const unsigned long long G = F + 0x0080808080808080ull;
+    return make_uint2((uint32_t)G, (uint32_t)(G >> 32));
+}
+
+// f16x2 digits from a word of biased bytes [b0, b1, b2, b3]: (b0, b1) with
+// SEL = 0x4140, (b2, b3) with SEL = 0x4342.
+template <uint32_t SEL>
+__device__ __forceinline__ uint32_t tc_widen(uint32_t w) {
+    const uint32_t t = __byte_perm(w, kTcF16Hi, SEL);
+    uint32_t r;
+    asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(r) : "r"(t), "r"(kTcF16Bias));
+    return r;
 }
 
 __device__ __forceinline__ double tc_pow2(int e) {   // e in [-1022, 1023]
@@ -73,7 +84,7 @@ __device__ __forceinline__ double tc_pow2(int e) {   // e in [-1022, 1023]
 
 // S = sum_t I_t 2^(8(5-t)) for t <= 4, plus I_5 + I_6 / 256 rounded (0.75 units
 // at most: the tail weighs 2^-40 of I_0 and the fold is one FP32 rounding),
-// from the seven exact accumulators; |S| < 2^61 for sums of at most 64 terms.
+// from the seven exact accumulators; |S| < 2^59 for sums of at most 64 terms.
 __device__ __forceinline__ long long tc_combine(float a0, float a1, float a2, float a3, float a4, float a5, float a6) {
     const long long hi = (long long)__float2int_rn(a0) * 65536 + (long long)__float2int_rn(a1) * 256 +
                          __float2int_rn(a2);
@@ -122,14 +133,16 @@ __device__ __forceinline__ double tc_accum(double acc, long long S, int s) {
     return acc + tc_int_to_double(S, s);
 }
 
-// Two rows' (or two K terms') digits packed as one bf16x2 word per digit, in
-// the two 16-byte units (digits 0-3 and 4-6) of a (column, pair) slot.
-__device__ __forceinline__ void tc_pack(const uint32_t (&d0)[kTcSlices], const uint32_t (&d1)[kTcSlices],
-                                        uint4& lo, uint4& hi) {
-    lo = make_uint4(__byte_perm(d0[0], d1[0], 0x7632), __byte_perm(d0[1], d1[1], 0x7632),
-                    __byte_perm(d0[2], d1[2], 0x7632), __byte_perm(d0[3], d1[3], 0x7632));
-    hi = make_uint4(__byte_perm(d0[4], d1[4], 0x7632), __byte_perm(d0[5], d1[5], 0x7632),
-                    __byte_perm(d0[6], d1[6], 0x7632), 0u);
+// Two rows' (or two K terms') digits as one f16x2 word per digit, in the two
+// 16-byte units (digits 0-3 and 4-6) of a (column, pair) slot of the shared
+// memory tiles: word p = (digit p of a, digit p of b).
+__device__ __forceinline__ void tc_pack(uint2 a, uint2 b, uint4& lo, uint4& hi) {
+    const uint32_t l01 = __byte_perm(a.x, b.x, 0x5140);   // bytes 0, 1 of a and b: digits 6, 5
+    const uint32_t l23 = __byte_perm(a.x, b.x, 0x7362);   // bytes 2, 3: digits 4, 3
+    const uint32_t h01 = __byte_perm(a.y, b.y, 0x5140);   // bytes 4, 5: digits 2, 1
+    const uint32_t h23 = __byte_perm(a.y, b.y, 0x7362);   // byte 6: digit 0
+    lo = make_uint4(tc_widen<0x4140>(h23), tc_widen<0x4342>(h01), tc_widen<0x4140>(h01), tc_widen<0x4342>(l23));
+    hi = make_uint4(tc_widen<0x4140>(l23), tc_widen<0x4342>(l01), tc_widen<0x4140>(l01), 0u);
 }
 
 // The 28 digit-pair MMAs of one k-step: A (16 x 16) and B (16 x 8) fragments of
@@ -149,7 +162,7 @@ __device__ __forceinline__ void tc_mma_step(float (&acc)[kTcSlices][4], const ui
     for (int p = 0; p < kTcSlices; ++p)
 #pragma unroll
         for (int r = 0; r < kTcSlices - p; ++r)
-            mma_bf16_16816(acc[p + r], A[p][0], A[p][1], A[p][2], A[p][3], B[r][0], B[r][1]);
+            mma_f16_16816(acc[p + r], A[p][0], A[p][1], A[p][2], A[p][3], B[r][0], B[r][1]);
 }
 
 // Asynchronous copies of a 64-row chunk of [Q(:, 0:k), V(:, 0:kx-k)] (columns
@@ -174,41 +187,63 @@ __device__ __forceinline__ void tc_stage64(const double* Q, int64_t ldq, int k, 
                      "l"(bytes ? p : V), "r"(bytes) : "memory");
 }
 
-// ---- digit basis: the seven digit slices of basis columns, kept in HBM so that
-// a column is sliced once however often it is read.  For 64-row chunk ch and
-// column c, units [(ch * capc + c) * 64, +64) hold the 32 row pairs' digits
-// 0-3 (units 0-31) and 4-6 (units 32-63) in the shared-memory unit format of the
-// Gram kernel (without its padding), and exps[ch * tc_dex_stride(capc) + c] the
-// chunk column's unbiased exponent (kTcBadExp for a NaN or infinity).  The
-// exponents follow the units in one buffer; a chunk's row of exponents starts
-// on a 16-byte boundary, so that one bulk copy can fetch it.
+// ---- digit basis: the seven biased digit bytes of basis columns, kept in HBM
+// so that a column is sliced once however often it is read (7 bytes per value
+// against FP64's 8).  For 64-row chunk ch and column c the 448 bytes at unit
+// (ch * capc + c) * kTcB8Units are 28 units of 16 bytes: unit 4p + g (digit p,
+// row group g = 0..3) holds, in its word w = 0..3, the biased digit p of rows
+// 16w + 2g, +1, +8, +9 as bytes 0-3: exactly the rows that lane (., g) of an
+// mma.sync fragment reads in k-step w, so a Gram lane widens each byte once
+// and the update lane takes rows r, r+8 of two columns with one permute.
+// exps[ch * tc_dex_stride(capc) + c] holds the chunk column's unbiased exponent
+// E (kTcBadExp for a NaN or infinity).  The exponents follow the units in one
+// buffer; a chunk's row of exponents starts on a 16-byte boundary.
+constexpr int kTcB8Units = 28;                // 16-byte units per (chunk, column)
+constexpr int kTcB8Bytes = kTcB8Units * 16;   // 448
+
 __host__ __device__ inline size_t tc_digits_units(int64_t n, int capc) {
-    return (size_t)((n + 63) / 64) * (size_t)capc * 64;
+    return (size_t)((n + 63) / 64) * (size_t)capc * kTcB8Units;
 }
 __host__ __device__ inline int tc_dex_stride(int capc) { return (capc + 3) & ~3; }
 __host__ __device__ inline size_t tc_digits_bytes(int64_t n, int capc) {
     return tc_digits_units(n, capc) * 16 + (size_t)((n + 63) / 64) * (size_t)tc_dex_stride(capc) * sizeof(int) + 256;
 }
 
-// Slice column c of a 64-row chunk (lane l holds rows 2l, 2l+1: x0, x1) into
-// the digit basis; one warp.
-__device__ __forceinline__ void tc_digits_store(double x0, double x1, int64_t ch, int c, int capc, uint4* units,
-                                                int* exps) {
-    const int lane = threadIdx.x & 31;
-    int eb = max(tc_bexp(x0), tc_bexp(x1));
+// The digit-basis word of digit p for the four rows r, r+1, r+8, r+9 from
+// their slices: bytes [a_p, b_p, c_p, d_p].
+template <int P>
+__device__ __forceinline__ uint32_t tc_b8_word(uint2 a, uint2 b, uint2 c, uint2 d) {
+    constexpr int byte = 6 - P;                       // byte of G that holds digit P
+    constexpr int bb = byte & 3;                      // its byte within the low or high word
+    constexpr uint32_t sel = (uint32_t)(bb | ((bb + 4) << 4));   // [x.bb, y.bb, ., .]
+    const uint32_t ab = byte < 4 ? __byte_perm(a.x, b.x, sel) : __byte_perm(a.y, b.y, sel);
+    const uint32_t cd = byte < 4 ? __byte_perm(c.x, d.x, sel) : __byte_perm(c.y, d.y, sel);
+    return __byte_perm(ab, cd, 0x5410);
+}
+
+// Slice and store the digits of one chunk column per half warp: called by all
+// 32 lanes of a warp (each half warp its own column), lane h = 4w + g of the
+// half holding rows 16w + 2g, +1, +8, +9 (x[0..3]; zeros past n).  The
+// column's exponent is the largest of its 64 rows.  units points at the
+// column's 28 units, *ex at its exponent.
+__device__ __forceinline__ void tc_b8_store(const double (&x)[4], uint4* units, int* ex) {
+    const int h = threadIdx.x & 15;
+    const int w = h >> 2, g = h & 3;
+    int eb = max(max(tc_bexp(x[0]), tc_bexp(x[1])), max(tc_bexp(x[2]), tc_bexp(x[3])));
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, off));
+    for (int off = 8; off > 0; off >>= 1) eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, off));
     const bool bad = eb == 0x7FF;
     if (bad || eb == 0) eb = 1023;
-    uint32_t d0[kTcSlices], d1[kTcSlices];
-    tc_slice(x0, eb, d0);
-    tc_slice(x1, eb, d1);
-    uint4 lo, hi;
-    tc_pack(d0, d1, lo, hi);
-    uint4* u = units + ((size_t)ch * capc + c) * 64;
-    u[lane] = lo;
-    u[32 + lane] = hi;
-    if (lane == 0) exps[(size_t)ch * tc_dex_stride(capc) + c] = bad ? kTcBadExp : eb - 1023;
+    const uint2 s0 = tc_slice(x[0], eb), s1 = tc_slice(x[1], eb), s2 = tc_slice(x[2], eb), s3 = tc_slice(x[3], eb);
+    uint32_t* u = reinterpret_cast<uint32_t*>(units) + g * 4 + w;   // unit 4p + g, word w
+    u[0 * 16] = tc_b8_word<0>(s0, s1, s2, s3);
+    u[1 * 16] = tc_b8_word<1>(s0, s1, s2, s3);
+    u[2 * 16] = tc_b8_word<2>(s0, s1, s2, s3);
+    u[3 * 16] = tc_b8_word<3>(s0, s1, s2, s3);
+    u[4 * 16] = tc_b8_word<4>(s0, s1, s2, s3);
+    u[5 * 16] = tc_b8_word<5>(s0, s1, s2, s3);
+    u[6 * 16] = tc_b8_word<6>(s0, s1, s2, s3);
+    if (h == 0) *ex = bad ? kTcBadExp : eb - 1023;
 }
 
 }  // namespace gm

@@ -1,12 +1,12 @@
-// Block update of BCGS-PIP (§IV-C, Fig. 4a, last step) on the bf16 tensor
+// Block update of BCGS-PIP (§IV-C, Fig. 4a, last step) on the f16 tensor
 // cores by exact slicing (tc_common.cuh):
 //     V <- (V - Q P) T^{-1} = [Q, V] W,   W = [-P T^{-1}; T^{-1}]   (kx = k + nb <= 64).
 // Every CTA forms W in FP64 from R (T^{-1} by substitution), slices its columns
 // once, and then streams 64-row chunks of X = [Q, V]: each row is sliced against
 // its own largest exponent (the output of a row is a dot product along that
 // row), the digit products run on the tensor cores with FP32 accumulators that
-// stay exact, and every output is S * 2^(e_row + f_col - 52) rounded once to
-// FP64.
+// stay exact, and every output is S * 2^(e_row + f_col - 50) rounded once to
+// FP64 (the scaling of tc_common.cuh).
 //
 // Equilibration: a row mixes Q entries (unit columns) with V entries whose
 // column norms ||V_j|| = ||R(:, j)|| can be far from one; slicing such a row
@@ -129,11 +129,8 @@ __device__ void update_tc_body(int64_t n, const double* __restrict__ Q, int64_t 
         const bool bad = eb == 0x7FF;
         if (bad || eb == 0) eb = 1023;
         if (lane == 0) fexp[j] = bad ? kTcBadExp : eb - 1023;
-        uint32_t d0[kTcSlices], d1[kTcSlices];
-        tc_slice(w0, eb, d0);
-        tc_slice(w1, eb, d1);
         uint4* u = wu + (size_t)j * 2 * kTcWp + lane;
-        tc_pack(d0, d1, u[0], u[kTcWp]);
+        tc_pack(tc_slice(w0, eb), tc_slice(w1, eb), u[0], u[kTcWp]);
     }
     __syncthreads();
 
@@ -183,10 +180,8 @@ __device__ void update_tc_body(int64_t n, const double* __restrict__ Q, int64_t 
             const int c0 = 2 * w, c1 = 2 * w + 1;
             const double x0 = c0 < kx ? raw[c0 * kTuRows + r] : 0.0;
             const double x1 = c1 < kx ? raw[c1 * kTuRows + r] : 0.0;
-            uint32_t d0[kTcSlices], d1[kTcSlices];
-            tc_slice(x0, eb + cshift[min(c0, kx - 1)], d0);
-            tc_slice(x1, eb + cshift[min(c1, kx - 1)], d1);
-            tc_pack(d0, d1, xu[tu_xunit(r, 0, w)], xu[tu_xunit(r, 1, w)]);
+            tc_pack(tc_slice(x0, eb + cshift[min(c0, kx - 1)]), tc_slice(x1, eb + cshift[min(c1, kx - 1)]),
+                    xu[tu_xunit(r, 0, w)], xu[tu_xunit(r, 1, w)]);
         }
         __syncthreads();
         // the raw tile is free: the next chunk streams in during the MMAs
@@ -226,23 +221,39 @@ __device__ void update_tc_body(int64_t n, const double* __restrict__ Q, int64_t 
                                                acc[6][i]);
                 const int er = rexp[ro], fj = fexp[j];
                 const double v = max(er, fj) == kTcBadExp ? __longlong_as_double(0x7FF8000000000000ll)
-                                                          : tc_int_to_double(S, er + fj - 52);
+                                                          : tc_int_to_double(S, er + fj - kTcShift);
                 if (DIG) otile[j * kTuRows + ro] = v;
                 else V[(size_t)j * ldv + row0 + ro] = v;
             }
         }
         if (DIG) {
-            // digit-basis copy of the new columns: one warp per column, lane l
-            // holds rows 2l, 2l + 1; the FP64 rows go out in pairs
+            // the new columns in FP64 and in the digit basis: half warp per
+            // column, lane h = 4w + g of the half holds rows 16w + 2g, +1, +8, +9
             __syncthreads();
-            for (int j = warp; j < nb; j += NW) {
-                const int64_t r0 = row0 + 2 * lane;
-                const double x0 = r0 < n ? otile[j * kTuRows + 2 * lane] : 0.0;
-                const double x1 = r0 + 1 < n ? otile[j * kTuRows + 2 * lane + 1] : 0.0;
-                double* dst = V + (size_t)j * ldv + r0;
-                if (r0 + 1 < n) *reinterpret_cast<double2*>(dst) = make_double2(x0, x1);
-                else if (r0 < n) *dst = x0;
-                tc_digits_store(x0, x1, ci, k + j, capc, dig, dex);
+            const int h = lane & 15, w = h >> 2, g = h & 3;
+            for (int j0 = 2 * warp; j0 < nb; j0 += 2 * NW) {
+                const int j = j0 + (lane >> 4);
+                const bool col = j < nb;
+                const int jj = col ? j : j0;
+                double x[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int rr = 16 * w + 2 * g + (q & 1) + 8 * (q >> 1);
+                    x[q] = row0 + rr < n ? otile[jj * kTuRows + rr] : 0.0;
+                }
+                if (col) {
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int64_t r0 = row0 + 16 * w + 2 * g + 8 * hh;
+                        double* dst = V + (size_t)j * ldv + r0;
+                        if (r0 + 1 < n) *reinterpret_cast<double2*>(dst) = make_double2(x[2 * hh], x[2 * hh + 1]);
+                        else if (r0 < n) *dst = x[2 * hh];
+                    }
+                }
+                uint4* units = dig + ((size_t)ci * capc + k + jj) * kTcB8Units;
+                int* ex = dex + (size_t)ci * tc_dex_stride(capc) + k + jj;
+                // a half warp past nb repeats column j0's digits (same values, same bytes)
+                tc_b8_store(x, units, ex);
             }
         }
     }

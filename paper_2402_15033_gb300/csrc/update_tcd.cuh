@@ -1,23 +1,27 @@
 // Narrow block update (nb <= 8) of BCGS-PIP (§IV-C, Fig. 4a, last step) on the
-// bf16 tensor cores from the digit basis:
+// f16 tensor cores from the digit basis:
 //     V <- (V - Q P) T^{-1} = [Q, V] W,   W = [-P T^{-1}; T^{-1}]   (k + nb <= 64).
 // The update of the slicing kernel (update_tc.cuh) slices every row of [Q, V]
 // against the row's largest exponent; here Q's columns are not sliced at all:
-// their digits come from the digit basis, sliced per 64-row chunk against each
-// column's own exponent e_c.  Writing X = X' D with D = diag(2^(e_c)) for the
-// chunk, X W = X' (D W): the chunk's W'' = D W (k + nb values per output
+// their digit bytes come from the digit basis, sliced per 64-row chunk against
+// each column's own exponent E_c.  Writing X = X' D with D = diag(2^(E_c)) for
+// the chunk, X W = X' (D W): the chunk's W'' = D W (k + nb values per output
 // column, exact power-of-two scalings of W) is sliced per output column, and
-// every digit product then carries the same scale 2^(f_j - 12), f_j the
-// largest exponent of W'' column j, so the seven FP32 accumulators stay exact
-// and the output is S * 2^(f_j - 52) rounded once to FP64 (tc_common.cuh).
-// The new block's V columns are sliced per chunk here like Q's in the digit
-// basis, and the updated columns' digits are written back to the digit basis,
-// so the next block reads them without slicing.
+// every digit product then carries the same scale, so the seven FP32
+// accumulators stay exact and the output is S * 2^(f_j - 50) rounded once to
+// FP64 (tc_common.cuh), f_j the largest exponent of W'' column j.  The new
+// block's V columns are sliced per chunk here like Q's in the digit basis, and
+// the updated columns' digits are written back to the digit basis, so the
+// next block reads them without slicing.
 //
-// Work per 64-row chunk: copy Q's digit units, slice nb columns of V and nb
-// columns of W'', 4 M-tiles x (k-steps over k + nb) MMAs shared by warp pairs
-// (the pair splits the k-steps and adds its exact integer sums), the outputs
-// staged in shared memory and written out with their digits.
+// Work per 64-row chunk: copy Q's digit bytes (448 per column, the layout of
+// the digit basis, columns 464 bytes apart in shared memory), slice nb
+// columns of V into the same layout and nb columns of W'' into f16 B
+// fragments, 4 M-tiles x (k-steps over k + nb) MMAs shared by warp pairs (the
+// pair splits the k-steps and adds its exact integer sums), the outputs staged
+// in shared memory and written out with their digits.  An A fragment takes
+// rows r and r + 8 of two K columns from one digit word of each column (one
+// byte permute), then widens them (two permutes and two f16x2 subtractions).
 #pragma once
 #include "pip_body.cuh"
 #include "tc_common.cuh"
@@ -26,16 +30,16 @@ namespace gm {
 
 constexpr int kUdRows = 64;                   // rows per chunk (= the digit basis chunk)
 constexpr int kUdMaxNB = 8;
-constexpr int kUdXs = 69;                     // units per column of X's digits in shared memory (64 + 5 pad)
+constexpr int kUdXw = 116;                    // words per column of X's digit bytes in shared memory (112 + 4 pad)
 
 __host__ __device__ constexpr size_t update_tcd_smem(int kx, int nb) {
-    return (size_t)64 * kUdXs * 16                          // X digit units (columns >= kx stay zero)
-           + (size_t)kUdMaxNB * 2 * kTcWp * 16              // W'' digit units
+    return (size_t)64 * kUdXw * 4                           // X digit bytes (columns past kx: zero digits)
+           + (size_t)kUdMaxNB * 2 * kTcWp * 16              // W'' f16 units
            + (size_t)nb * kUdRows * sizeof(double)          // raw V chunk
            + (size_t)kx * nb * sizeof(double)               // W (FP64)
            + (size_t)nb * kUdRows * sizeof(double)          // output tile
            + (size_t)4 * 4 * 32 * sizeof(long long)         // the warp pairs' integer sums
-           + (64 + kUdMaxNB) * sizeof(int);                 // e_c, f_j
+           + (64 + kUdMaxNB) * sizeof(int);                 // E_c, f_j
 }
 
 // Q(:, 0:k) digits from the digit basis (dig, dex, capc), V(:, 0:nb) raw; the
@@ -47,8 +51,8 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int gid = lane >> 2, tig = lane & 3;
     const int nks = (kx + 15) / 16;
-    uint4* xu = reinterpret_cast<uint4*>(smem);                                  // [64][kUdXs]
-    uint4* wu = xu + 64 * kUdXs;                                                 // [8][2][kTcWp]
+    uint32_t* xw = reinterpret_cast<uint32_t*>(smem);                            // [64][kUdXw] digit words
+    uint4* wu = reinterpret_cast<uint4*>(xw + 64 * kUdXw);                       // [8][2][kTcWp]
     double* raw = reinterpret_cast<double*>(wu + kUdMaxNB * 2 * kTcWp);          // [nb][64]
     double* W = raw + nb * kUdRows;                                              // [nb][kx]  (W[c + j kx])
     double* otile = W + kx * nb;                                                 // [nb][64]
@@ -58,7 +62,7 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
 
     // ---- W = [-P T^{-1}; T^{-1}] in FP64 (T^{-1} by substitution; the X region is scratch)
     {
-        double* Ts = reinterpret_cast<double*>(xu);
+        double* Ts = reinterpret_cast<double*>(xw);
         double* Ti = Ts + nb * nb;
         double* Dinv = Ti + nb * nb;
         const bool notrsm = (mode & kPipNoTrsm) != 0;
@@ -93,7 +97,8 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
         }
         __syncthreads();
     }
-    for (int e = tid; e < 64 * kUdXs; e += blockDim.x) xu[e] = make_uint4(0u, 0u, 0u, 0u);
+    // columns past kx read by the last k-step hold zero digits (biased 0x80)
+    for (int e = tid; e < 64 * kUdXw; e += blockDim.x) xw[e] = 0x80808080u;
     for (int e = tid; e < kUdMaxNB * 2 * kTcWp; e += blockDim.x) wu[e] = make_uint4(0u, 0u, 0u, 0u);
 
     // warp pair (tile t = warp / 2: rows 16t .. 16t+15) splits the k-steps
@@ -101,8 +106,10 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
     const int kmid = (nks + 1) / 2;
     const int ks0 = khalf ? kmid : 0, ks1 = khalf ? nks : kmid;
     const int m0 = 16 * t;
-    const uint32_t sel = (gid & 1) ? 0x7632u : 0x5410u;   // this thread's row within its row pair
-    const int rp0 = (m0 + gid) >> 1, rp1 = rp0 + 4;        // row pairs of rows m0+gid and m0+gid+8
+    // rows m0 + gid and + 8 are bytes (gid & 1) and 2 + (gid & 1) of word t of unit
+    // 4p + gid / 2; one permute takes them from columns c and c + 1
+    const uint32_t sel = (gid & 1) ? 0x7351u : 0x6240u;
+    const int uoff = (gid >> 1) * 4 + t;                   // word of digit 0 within a column
 
     const int64_t nchunks = (n + kUdRows - 1) / kUdRows;
     // raw V: rows 2(tid % 32), +1 of columns tid / 32 (one column per warp)
@@ -115,11 +122,14 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
         }
         cp_async_commit();
     };
-    // Q's digit units and exponents of chunk ch from the digit basis (issued a
-    // chunk ahead, as soon as the previous chunk's MMAs are done with xu)
+    // Q's digit bytes and exponents of chunk ch from the digit basis (issued a
+    // chunk ahead, as soon as the previous chunk's MMAs are done with xw)
     auto stage_q = [&](int64_t ch) {
-        const uint4* src = dig + (size_t)ch * capc * 64;
-        for (int e = tid; e < k * 64; e += blockDim.x) cp_async16(xu + (e >> 6) * kUdXs + (e & 63), src + e, 16);
+        const uint4* src = dig + (size_t)ch * capc * kTcB8Units;
+        for (int e = tid; e < k * kTcB8Units; e += blockDim.x) {
+            const int c = e / kTcB8Units, u = e - c * kTcB8Units;
+            cp_async16(xw + c * kUdXw + 4 * u, src + e, 16);
+        }
         cp_async_commit();
         for (int c = tid; c < k; c += blockDim.x) ec[c] = dex[(size_t)ch * tc_dex_stride(capc) + c];
     };
@@ -128,24 +138,18 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
         stage_v(b);
         stage_q(b);
     }
+    const int h = lane & 15, hw_w = h >> 2, hw_g = h & 3;   // half-warp roles (rows 16w + 2g, +1, +8, +9)
     for (int64_t ci = b; ci < nchunks; ci += G) {
         const int64_t row0 = ci * kUdRows;
         cp_async_wait_all();
         __syncthreads();
-        // 1. V's columns sliced next to Q's digit units (already landed)
-        if (warp < nb) {
-            const int c = k + warp;
-            const double x0 = raw[warp * kUdRows + 2 * lane], x1 = raw[warp * kUdRows + 2 * lane + 1];
-            int eb = max(tc_bexp(x0), tc_bexp(x1));
+        // 1. V's columns sliced into digit bytes next to Q's (half warp per column)
+        for (int j0 = 2 * warp; j0 < nb; j0 += 16) {
+            const int jj = j0 + (lane >> 4) < nb ? j0 + (lane >> 4) : j0;
+            double x[4];
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, off));
-            const bool bad = eb == 0x7FF;
-            if (bad || eb == 0) eb = 1023;
-            if (lane == 0) ec[c] = bad ? kTcBadExp : eb - 1023;
-            uint32_t d0[kTcSlices], d1[kTcSlices];
-            tc_slice(x0, eb, d0);
-            tc_slice(x1, eb, d1);
-            tc_pack(d0, d1, xu[c * kUdXs + lane], xu[c * kUdXs + 32 + lane]);
+            for (int q = 0; q < 4; ++q) x[q] = raw[jj * kUdRows + 16 * hw_w + 2 * hw_g + (q & 1) + 8 * (q >> 1)];
+            tc_b8_store(x, reinterpret_cast<uint4*>(xw + (k + jj) * kUdXw), ec + k + jj);
         }
         __syncthreads();
         // the raw tile is free: the next chunk's V streams in
@@ -168,14 +172,12 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
             }
             if (f == -100000) f = 1023;
             if (lane == 0) fj[j] = bad ? kTcBadExp : f - 1023;
-            uint32_t d0[kTcSlices], d1[kTcSlices];
-            tc_slice(e0 == kTcBadExp ? 0.0 : w0, f - e0, d0);
-            tc_slice(e1 == kTcBadExp ? 0.0 : w1, f - e1, d1);
-            tc_pack(d0, d1, wu[(j * 2) * kTcWp + lane], wu[(j * 2 + 1) * kTcWp + lane]);
+            tc_pack(tc_slice(e0 == kTcBadExp ? 0.0 : w0, f - e0), tc_slice(e1 == kTcBadExp ? 0.0 : w1, f - e1),
+                    wu[(j * 2) * kTcWp + lane], wu[(j * 2 + 1) * kTcWp + lane]);
         }
         __syncthreads();
-        // 3. MMAs of tile t over this warp's k-steps: A = X (rows x K columns) built
-        //    from the column-major digit units by one byte permute per word
+        // 3. MMAs of tile t over this warp's k-steps: A = X (rows x K columns) from
+        //    the column-major digit bytes, B = W''
         float acc[kTcSlices][4];
 #pragma unroll
         for (int q = 0; q < kTcSlices; ++q)
@@ -184,37 +186,21 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
 #pragma unroll 1
         for (int ks = ks0; ks < ks1; ++ks) {
             const int ca = 16 * ks + 2 * tig;     // K columns ca, ca+1 (a0, a1) and ca+8, ca+9 (a2, a3)
-            uint32_t A[kTcSlices][4];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint4 u00 = xu[ca * kUdXs + h * 32 + rp0], u01 = xu[(ca + 1) * kUdXs + h * 32 + rp0];
-                const uint4 u10 = xu[ca * kUdXs + h * 32 + rp1], u11 = xu[(ca + 1) * kUdXs + h * 32 + rp1];
-                const uint4 u20 = xu[(ca + 8) * kUdXs + h * 32 + rp0], u21 = xu[(ca + 9) * kUdXs + h * 32 + rp0];
-                const uint4 u30 = xu[(ca + 8) * kUdXs + h * 32 + rp1], u31 = xu[(ca + 9) * kUdXs + h * 32 + rp1];
-                const uint32_t s00[4] = {u00.x, u00.y, u00.z, u00.w}, s01[4] = {u01.x, u01.y, u01.z, u01.w};
-                const uint32_t s10[4] = {u10.x, u10.y, u10.z, u10.w}, s11[4] = {u11.x, u11.y, u11.z, u11.w};
-                const uint32_t s20[4] = {u20.x, u20.y, u20.z, u20.w}, s21[4] = {u21.x, u21.y, u21.z, u21.w};
-                const uint32_t s30[4] = {u30.x, u30.y, u30.z, u30.w}, s31[4] = {u31.x, u31.y, u31.z, u31.w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int p = h * 4 + q;
-                    if (p < kTcSlices) {
-                        A[p][0] = __byte_perm(s00[q], s01[q], sel);
-                        A[p][1] = __byte_perm(s10[q], s11[q], sel);
-                        A[p][2] = __byte_perm(s20[q], s21[q], sel);
-                        A[p][3] = __byte_perm(s30[q], s31[q], sel);
-                    }
-                }
-            }
+            const uint32_t* x0 = xw + ca * kUdXw + uoff;
             const uint4* pb = wu + gid * 2 * kTcWp + ks * 8 + tig;
             const uint4 b0l = pb[0], b0h = pb[kTcWp], b1l = pb[4], b1h = pb[4 + kTcWp];
             const uint32_t B[kTcSlices][2] = {{b0l.x, b1l.x}, {b0l.y, b1l.y}, {b0l.z, b1l.z}, {b0l.w, b1l.w},
                                               {b0h.x, b1h.x}, {b0h.y, b1h.y}, {b0h.z, b1h.z}};
 #pragma unroll
-            for (int p = 0; p < kTcSlices; ++p)
+            for (int p = 0; p < kTcSlices; ++p) {
+                const uint32_t* xp = x0 + 16 * p;
+                const uint32_t v01 = __byte_perm(xp[0], xp[kUdXw], sel);
+                const uint32_t v89 = __byte_perm(xp[8 * kUdXw], xp[9 * kUdXw], sel);
+                const uint32_t a0 = tc_widen<0x4140>(v01), a1 = tc_widen<0x4342>(v01);
+                const uint32_t a2 = tc_widen<0x4140>(v89), a3 = tc_widen<0x4342>(v89);
 #pragma unroll
-                for (int r = 0; r < kTcSlices - p; ++r)
-                    mma_bf16_16816(acc[p + r], A[p][0], A[p][1], A[p][2], A[p][3], B[r][0], B[r][1]);
+                for (int r = 0; r < kTcSlices - p; ++r) mma_f16_16816(acc[p + r], a0, a1, a2, a3, B[r][0], B[r][1]);
+            }
         }
         // 4. the pair's exact integer sums: the second warp hands its S to the first
         long long S[4];
@@ -225,7 +211,7 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
 #pragma unroll
             for (int e = 0; e < 4; ++e) ksum[(t * 4 + e) * 32 + lane] = S[e];
         __syncthreads();
-        // every MMA is done with xu: the next chunk's Q digits stream in during the
+        // every MMA is done with xw: the next chunk's Q digits stream in during the
         // combine and the column pass
         if (ci + G < nchunks) stage_q(ci + G);
         if (khalf == 0) {
@@ -237,20 +223,31 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
                 const long long St = S[e] + ksum[(t * 4 + e) * 32 + lane];
                 const int f = fj[j];
                 otile[j * kUdRows + r] = f == kTcBadExp ? __longlong_as_double(0x7FF8000000000000ll)
-                                                        : tc_int_to_double(St, f - 52);
+                                                        : tc_int_to_double(St, f - kTcShift);
             }
         }
         __syncthreads();
-        // 5. the new columns: FP64 rows in pairs and their digits (one warp per column)
-        if (warp < nb) {
-            const int j = warp;
-            const int64_t r0 = row0 + 2 * lane;
-            const double x0 = r0 < n ? otile[j * kUdRows + 2 * lane] : 0.0;
-            const double x1 = r0 + 1 < n ? otile[j * kUdRows + 2 * lane + 1] : 0.0;
-            double* dst = V + (size_t)j * ldv + r0;
-            if (r0 + 1 < n) *reinterpret_cast<double2*>(dst) = make_double2(x0, x1);
-            else if (r0 < n) *dst = x0;
-            tc_digits_store(x0, x1, ci, k + j, capc, dig, dex);
+        // 5. the new columns: FP64 rows and their digits (half warp per column)
+        for (int j0 = 2 * warp; j0 < nb; j0 += 16) {
+            const int j = j0 + (lane >> 4);
+            const int jj = j < nb ? j : j0;
+            double x[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int rr = 16 * hw_w + 2 * hw_g + (q & 1) + 8 * (q >> 1);
+                x[q] = row0 + rr < n ? otile[jj * kUdRows + rr] : 0.0;
+            }
+            if (j < nb) {
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int64_t r0 = row0 + 16 * hw_w + 2 * hw_g + 8 * hh;
+                    double* dst = V + (size_t)j * ldv + r0;
+                    if (r0 + 1 < n) *reinterpret_cast<double2*>(dst) = make_double2(x[2 * hh], x[2 * hh + 1]);
+                    else if (r0 < n) *dst = x[2 * hh];
+                }
+            }
+            tc_b8_store(x, dig + ((size_t)ci * capc + k + jj) * kTcB8Units,
+                        dex + (size_t)ci * tc_dex_stride(capc) + k + jj);
         }
     }
     cp_async_wait_all();

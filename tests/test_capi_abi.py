@@ -95,12 +95,12 @@ def test_bad_arguments_are_rejected_before_any_launch(capi):
 
 
 def test_digit_basis_size_formula(capi):
-    """ortho_digits_bytes (host code): per 64-row chunk, capc columns of 64
-    16-byte digit units, then each chunk's row of int32 exponents padded to a
-    multiple of four columns (16-byte aligned rows), plus 256 bytes."""
+    """ortho_digits_bytes (host code): per 64-row chunk, capc columns of 448
+    digit bytes (seven per row), then each chunk's row of int32 exponents padded
+    to a multiple of four columns (16-byte aligned rows), plus 256 bytes."""
     for n, capc in [(1, 1), (64, 5), (65, 61), (4194304, 64), (1000, 63), (129, 62)]:
         chunks = (n + 63) // 64
-        expect = chunks * capc * 64 * 16 + chunks * ((capc + 3) // 4 * 4) * 4 + 256
+        expect = chunks * capc * 64 * 7 + chunks * ((capc + 3) // 4 * 4) * 4 + 256
         assert capi.digits_bytes(n, capc) == expect, (n, capc)
 
 
@@ -108,7 +108,7 @@ def test_footprint_covers_the_resident_state(capi):
     """gmres_footprint (host code; the serving loop admits requests by it): at
     least the basis (m+1) x n in the basis precision plus the CSR, as the
     admission rule states; the tensor-core arithmetic adds the digit basis
-    (16 bytes per basis entry); monotone in n and nnz; 0 for invalid input."""
+    (7 bytes per basis entry); monotone in n and nnz; 0 for invalid input."""
     n, nnz = 1 << 20, 5 << 20
     ldq = (n + 31) // 32 * 32
     csr = (n + 1) * 4 + nnz * 4 + nnz * 8
@@ -118,7 +118,8 @@ def test_footprint_covers_the_resident_state(capi):
     assert f64 >= 61 * ldq * 8 + csr
     assert mix >= 61 * ldq * 4 + csr + nnz * 4     # FP32 basis, plus the FP32 copy of the values
     assert mix < f64 - 61 * ldq * 3                 # the basis takes half the bytes
-    assert tc - f64 >= 61 * n * 16                  # seven bf16 digits (+ one spare) per entry
+    assert tc - f64 >= 61 * n * 7                   # seven digit bytes per entry
+    assert tc - f64 < 61 * n * 8                    # and no more than the FP64 basis itself
     assert f64 - csr < 61 * ldq * 8 * 1.25          # and not much else
     assert capi.footprint(2 * n, nnz, capi.default_opts(m=60, s=5, panel=60)) > f64
     assert capi.footprint(n, 2 * nnz, capi.default_opts(m=60, s=5, panel=60)) > f64

@@ -445,12 +445,12 @@ def test_digit_basis_update_matches_oracle_and_writes_digits(lib, n, k, nb):
     capi.digits_fill(X[:, k:], k, ref, capc)
     torch.cuda.synchronize()
     nch = (n + 63) // 64
-    units = dig[: nch * capc * 1024].view(nch, capc, 1024)
-    runits = ref[: nch * capc * 1024].view(nch, capc, 1024)
+    units = dig[: nch * capc * 448].view(nch, capc, 448)     # 7 digit bytes per value, 64 rows
+    runits = ref[: nch * capc * 448].view(nch, capc, 448)
     assert torch.equal(units[:, k:k + nb], runits[:, k:k + nb])
     capx = (capc + 3) // 4 * 4      # a chunk's exponent row starts on a 16-byte boundary
-    ex = dig[nch * capc * 1024: nch * capc * 1024 + nch * capx * 4].view(torch.int32).view(nch, capx)
-    rex = ref[nch * capc * 1024: nch * capc * 1024 + nch * capx * 4].view(torch.int32).view(nch, capx)
+    ex = dig[nch * capc * 448: nch * capc * 448 + nch * capx * 4].view(torch.int32).view(nch, capx)
+    rex = ref[nch * capc * 448: nch * capc * 448 + nch * capx * 4].view(torch.int32).view(nch, capx)
     assert torch.equal(ex[:, k:k + nb], rex[:, k:k + nb])
 
 
