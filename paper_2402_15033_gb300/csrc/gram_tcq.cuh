@@ -129,7 +129,10 @@ __device__ void gram_tcq_part(int64_t n, const double* __restrict__ V, int64_t l
     int ev = 0;                     // exponent of V column gid in the current chunk
     int j = 0;                      // consume cursor (item index)
     for (int t = 0; t < (int)tw; ++t) {
-        for (int m = 0; m < nmt; ++m, ++j) {
+        // M-tiles unrolled, so that out[m] stays in registers
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            if (m >= nmt) break;
             // item j's copies (and, at a chunk start, the chunk's V) have landed:
             // V(t) was committed in item j's group or, for one-tile chunks, in the
             // group right after it
@@ -186,11 +189,13 @@ __device__ void gram_tcq_part(int64_t n, const double* __restrict__ V, int64_t l
                 vl[cc] = (((c - k) & 7) << 2) | tig;
             }
             const bool vtile = m0 + 15 >= k;   // warp-uniform: the M-tile holds V columns
-            float acc[kTcSlices][4];
+            // even and odd k-steps accumulate separately (each sum stays an exact
+            // integer below 2^23), so that consecutive MMAs never wait on each other
+            float acc[kTcSlices][4], acc1[kTcSlices][4];
 #pragma unroll
             for (int tt = 0; tt < kTcSlices; ++tt)
 #pragma unroll
-                for (int i = 0; i < 4; ++i) acc[tt][i] = 0.f;
+                for (int i = 0; i < 4; ++i) acc[tt][i] = acc1[tt][i] = 0.f;
 #pragma unroll
             for (int p = 0; p < kTcSlices; ++p) {
                 const uint4 u0 = rs[p * 32], u1 = rs[(kTcSlices + p) * 32];
@@ -209,10 +214,16 @@ __device__ void gram_tcq_part(int64_t n, const double* __restrict__ V, int64_t l
                         if (isv[1]) { a1 = s1; a3 = s3; }
                     }
 #pragma unroll
-                    for (int r = 0; r < kTcSlices - p; ++r)
-                        mma_f16_16816(acc[p + r], a0, a1, a2, a3, bv[ks][r][0], bv[ks][r][1]);
+                    for (int r = 0; r < kTcSlices - p; ++r) {
+                        if (ks & 1) mma_f16_16816(acc1[p + r], a0, a1, a2, a3, bv[ks][r][0], bv[ks][r][1]);
+                        else mma_f16_16816(acc[p + r], a0, a1, a2, a3, bv[ks][r][0], bv[ks][r][1]);
+                    }
                 }
             }
+#pragma unroll
+            for (int tt = 0; tt < kTcSlices; ++tt)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[tt][i] += acc1[tt][i];
             // the M-tile's chunk contribution S * 2^(E_i + E_j - 50)
             const int ej0 = __shfl_sync(0xffffffffu, ev, (2 * tig) << 2);
             const int ej1 = __shfl_sync(0xffffffffu, ev, (2 * tig + 1) << 2);
@@ -233,6 +244,7 @@ __device__ void gram_tcq_part(int64_t n, const double* __restrict__ V, int64_t l
                 out[m][e] = max(e1, e2) == kTcBadExp ? __longlong_as_double(0x7FF8000000000000ll)
                                                      : tc_accum(out[m][e], S, e1 + e2 - kTcShift);
             }
+            ++j;
         }
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");

@@ -207,7 +207,7 @@ cudaError_t launch_update_tc(cudaStream_t st, int64_t n, const double* Q, int64_
 }
 
 // Narrow update from the digit basis (update_tcd.cuh), nb <= 8, k + nb <= 64.
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(kUdThreads, 4)
 update_tcd_kernel(int64_t n, int k, double* V, int64_t ldv, int nb, const double* __restrict__ R, int ldr,
                   const int32_t* d_status, const int32_t* d_skip, int mode, uint4* dig, int* dex, int capc) {
     extern __shared__ __align__(16) char td_smem[];
@@ -221,11 +221,11 @@ cudaError_t launch_update_tcd(cudaStream_t st, int64_t n, int k, double* V, int6
     static const cudaError_t attr = smem_limit(update_tcd_kernel, update_tcd_smem(kTuMaxKX, kUdMaxNB));
     if (attr != cudaSuccess) return attr;
     const int64_t chunks = (n + kUdRows - 1) / kUdRows;
-    const int G = (int)std::min<int64_t>(chunks, 2 * (int64_t)num_sms());
+    const int G = (int)std::min<int64_t>(chunks, 4 * (int64_t)num_sms());
     uint4* dig = static_cast<uint4*>(digits);
     int* dex = reinterpret_cast<int*>(dig + tc_digits_units(n, capc));
-    update_tcd_kernel<<<G, 256, update_tcd_smem(k + nb, nb), st>>>(n, k, V, ldv, nb, R, ldr, d_status, d_skip, mode,
-                                                                   dig, dex, capc);
+    update_tcd_kernel<<<G, kUdThreads, update_tcd_smem(k + nb, nb), st>>>(n, k, V, ldv, nb, R, ldr, d_status, d_skip,
+                                                                          mode, dig, dex, capc);
     return cudaGetLastError();
 }
 

@@ -17,9 +17,11 @@
 // Work per 64-row chunk: copy Q's digit bytes (448 per column, the layout of
 // the digit basis, columns 464 bytes apart in shared memory), slice nb
 // columns of V into the same layout and nb columns of W'' into f16 B
-// fragments, 4 M-tiles x (k-steps over k + nb) MMAs shared by warp pairs (the
-// pair splits the k-steps and adds its exact integer sums), the outputs staged
-// in shared memory and written out with their digits.  An A fragment takes
+// fragments, 4 M-tiles x (k-steps over k + nb) MMAs, one warp per M-tile, the
+// outputs staged in shared memory and written out with their digits.  A CTA is
+// four warps and four CTAs share an SM, so that the slicing phases of one
+// chunk (few warps, short dependent chains between barriers) overlap the MMAs
+// of the others.  An A fragment takes
 // rows r and r + 8 of two K columns from one digit word of each column (one
 // byte permute), then widens them (two permutes and two f16x2 subtractions).
 #pragma once
@@ -30,6 +32,8 @@ namespace gm {
 
 constexpr int kUdRows = 64;                   // rows per chunk (= the digit basis chunk)
 constexpr int kUdMaxNB = 8;
+constexpr int kUdWarps = 4;                   // one warp per 16-row M-tile
+constexpr int kUdThreads = 32 * kUdWarps;
 constexpr int kUdXw = 116;                    // words per column of X's digit bytes in shared memory (112 + 4 pad)
 
 __host__ __device__ constexpr size_t update_tcd_smem(int kx, int nb) {
@@ -38,13 +42,12 @@ __host__ __device__ constexpr size_t update_tcd_smem(int kx, int nb) {
            + (size_t)nb * kUdRows * sizeof(double)          // raw V chunk
            + (size_t)kx * nb * sizeof(double)               // W (FP64)
            + (size_t)nb * kUdRows * sizeof(double)          // output tile
-           + (size_t)4 * 4 * 32 * sizeof(long long)         // the warp pairs' integer sums
            + (64 + kUdMaxNB) * sizeof(int);                 // E_c, f_j
 }
 
 // Q(:, 0:k) digits from the digit basis (dig, dex, capc), V(:, 0:nb) raw; the
-// updated V and its digits (digit columns k .. k+nb-1) written back.  256
-// threads; 64-row chunks b, b+G, ...
+// updated V and its digits (digit columns k .. k+nb-1) written back.
+// kUdThreads threads; 64-row chunks b, b+G, ...
 __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb, const double* __restrict__ R,
                                 int ldr, int mode, int b, int G, char* smem, uint4* dig, int* dex, int capc) {
     const int kx = k + nb;
@@ -56,8 +59,7 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
     double* raw = reinterpret_cast<double*>(wu + kUdMaxNB * 2 * kTcWp);          // [nb][64]
     double* W = raw + nb * kUdRows;                                              // [nb][kx]  (W[c + j kx])
     double* otile = W + kx * nb;                                                 // [nb][64]
-    long long* ksum = reinterpret_cast<long long*>(otile + nb * kUdRows);        // [4][4][32]
-    int* ec = reinterpret_cast<int*>(ksum + 4 * 4 * 32);                         // [64] chunk column exponents
+    int* ec = reinterpret_cast<int*>(otile + nb * kUdRows);                      // [64] chunk column exponents
     int* fj = ec + 64;                                                           // [8]
 
     // ---- W = [-P T^{-1}; T^{-1}] in FP64 (T^{-1} by substitution; the X region is scratch)
@@ -101,10 +103,8 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
     for (int e = tid; e < 64 * kUdXw; e += blockDim.x) xw[e] = 0x80808080u;
     for (int e = tid; e < kUdMaxNB * 2 * kTcWp; e += blockDim.x) wu[e] = make_uint4(0u, 0u, 0u, 0u);
 
-    // warp pair (tile t = warp / 2: rows 16t .. 16t+15) splits the k-steps
-    const int t = warp >> 1, khalf = warp & 1;
-    const int kmid = (nks + 1) / 2;
-    const int ks0 = khalf ? kmid : 0, ks1 = khalf ? nks : kmid;
+    // warp t: tile t (rows 16t .. 16t+15), every k-step
+    const int t = warp;
     const int m0 = 16 * t;
     // rows m0 + gid and + 8 are bytes (gid & 1) and 2 + (gid & 1) of word t of unit
     // 4p + gid / 2; one permute takes them from columns c and c + 1
@@ -112,13 +112,13 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
     const int uoff = (gid >> 1) * 4 + t;                   // word of digit 0 within a column
 
     const int64_t nchunks = (n + kUdRows - 1) / kUdRows;
-    // raw V: rows 2(tid % 32), +1 of columns tid / 32 (one column per warp)
+    // raw V: rows 2(tid % 32), +1 of columns warp, warp + 4, ...
     auto stage_v = [&](int64_t ch) {
         const int64_t row = ch * kUdRows + 2 * lane;
-        if (warp < nb) {
-            const int bytes = row + 2 <= n ? 16 : (row < n ? 8 : 0);
-            const double* p = V + (int64_t)warp * ldv + row;
-            cp_async16(raw + warp * kUdRows + 2 * lane, bytes ? (const void*)p : (const void*)V, bytes);
+        const int bytes = row + 2 <= n ? 16 : (row < n ? 8 : 0);
+        for (int j = warp; j < nb; j += kUdWarps) {
+            const double* p = V + (int64_t)j * ldv + row;
+            cp_async16(raw + j * kUdRows + 2 * lane, bytes ? (const void*)p : (const void*)V, bytes);
         }
         cp_async_commit();
     };
@@ -144,7 +144,7 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
         cp_async_wait_all();
         __syncthreads();
         // 1. V's columns sliced into digit bytes next to Q's (half warp per column)
-        for (int j0 = 2 * warp; j0 < nb; j0 += 16) {
+        for (int j0 = 2 * warp; j0 < nb; j0 += 2 * kUdWarps) {
             const int jj = j0 + (lane >> 4) < nb ? j0 + (lane >> 4) : j0;
             double x[4];
 #pragma unroll
@@ -156,8 +156,8 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
         if (ci + G < nchunks) stage_v(ci + G);
         // 2. W'' = D W per output column j (lane = K pair: rows 2l, 2l+1 of W''),
         //    sliced against its largest exponent f_j
-        if (warp < nb) {
-            const int j = warp, c0 = 2 * lane, c1 = 2 * lane + 1;
+        for (int j = warp; j < nb; j += kUdWarps) {
+            const int c0 = 2 * lane, c1 = 2 * lane + 1;
             const double w0 = c0 < kx ? W[c0 + j * kx] : 0.0, w1 = c1 < kx ? W[c1 + j * kx] : 0.0;
             const int e0 = c0 < kx ? ec[c0] : 0, e1 = c1 < kx ? ec[c1] : 0;
             const int b0 = tc_bexp(w0), b1 = tc_bexp(w1);
@@ -184,7 +184,7 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[q][e] = 0.f;
 #pragma unroll 1
-        for (int ks = ks0; ks < ks1; ++ks) {
+        for (int ks = 0; ks < nks; ++ks) {
             const int ca = 16 * ks + 2 * tig;     // K columns ca, ca+1 (a0, a1) and ca+8, ca+9 (a2, a3)
             const uint32_t* x0 = xw + ca * kUdXw + uoff;
             const uint4* pb = wu + gid * 2 * kTcWp + ks * 8 + tig;
@@ -202,33 +202,24 @@ __device__ void update_tcd_body(int64_t n, int k, double* V, int64_t ldv, int nb
                 for (int r = 0; r < kTcSlices - p; ++r) mma_f16_16816(acc[p + r], a0, a1, a2, a3, B[r][0], B[r][1]);
             }
         }
-        // 4. the pair's exact integer sums: the second warp hands its S to the first
-        long long S[4];
+        // 4. the outputs S * 2^(f_j - 50), S from the seven exact sums
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-            S[e] = tc_combine(acc[0][e], acc[1][e], acc[2][e], acc[3][e], acc[4][e], acc[5][e], acc[6][e]);
-        if (khalf == 1)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) ksum[(t * 4 + e) * 32 + lane] = S[e];
-        __syncthreads();
-        // every MMA is done with xw: the next chunk's Q digits stream in during the
-        // combine and the column pass
-        if (ci + G < nchunks) stage_q(ci + G);
-        if (khalf == 0) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int r = m0 + gid + ((e & 2) ? 8 : 0);
-                const int j = 2 * tig + (e & 1);
-                if (j >= nb) continue;
-                const long long St = S[e] + ksum[(t * 4 + e) * 32 + lane];
-                const int f = fj[j];
-                otile[j * kUdRows + r] = f == kTcBadExp ? __longlong_as_double(0x7FF8000000000000ll)
-                                                        : tc_int_to_double(St, f - kTcShift);
-            }
+        for (int e = 0; e < 4; ++e) {
+            const int r = m0 + gid + ((e & 2) ? 8 : 0);
+            const int j = 2 * tig + (e & 1);
+            if (j >= nb) continue;
+            const long long S =
+                tc_combine(acc[0][e], acc[1][e], acc[2][e], acc[3][e], acc[4][e], acc[5][e], acc[6][e]);
+            const int f = fj[j];
+            otile[j * kUdRows + r] = f == kTcBadExp ? __longlong_as_double(0x7FF8000000000000ll)
+                                                    : tc_int_to_double(S, f - kTcShift);
         }
         __syncthreads();
+        // every MMA is done with xw: the next chunk's Q digits stream in during the
+        // column pass and the next chunk's slicing
+        if (ci + G < nchunks) stage_q(ci + G);
         // 5. the new columns: FP64 rows and their digits (half warp per column)
-        for (int j0 = 2 * warp; j0 < nb; j0 += 16) {
+        for (int j0 = 2 * warp; j0 < nb; j0 += 2 * kUdWarps) {
             const int j = j0 + (lane >> 4);
             const int jj = j < nb ? j : j0;
             double x[4];
