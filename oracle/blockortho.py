@@ -138,6 +138,40 @@ def bcgs_pip(Q: np.ndarray, V: np.ndarray, where: str = "bcgs_pip"):
     return right_trsm_upper(W, T), P, T
 
 
+UNIT_ROUNDOFF = 2.0 ** -53
+
+
+def cholqr_shift(n: int, c: int, fro2: float) -> float:
+    """Shift of shifted CholQR (Fukaya, Kannan, Nakatsukasa, Zhang, Yamamoto,
+    SIAM J. Sci. Comput. 2020; cited in §II as the remedy for CholQR's
+    instability): sigma = 11 (n c + c (c + 1)) u ||X||^2 for an n x c block X,
+    u the unit roundoff.  ||X||_2^2 is bounded here by the Frobenius norm
+    squared ``fro2`` (the trace of the block's Gram), which keeps the
+    guarantee (a larger shift)."""
+    return 11.0 * (n * c + c * (c + 1)) * UNIT_ROUNDOFF * fro2
+
+
+def bcgs_pip_shifted(Q: np.ndarray, V: np.ndarray, where: str = "bcgs_pip_shifted"):
+    """BCGS-PIP with a shifted Cholesky (§II's shifted CholQR inside the
+    Pythagorean step of Fig. 4a): [P; G] = [Q, V]^T V; T = Chol(G - P^T P +
+    sigma I) with sigma = cholqr_shift(n, nb, trace(G)); Q^ = (V - Q P) T^{-1}.
+    V = Q P + Q^ T still holds, but Q^ is only well conditioned, not
+    orthonormal: Q^^T Q^ = I - sigma (T^T T)^{-1} for an orthonormal Q.
+    Returns (Q^, P, T)."""
+    k = Q.shape[1]
+    n, c = V.shape
+    X = np.concatenate([Q, V], axis=1)
+    PG = X.T @ V                      # the single reduction
+    P = PG[:k, :]
+    G = PG[k:, :]
+    S = G - P.T @ P + cholqr_shift(n, c, float(np.trace(G))) * np.eye(c)
+    T, info = chol_upper(S)
+    if info:
+        raise Breakdown(info, where, pivot_value(S, T, info), pip_margin(Q, V, P))
+    W = V - Q @ P
+    return right_trsm_upper(W, T), P, T
+
+
 def bcgs_pip2(Q: np.ndarray, V: np.ndarray, where: str = "bcgs_pip2"):
     """BCGS-PIP2 (Fig. 4b, §IV-C): BCGS-PIP applied twice.
 
@@ -174,6 +208,30 @@ def stage1_lowp(Qacc: np.ndarray, V: np.ndarray, where: str = "stage1", store=np
     if info:
         raise Breakdown(info, where, pivot_value(G, T, info))
     return right_trsm_upper(W, T).astype(store).astype(np.float64), P, T
+
+
+def stage1_shifted(Qacc: np.ndarray, V: np.ndarray, where: str = "stage1"):
+    """Stage 1 with the shifted Cholesky (``bcgs_pip_shifted``): the block is
+    pre-processed to a well-conditioned one even where the unshifted
+    Pythagorean Cholesky would break down on an ill-conditioned MPK block."""
+    return bcgs_pip_shifted(Qacc, V, where)
+
+
+def stage2_shifted(Qfin: np.ndarray, Qhat: np.ndarray, where: str = "stage2"):
+    """Stage 2 after shifted stage-1 blocks: shifted CholQR3 (Fukaya et al.:
+    one shifted pass, then CholQR twice) of the big panel, each pass a
+    BCGS-PIP against Q_fin.  The shifted stage-1 blocks are well conditioned
+    but not orthonormal, so the panel's condition number can reach
+    u^(-1/2); the shifted pass brings it to O(1) and the two plain passes to
+    orthonormal.  Returns (Q, P, T) with Q^ = Q_fin P + Q T: pass i gives
+    (P_i, T_i) and P = P_a + P_b T_a + P_c T_b T_a, T = T_c T_b T_a."""
+    Qa, P, T = bcgs_pip_shifted(Qfin, Qhat, where + "/shifted")
+    Q = Qa
+    for q in ("second", "third"):
+        Q, Pq, Tq = bcgs_pip(Qfin, Q, where + "/" + q)
+        P = P + Pq @ T
+        T = Tq @ T
+    return Q, P, T
 
 
 def stage2(Qfin: np.ndarray, Qhat: np.ndarray, where: str = "stage2"):

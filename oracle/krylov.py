@@ -256,7 +256,8 @@ def newton_sigma(theta, fallback: float) -> float:
 
 
 def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=1000,
-                ortho="two_stage", sigma=None, theta=None, return_basis=False, basis_dtype=np.float64):
+                ortho="two_stage", sigma=None, theta=None, return_basis=False, basis_dtype=np.float64,
+                shift=False):
     """s-step GMRES (Fig. 1, §III) with the chosen block orthogonalization.
 
     ``panel`` is the second step size s^ of the two-stage scheme (§V); it must
@@ -265,6 +266,9 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
     same block machinery), ``newton_shifts`` turns its Hessenberg matrix into s
     shifts, and every later cycle uses the Newton basis with them, scaled by
     ``newton_sigma`` unless ``sigma`` is given.  ``ortho`` in {"two_stage", "bcgs_pip2", "bcgs2_cholqr2"}.
+    ``shift=True`` (two-stage, FP64 basis) runs stage 1 with the shifted
+    Cholesky of ``blockortho.stage1_shifted`` and stage 2 as shifted CholQR3
+    of the big panel (``blockortho.stage2_shifted``).
     ``basis_dtype=np.float32`` is the mixed-precision pattern: the basis is
     stored in FP32 and the MPK runs in FP32 on an FP32 copy of A, while every
     Gram product and sum, the Cholesky factors, the Hessenberg/Givens work, x
@@ -355,7 +359,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
                 W = mpk(Mb, Q[:, st], s, sig, th)
                 cols = slice(st + 1, st + s + 1)
                 if ortho == "two_stage":
-                    st1 = bo.stage1_lowp if lowp else bo.stage1
+                    st1 = bo.stage1_lowp if lowp else (bo.stage1_shifted if shift else bo.stage1)
                     Qh, P, T = st1(Q[:, : st + 1].astype(f64), W.astype(f64), f"cycle{cyc}/block{j}")
                     Q[:, cols] = Qh
                     Rhat[: st + 1, cols] = P
@@ -364,8 +368,8 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
                     if t < hi:
                         continue
                     where_blk = m // s + (t // panel) - 1
-                    Qn, P2, T2 = bo.stage2(Q[:, :lo].astype(f64), Q[:, lo:t + 1].astype(f64),
-                                           f"cycle{cyc}/stage2@{t}")
+                    st2 = bo.stage2_shifted if (shift and not lowp) else bo.stage2
+                    Qn, P2, T2 = st2(Q[:, :lo].astype(f64), Q[:, lo:t + 1].astype(f64), f"cycle{cyc}/stage2@{t}")
                     Q[:, lo:t + 1] = Qn
                     C[:lo, lo:t + 1] = P2
                     C[lo:t + 1, lo:t + 1] = T2

@@ -200,6 +200,77 @@ def test_two_stage_panel_equals_householder_r():
     assert np.allclose(Rd, r, atol=1e-12 * np.abs(r).max())
 
 
+# ---------------------------------------------------------------- shifted CholQR (§II)
+def test_cholqr_shift_by_hand():
+    """sigma = 11 (n c + c (c + 1)) u ||X||^2 with u = 2^-53: for n = 1000,
+    c = 5, ||X||_F^2 = 3: 11 * 5030 * 3 / 2^53, exactly."""
+    assert bo.cholqr_shift(1000, 5, 3.0) == 165990.0 / 2.0 ** 53
+    assert bo.cholqr_shift(1, 1, 0.0) == 0.0
+
+
+def test_shifted_pip_identity_and_reconstruction():
+    """For an orthonormal Q, T^T T = (V - Q P)^T (V - Q P) + sigma I, so the
+    shifted stage-1 block satisfies Q^^T Q^ + sigma T^-T T^-1 = I exactly in
+    exact arithmetic.  On a block of condition 1e9 the shift term is of order
+    one, and the rounding of G - P^T P, amplified by ||T^-1||^2, stays a fixed
+    fraction (about 1/(11 nb), by the choice of sigma) of it: the identity
+    holds to 5% of the shift term, so a dropped sigma or one off by 10% fails.
+    V = Q P + Q^ T to rounding."""
+    g = synth.rng(4545)
+    n, k, c = 3000, 4, 5
+    Q, _ = _sign_fixed_qr(g.standard_normal((n, k)))
+    V = synth.logscaled(n, c, 1e9, seed=7) + Q @ g.standard_normal((k, c))
+    Qh, P, T = bo.bcgs_pip_shifted(Q, V)
+    sig = bo.cholqr_shift(n, c, float(np.trace(V.T @ V)))
+    Ti = np.linalg.inv(T)
+    E = Qh.T @ Qh + sig * (Ti.T @ Ti) - np.eye(c)
+    term = np.abs(sig * (Ti.T @ Ti)).max()
+    assert term > 0.1                                        # the shift matters here
+    assert np.abs(E).max() <= 0.05 * term, (np.abs(E).max(), term)
+    assert np.abs(Q @ P + Qh @ T - V).max() <= 1e-13 * np.abs(V).max()
+
+
+def test_shifted_two_stage_is_stable_where_cholqr_breaks_down():
+    """§II: shifted CholQR is stable as long as the input is numerically full
+    rank.  A big panel of condition 1e12 (beyond u^(-1/2), where the plain
+    Pythagorean stage 1 breaks down): shifted stage 1 per block, then stage 2
+    as shifted CholQR3 (a shifted pass and two plain ones), gives
+    ||I - Q^T Q|| = O(eps) and V = Q R to rounding."""
+    n, c, p = 20000, 3, 2
+    V = synth.logscaled(n, c * p, 1e12, seed=11)
+    blocks = [V[:, i * c:(i + 1) * c] for i in range(p)]
+    with pytest.raises(bo.Breakdown):
+        bo.two_stage_panel(np.zeros((n, 0)), blocks)
+    Qhat = np.zeros_like(V)
+    Rh = np.zeros((c * p, c * p))
+    for i, B in enumerate(blocks):
+        Qh, P, T = bo.stage1_shifted(Qhat[:, :i * c], B)
+        Qhat[:, i * c:(i + 1) * c] = Qh
+        Rh[:i * c, i * c:(i + 1) * c] = P
+        Rh[i * c:(i + 1) * c, i * c:(i + 1) * c] = T
+    Qf, _, T2 = bo.stage2_shifted(np.zeros((n, 0)), Qhat)
+    assert checks.orth_error(Qf)[0] < 100 * EPS
+    assert np.abs(Qf @ (T2 @ Rh) - V).max() <= 1e-13 * np.abs(V).max()
+
+
+def test_shifted_sstep_gmres_solves_where_the_monomial_basis_breaks_down():
+    """s = 10 monomial on the 64 x 64 Laplacian: the plain two-stage scheme
+    breaks down in its first cycle; with the shifted stage 1 (and the
+    re-orthogonalized stage 2) it converges to 1e-8, with the forward error
+    within the closed-form condition number times the tolerance."""
+    A = synth.laplace2d(64)
+    M = kr.as_operator(A)
+    xt = synth.x_true(A.n, 0)
+    b = M @ xt
+    _, i0 = kr.sstep_gmres(A, b, m=60, s=10, panel=60, tol=1e-8)
+    assert i0["status"] == kr.STATUS_BREAKDOWN
+    x, i1 = kr.sstep_gmres(A, b, m=60, s=10, panel=60, tol=1e-8, shift=True)
+    assert i1["status"] == 0
+    assert np.linalg.norm(b - M @ x) / np.linalg.norm(b) <= 1e-8
+    lo, hi = checks.laplace2d_extreme_eigs(64)
+    assert np.linalg.norm(x - xt) / np.linalg.norm(xt) <= (hi / lo) * 1e-8
+
+
 # ---------------------------------------------------------------- least squares and Hessenberg
 def test_givens_solves_the_hessenberg_least_squares():
     g = synth.rng(19)
