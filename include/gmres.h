@@ -81,6 +81,17 @@ extern "C" {
                                       /* that do not start on a 16-byte boundary (odd ld for FP64)     */
                                       /* run the FP64 kernels instead.                                 */
 
+#define GMRES_SHIFT_NONE           0  /* stage 1 factors G - P^T P as in Fig. 4a (default)              */
+#define GMRES_SHIFT_CHOLQR3        1  /* opt-in: shifted CholQR (§II, Fukaya et al. 2020) for blocks     */
+                                      /* beyond the u^(-1/2) condition of Eq. (1): stage 1 factors      */
+                                      /* G - P^T P + sigma I, sigma = 11 (n s + s (s+1)) u ||V||_F^2,    */
+                                      /* so it does not break down on numerically full-rank blocks but  */
+                                      /* leaves them only well conditioned; stage 2 is then shifted     */
+                                      /* CholQR3 of the big panel (a shifted pass, two plain passes).   */
+                                      /* A numerically rank-deficient panel still breaks down.  FP64    */
+                                      /* basis, two-stage or BCGS-PIP2 ortho, any arithmetic; not in the  */
+                                      /* batched engine.  The paper has no measurement of it.           */
+
 typedef struct gmres_opts {
     int32_t m;             /* restart length: m+1 basis vectors per cycle (Table 1)            */
     int32_t s;             /* step size of the first stage (Table 1), 1 <= s <= 16            */
@@ -96,7 +107,8 @@ typedef struct gmres_opts {
     double  inner_tol;     /* mixed precision: relative tolerance of each inner FP32 solve     */
     int32_t max_ir;        /* mixed precision: maximum FP64 refinement steps                   */
     int32_t arith;         /* GMRES_ARITH_*: arithmetic of the Gram and block-update kernels   */
-    int32_t reserved[6];
+    int32_t shift;         /* GMRES_SHIFT_*: shifted CholQR in the two-stage scheme             */
+    int32_t reserved[5];
 } gmres_opts;
 
 typedef struct gmres_result {
@@ -186,6 +198,17 @@ int ortho_stage1(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t 
 int ortho_stage2(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
                  double* V, int64_t ldv, int32_t nb, double* R, int32_t ldr,
                  void* d_work, size_t work_bytes, int32_t* d_status);
+
+/* Stage 1 with the shifted Cholesky of shifted CholQR (§II; GMRES_SHIFT_CHOLQR3):
+ * [P; G] = [Q, V]^T V, T = Chol(G - P^T P + sigma I) with
+ * sigma = 11 (n nb + nb (nb + 1)) u trace(G), u = 2^-53, and
+ * V <- (V - Q P) T^{-1}.  V = Q P + V_out T holds as for ortho_stage1, but the
+ * output block is only well conditioned (V_out^T V_out = I - sigma T^-T T^-1 for
+ * an orthonormal Q); it does not break down on numerically full-rank blocks.
+ * Arguments, limits and errors as for ortho_stage1 (FP64 arithmetic). */
+int ortho_stage1_shifted(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k,
+                         double* V, int64_t ldv, int32_t nb, double* R, int32_t ldr,
+                         void* d_work, size_t work_bytes, int32_t* d_status);
 
 /* FP32-basis variants (the mixed-precision pattern): Q and V are FP32, every
  * product and sum is formed in FP64 (FP32 inputs widen exactly), R and the

@@ -36,6 +36,8 @@ GMRES_BASIS_NEWTON_AUTO = 2
 GMRES_ARITH_FP64 = 0
 GMRES_ARITH_DD = 1
 GMRES_ARITH_TC = 2
+GMRES_SHIFT_NONE = 0
+GMRES_SHIFT_CHOLQR3 = 1
 
 
 class gmres_opts(C.Structure):
@@ -43,7 +45,7 @@ class gmres_opts(C.Structure):
                 ("tol", C.c_double), ("sigma", C.c_double),
                 ("ortho", C.c_int32), ("precision", C.c_int32), ("basis", C.c_int32), ("timing", C.c_int32),
                 ("theta", C.c_double * 16), ("inner_tol", C.c_double), ("max_ir", C.c_int32),
-                ("arith", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("arith", C.c_int32), ("shift", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class gmres_server_stats(C.Structure):
@@ -82,6 +84,7 @@ SIGNATURES = {
     "gmres_last_error": (C.c_char_p, []),
     "ortho_workspace_bytes": (_sz, [_i64, _i32, _i32]),
     "ortho_stage1": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
+    "ortho_stage1_shifted": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "ortho_stage2": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "gmres_mpk": (_i32, [_vp, _vp, _vp, _i64, _i32, _dbl, C.POINTER(_dbl)]),
     "ortho_gram_chol": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
@@ -464,6 +467,13 @@ def ortho_stage1(Q, V, R, work, status, k=None, stream=None):
     Tensors are column-major views (``t.T`` of a row-major (cols, ld) tensor)."""
     k = (Q.shape[1] if Q is not None else 0) if k is None else k
     return check(_ortho(load().ortho_stage1, Q, V, R, work, status, k, stream))
+
+
+def ortho_stage1_shifted(Q, V, R, work, status, k=None, stream=None):
+    """Stage 1 with the shifted Cholesky of shifted CholQR: T = Chol(G - P^T P +
+    sigma I), sigma = 11 (n nb + nb (nb + 1)) u trace(G); FP64 arithmetic."""
+    k = (Q.shape[1] if Q is not None else 0) if k is None else k
+    return check(_ortho(load().ortho_stage1_shifted, Q, V, R, work, status, k, stream))
 
 
 def ortho_stage1_f32(Q, V, R, work, status, k=None, stream=None):

@@ -45,6 +45,7 @@ struct PipStatus {
 // Mode bits of the BCGS-PIP launchers.
 constexpr int kPipGramOnly = 1;   // Gram kernel: write [P; G] (upper G), no Cholesky, status 0
 constexpr int kPipNoTrsm = 2;     // update kernel: V <- V - Q P only (T taken as the identity)
+constexpr int kPipShift = 4;      // Gram kernel: factor G - P^T P + sigma I (shifted CholQR, see pip_finish)
 
 // Arithmetic of the Gram and update kernels (gmres_opts.arith).
 constexpr int kArithFP64 = 0;     // native FP64 pipe (default)
@@ -84,7 +85,8 @@ cudaError_t launch_pip_update(cudaStream_t st, int64_t n,
 // and X must start on 16-byte boundaries; k + nb <= 64.
 cudaError_t launch_gram_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, const double* V,
                                   int64_t ldv, int nb, double* R, int ldr, const PipWork& w, int32_t* d_status,
-                                  int grid, const void* digits, int capc, int kc, int32_t* d_skip = nullptr);
+                                  int grid, const void* digits, int capc, int kc, int32_t* d_skip = nullptr,
+                                  int mode = 0);
 cudaError_t launch_update_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, double* V,
                                     int64_t ldv, int nb, const double* R, int ldr, const int32_t* d_status,
                                     void* digits, int capc, const int32_t* d_skip = nullptr);

@@ -44,7 +44,7 @@ gram_skinny_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, int k,
     const size_t ps = (size_t)kMaxNB * NB;
     double* partial0 = partial + (size_t)g * G * ps;
     gram_skinny_part<T, NB>(n, Q, ldq, k, V, ldv, g, blockIdx.x, G, partial0 + blockIdx.x * ps, smem);
-    pip_finish(k, NB, g, gridDim.y, G, R, ldr, partial0, ps, counter, gram, d_status, d_skip, smem, mode);
+    pip_finish(k, NB, g, gridDim.y, G, R, ldr, partial0, ps, counter, gram, d_status, d_skip, smem, mode, n);
 }
 
 template <typename T>
@@ -59,7 +59,7 @@ gram_wide_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, int k,
     const size_t ps = (size_t)kMaxNB * nb;
     double* partial0 = partial + (size_t)g * G * ps;
     gram_wide_part<T>(n, Q, ldq, k, V, ldv, nb, g, blockIdx.x, G, partial0 + blockIdx.x * ps, smem);
-    pip_finish(k, nb, g, gridDim.y, G, R, ldr, partial0, ps, counter, gram, d_status, d_skip, smem, mode);
+    pip_finish(k, nb, g, gridDim.y, G, R, ldr, partial0, ps, counter, gram, d_status, d_skip, smem, mode, n);
 }
 
 // Exact-slice tensor-core Gram (gram_tc.cuh), k + nb <= 64: one column group.
@@ -74,7 +74,7 @@ gram_tc_kernel(int64_t n, const double* __restrict__ Q, int64_t ldq, int k,
     const int G = gridDim.x;
     const size_t ps = (size_t)kMaxNB * nb;
     gram_tc_part(n, Q, ldq, k, V, ldv, nb, blockIdx.x, G, partial + blockIdx.x * ps, smem, dig, dex, capc, kc);
-    pip_finish(k, nb, 0, 1, G, R, ldr, partial, ps, counter, gram, d_status, d_skip, smem, mode);
+    pip_finish(k, nb, 0, 1, G, R, ldr, partial, ps, counter, gram, d_status, d_skip, smem, mode, n);
 }
 
 // Narrow Gram with every Q column from the digit basis (gram_tcq.cuh): one CTA
@@ -89,7 +89,7 @@ gram_tcq_kernel(int64_t n, const double* __restrict__ V, int64_t ldv, int k, int
     const size_t ps = (size_t)kMaxNB * nb;
     gram_tcq_part(n, V, ldv, k, nb, blockIdx.x, G, partial + blockIdx.x * ps, gq_smem, dig, dex, capc);
     pip_finish(k, nb, 0, 1, G, R, ldr, partial, ps, counter, gram, d_status, d_skip,
-               reinterpret_cast<double*>(gq_smem), mode);
+               reinterpret_cast<double*>(gq_smem), mode, n);
 }
 
 cudaError_t launch_gram_tcq(cudaStream_t st, int64_t n, int k, const double* V, int64_t ldv, int nb, double* R,
@@ -274,7 +274,7 @@ gram_skinny_df_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, int k,
     const size_t ps = (size_t)kMaxNB * NB;
     double* partial0 = partial + (size_t)g * G * ps;
     gram_skinny_part_df<T, NB>(n, Q, ldq, k, V, ldv, g, blockIdx.x, G, partial0 + blockIdx.x * ps, smem);
-    pip_finish(k, NB, g, gridDim.y, G, R, ldr, partial0, ps, counter, gram, d_status, d_skip, smem, mode);
+    pip_finish(k, NB, g, gridDim.y, G, R, ldr, partial0, ps, counter, gram, d_status, d_skip, smem, mode, n);
 }
 
 template <typename T>
@@ -289,7 +289,7 @@ gram_wide_df_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, int k,
     const size_t ps = (size_t)kMaxNB * nb;
     double* partial0 = partial + (size_t)g * G * ps;
     gram_wide_part_df<T>(n, Q, ldq, k, V, ldv, nb, g, blockIdx.x, G, partial0 + blockIdx.x * ps, smem);
-    pip_finish(k, nb, g, gridDim.y, G, R, ldr, partial0, ps, counter, gram, d_status, d_skip, smem, mode);
+    pip_finish(k, nb, g, gridDim.y, G, R, ldr, partial0, ps, counter, gram, d_status, d_skip, smem, mode, n);
 }
 
 // Double-float update, nb <= 16: W = [-P T^{-1}; T^{-1}] staged pre-split, one thread per row.
@@ -496,11 +496,11 @@ cudaError_t launch_pip_update(cudaStream_t st, int64_t n, const float* Q, int64_
 // Tensor-core halves with a digit basis (entry points ortho_*_tcd, ortho_digits_fill).
 cudaError_t launch_gram_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, const double* V,
                                   int64_t ldv, int nb, double* R, int ldr, const PipWork& w, int32_t* d_status,
-                                  int grid, const void* digits, int capc, int kc, int32_t* d_skip) {
+                                  int grid, const void* digits, int capc, int kc, int32_t* d_skip, int mode) {
     // narrow blocks against a Q held entirely in the digit basis: per-warp streaming
     if (nb <= kGqMaxNB && kc == k && k + nb <= kGqMaxKX)
-        return launch_gram_tcq(st, n, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, 0, digits, capc);
-    return launch_gram_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, 0, digits, capc, kc);
+        return launch_gram_tcq(st, n, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode, digits, capc);
+    return launch_gram_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode, digits, capc, kc);
 }
 cudaError_t launch_update_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, double* V,
                                     int64_t ldv, int nb, const double* R, int ldr, const int32_t* d_status,

@@ -178,10 +178,14 @@ __device__ void gram_wide_part(int64_t n, const T* __restrict__ Q, int64_t ldq, 
 // that completes the group sums its G slots (partial0 + b * ps, b = 0..G-1) in
 // order into `gram`; the last group to complete forms S = G - P^T P and factors
 // it (kernel (d)), or, with kPipGramOnly, writes [P; G] unfactored.  R = [P; T].
+// With kPipShift the factored matrix is G - P^T P + sigma I, the shift of
+// shifted CholQR (Fukaya, Kannan, Nakatsukasa, Zhang and Yamamoto, 2020; §II):
+// sigma = 11 (nrows nb + nb (nb + 1)) u trace(G), u = 2^-53, where trace(G) =
+// ||V||_F^2 bounds the block's squared 2-norm from above.
 // counter holds groups + 1 arrival counters; every counter is re-armed to zero.
 __device__ inline void pip_finish(int k, int nb, int g, int groups, int G, double* R, int ldr,
                                   const double* partial0, size_t ps, unsigned* counter, double* gram,
-                                  int32_t* d_status, int32_t* d_skip, double* smem, int mode) {
+                                  int32_t* d_status, int32_t* d_skip, double* smem, int mode, int64_t nrows = 0) {
     __shared__ unsigned s_ticket;
     __shared__ int s_info;
     __shared__ double s_inv;
@@ -254,6 +258,15 @@ __device__ inline void pip_finish(int k, int nb, int g, int groups, int G, doubl
     }
     if (tid == 0) s_info = 0;
     __syncthreads();
+    if (mode & kPipShift) {
+        if (tid == 0) {
+            double tr = 0.0;
+            for (int j = 0; j < nb; ++j) tr += __ldcg(gram + (k + j) + (size_t)j * kx);
+            const double sig = 11.0 * ((double)nrows * nb + (double)nb * (nb + 1)) * 0x1p-53 * tr;
+            for (int j = 0; j < nb; ++j) S[j + j * kSLd] += sig;
+        }
+        __syncthreads();
+    }
 
     // right-looking Cholesky S = T^T T in shared memory (kernel (d))
     for (int j = 0; j < nb; ++j) {

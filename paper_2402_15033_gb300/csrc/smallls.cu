@@ -27,6 +27,11 @@ __global__ void __launch_bounds__(256) bcgs2_combine_kernel(const DevState* st, 
 
 __global__ void __launch_bounds__(256) eye_panel_kernel(DevState* st, int lo, int t) { eye_panel_body(st, lo, t); }
 
+__global__ void __launch_bounds__(256) pip3_combine_kernel(DevState* st, int lo, int t, const double* Sb,
+                                                           const double* Sc, double* Su, double* Sp) {
+    pip3_combine_body(st, lo, t, Sb, Sc, Su, Sp);
+}
+
 }  // namespace
 
 cudaError_t launch_cycle_begin(cudaStream_t st, DevState* ds, const CycleBasis& cb) {
@@ -43,6 +48,13 @@ cudaError_t launch_hessenberg_ls(cudaStream_t st, DevState* ds, int lo, int t) {
 
 cudaError_t launch_bcgs2_combine(cudaStream_t st, const DevState* ds, int k, int s, const double* S, double* R) {
     bcgs2_combine_kernel<<<1, 256, 0, st>>>(ds, k, s, S, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pip3_combine(cudaStream_t st, DevState* ds, int lo, int t, const double* S) {
+    const size_t SB = (size_t)kLsLd * kLsLd;
+    pip3_combine_kernel<<<1, 256, 0, st>>>(ds, lo, t, S, S + SB, const_cast<double*>(S) + 2 * SB,
+                                           const_cast<double*>(S) + 3 * SB);
     return cudaGetLastError();
 }
 

@@ -242,6 +242,52 @@ __device__ inline void bcgs2_combine_body(const DevState* st, int k, int s, cons
     }
 }
 
+// Stage-2 factor of a big panel orthogonalized by three passes (shifted
+// CholQR3: a shifted BCGS-PIP, then two plain ones, against the finished
+// columns 0 .. lo-1).  Pass a left [P_a; T_a] in Cm(:, lo..t); passes b and c
+// left [P_b; T_b] and [P_c; T_c] in Sb and Sc (same layout, ld kLsLd: rows
+// 0..lo-1 the projection, rows lo..t the triangular factor).  Since
+// Q^ = Q_fin P_a + Q_a T_a, Q_a = Q_fin P_b + Q_b T_b, Q_b = Q_fin P_c + Q T_c:
+//     Cm(:, lo..t) <- [P_a + P_b T_a + P_c T_b T_a; T_c T_b T_a].
+// U = T_b T_a and P_ab = P_a + P_b T_a go through Su and Sp.
+__device__ inline void pip3_combine_body(DevState* st, int lo, int t, const double* Sb, const double* Sc, double* Su,
+                                         double* Sp) {
+    if (st->done) return;
+    const int np = t - lo + 1, tid = threadIdx.x;
+    double* Cm = st->Cm;
+    auto Ta = [&](int i, int j) { return Cm[(lo + i) + (size_t)(lo + j) * kLsLd]; };
+    for (int e = tid; e < (lo + np) * np; e += blockDim.x) {
+        const int i = e % (lo + np), j = e / (lo + np);
+        double acc;
+        if (i < lo) {           // P_ab = P_a + P_b T_a
+            acc = Cm[i + (size_t)(lo + j) * kLsLd];
+            for (int l = 0; l <= j; ++l) acc = fma(Sb[i + (size_t)(lo + l) * kLsLd], Ta(l, j), acc);
+            Sp[i + (size_t)j * kLsLd] = acc;
+        } else {                // U = T_b T_a (upper triangular)
+            const int ii = i - lo;
+            acc = 0.0;
+            for (int l = ii; l <= j; ++l) acc = fma(Sb[(lo + ii) + (size_t)(lo + l) * kLsLd], Ta(l, j), acc);
+            Su[ii + (size_t)j * kLsLd] = ii <= j ? acc : 0.0;
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < (lo + np) * np; e += blockDim.x) {
+        const int i = e % (lo + np), j = e / (lo + np);
+        double acc;
+        if (i < lo) {           // P = P_ab + P_c U
+            acc = Sp[i + (size_t)j * kLsLd];
+            for (int l = 0; l <= j; ++l) acc = fma(Sc[i + (size_t)(lo + l) * kLsLd], Su[l + (size_t)j * kLsLd], acc);
+        } else {                // T = T_c U
+            const int ii = i - lo;
+            acc = 0.0;
+            for (int l = ii; l <= j; ++l)
+                acc = fma(Sc[(lo + ii) + (size_t)(lo + l) * kLsLd], Su[l + (size_t)j * kLsLd], acc);
+            if (ii > j) acc = 0.0;
+        }
+        Cm[i + (size_t)(lo + j) * kLsLd] = acc;
+    }
+}
+
 // Stage-2 factor of a one-stage scheme whose blocks come out final: the
 // identity on the panel's columns [lo, t] (no projection part).
 __device__ inline void eye_panel_body(DevState* st, int lo, int t) {

@@ -214,6 +214,9 @@ static int check_opts(const gmres_opts* o) {
     GM_ARG(o->sigma >= 0.0 && std::isfinite(o->sigma), "sigma must be >= 0");
     GM_ARG(o->arith == GMRES_ARITH_DD || o->arith == GMRES_ARITH_FP64 || o->arith == GMRES_ARITH_TC,
            "unknown arith");
+    GM_ARG(o->shift == GMRES_SHIFT_NONE || o->shift == GMRES_SHIFT_CHOLQR3, "unknown shift");
+    GM_ARG(o->shift == GMRES_SHIFT_NONE || (o->precision == GMRES_PREC_FP64 && o->ortho != GMRES_ORTHO_BCGS2_CHOLQR2),
+           "shifted CholQR needs an FP64 basis and the two-stage or BCGS-PIP2 scheme");
     return GMRES_OK;
 }
 
@@ -369,7 +372,9 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
         CK(cuda_rc(cudaMalloc(&c->digits, db), "cudaMalloc digit basis"));
         CK(cuda_rc(cudaMemsetAsync(c->digits, 0, db, s), "memset digit basis"));
     }
-    if (o.ortho == GMRES_ORTHO_BCGS2_CHOLQR2) {
+    if (o.ortho == GMRES_ORTHO_BCGS2_CHOLQR2 || o.shift != GMRES_SHIFT_NONE) {
+        // BCGS2-CholQR2: the five reductions' factors; shifted CholQR3: the
+        // second and third stage-2 passes' factors and two combine blocks
         const size_t sb = 5 * (size_t)kMaxCols * kMaxCols * sizeof(double);
         CK(cuda_rc(cudaMalloc(&c->bscr, sb), "cudaMalloc bcgs2 scratch"));
         CK(cuda_rc(cudaMemsetAsync(c->bscr, 0, sb, s), "memset bcgs2 scratch"));
@@ -413,6 +418,8 @@ static int run_cycle(gmres_ctx* c, const CycleBasis& cb, std::vector<std::pair<i
     };
     const int nblk = o.m / cb.s;
     int panel_idx = 0;
+    const bool shifted = o.shift != GMRES_SHIFT_NONE;
+    const int s1mode = shifted ? kPipShift : 0;   // stage 1: shifted Cholesky (§II)
     cudaError_t e = launch_cycle_begin(s, ds, cb);
     if (e == cudaSuccess) e = launch_scale(s, c->n, c->r ? c->r : static_cast<double*>(c->basis), basis, ds);
     const int capc = o.m + 1;
@@ -463,14 +470,14 @@ static int run_cycle(gmres_ctx* c, const CycleBasis& cb, std::vector<std::pair<i
                 // digits read from the digit basis, the block's written back
                 const double* Bd = reinterpret_cast<const double*>(basis);
                 e = launch_gram_tc_digits(s, c->n, Bd, c->ldq, k, reinterpret_cast<const double*>(V), c->ldq, cb.s, R,
-                                          kMaxCols, w, stat, reduction_grid(c->n), dig, capc, k, done);
+                                          kMaxCols, w, stat, reduction_grid(c->n), dig, capc, k, done, s1mode);
                 if (e == cudaSuccess)
                     e = launch_update_tc_digits(s, c->n, Bd, c->ldq, k, reinterpret_cast<double*>(V), c->ldq, cb.s, R,
                                                 kMaxCols, stat, dig, capc, done);
             } else if (sizeof(T) == sizeof(double)) {
                 // BCGS-PIP (Fig. 4a): one reduction, Pythagorean Gram
                 e = launch_pip_gram_chol(s, c->n, basis, c->ldq, k, V, c->ldq, cb.s, R, kMaxCols, w, stat, done,
-                                         reduction_grid(c->n), 0, o.arith);
+                                         reduction_grid(c->n), s1mode, o.arith);
                 if (e == cudaSuccess)
                     e = launch_pip_update(s, c->n, basis, c->ldq, k, V, c->ldq, cb.s, R, kMaxCols, stat, done, 0,
                                           o.arith);
@@ -506,6 +513,23 @@ static int run_cycle(gmres_ctx* c, const CycleBasis& cb, std::vector<std::pair<i
             if (o.ortho == GMRES_ORTHO_BCGS2_CHOLQR2) {
                 // the block is final after its five reductions: identity stage-2 factor
                 if (e == cudaSuccess) e = launch_eye_panel(s, ds, lo, t);
+            } else if (shifted) {
+                // shifted CholQR3 of the big panel (§II): a shifted BCGS-PIP into Cm,
+                // then two plain ones into scratch, and the product of the factors.
+                // The passes read the basis itself; the final panel's digits are
+                // refilled for the blocks after it
+                const size_t SB = (size_t)kMaxCols * kMaxCols;
+                double* Rq[3] = {R, c->bscr + lo * kMaxCols, c->bscr + SB + lo * kMaxCols};
+                for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
+                    e = launch_pip_gram_chol(s, c->n, basis, c->ldq, lo, V, c->ldq, np, Rq[q], kMaxCols, w, stat, done,
+                                             reduction_grid(c->n), q == 0 ? kPipShift : 0, o.arith);
+                    if (e == cudaSuccess)
+                        e = launch_pip_update(s, c->n, basis, c->ldq, lo, V, c->ldq, np, Rq[q], kMaxCols, stat, done, 0,
+                                              o.arith);
+                }
+                if (e == cudaSuccess) e = launch_pip3_combine(s, ds, lo, t, c->bscr);
+                if (e == cudaSuccess && dig && t < o.m)
+                    e = launch_digits_fill_cols(s, c->n, reinterpret_cast<const double*>(V), c->ldq, lo, np, dig, capc);
             } else if (dig) {
                 // every column 0 .. t is in the digit basis; the panel's final
                 // columns are written back for the panels and blocks after it
@@ -965,6 +989,23 @@ int ortho_stage1(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t 
 int ortho_stage2(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V, int64_t ldv,
                  int32_t nb, double* R, int32_t ldr, void* d_work, size_t work_bytes, int32_t* d_status) {
     return ortho_pip(stream, n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status);
+}
+
+int ortho_stage1_shifted(void* stream, int64_t n, const double* Q, int64_t ldq, int32_t k, double* V,
+                         int64_t ldv, int32_t nb, double* R, int32_t ldr, void* d_work, size_t work_bytes,
+                         int32_t* d_status) {
+    clear_error();
+    int code = GMRES_OK;
+    if (check_pip_args(n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status, &code)) return code;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PipWork w = pip_work_layout(d_work, n, k, nb);
+    cudaError_t e = cudaMemsetAsync(w.counter, 0, 256, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess)
+        e = launch_pip_gram_chol(s, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, nullptr, reduction_grid(n),
+                                 kPipShift, kArithFP64);
+    if (e == cudaSuccess) e = launch_pip_update(s, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, nullptr);
+    return cuda_rc(e, "ortho launch");
 }
 
 int ortho_stage1_f32(void* stream, int64_t n, const float* Q, int64_t ldq, int32_t k, float* V, int64_t ldv,

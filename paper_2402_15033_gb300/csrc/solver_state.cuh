@@ -78,5 +78,8 @@ cudaError_t launch_hessenberg_ls(cudaStream_t st, DevState* ds, int lo, int t);
 cudaError_t launch_bcgs2_combine(cudaStream_t st, const DevState* ds, int k, int s, const double* S, double* R);
 // identity stage-2 factor on the panel [lo, t] (one-stage schemes)
 cudaError_t launch_eye_panel(cudaStream_t st, DevState* ds, int lo, int t);
+// Stage-2 factor of a three-pass (shifted CholQR3) panel: S holds four
+// kMaxCols^2 blocks (passes b and c, then two scratch blocks).
+cudaError_t launch_pip3_combine(cudaStream_t st, DevState* ds, int lo, int t, const double* S);
 
 }  // namespace gm

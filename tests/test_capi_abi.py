@@ -45,11 +45,12 @@ def test_struct_layouts_match_the_header(capi):
     assert capi.gmres_opts.tol.offset == 16
     assert capi.gmres_opts.theta.offset == 48
     assert capi.gmres_result.relres_implicit.offset == 24
+    assert capi.gmres_opts.shift.offset == capi.gmres_opts.arith.offset + 4
 
 
 def test_default_opts(capi):
     o = capi.default_opts()
-    assert (o.m, o.s, o.panel, o.tol, o.ortho, o.precision) == (60, 5, 60, 1e-8, 0, 0)
+    assert (o.m, o.s, o.panel, o.tol, o.ortho, o.precision, o.shift) == (60, 5, 60, 1e-8, 0, 0, 0)
 
 
 def test_workspace_size_is_positive_and_monotone(capi):
@@ -91,6 +92,13 @@ def test_bad_arguments_are_rejected_before_any_launch(capi):
     rc = lib.gmres_create(C.byref(h), 1, 1, rp.ctypes.data_as(C.c_void_p), ci.ctypes.data_as(C.c_void_p),
                           vv.ctypes.data_as(C.c_void_p), 0, C.byref(o), None)
     assert rc == capi.GMRES_ERR_ARG and "panel" in capi.last_error()
+    # shifted CholQR: a known shift, FP64 basis, not the five-reduction scheme
+    for bad in (dict(shift=2), dict(shift=1, precision=capi.GMRES_PREC_MIXED),
+                dict(shift=1, ortho=capi.GMRES_ORTHO_BCGS2_CHOLQR2, panel=5)):
+        o = capi.default_opts(**bad)
+        rc = lib.gmres_create(C.byref(h), 1, 1, rp.ctypes.data_as(C.c_void_p), ci.ctypes.data_as(C.c_void_p),
+                              vv.ctypes.data_as(C.c_void_p), 0, C.byref(o), None)
+        assert rc == capi.GMRES_ERR_ARG and "shift" in capi.last_error(), bad
     assert lib.gmres_destroy(None) == capi.GMRES_OK
 
 
