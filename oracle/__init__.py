@@ -20,5 +20,6 @@ Modules
 ``krylov``      MPK, Givens least squares, Hessenberg recovery, standard
                 GMRES with CGS2, s-step GMRES with the three block schemes.
 ``checks``      orthogonality error, condition number, exact dot products.
+``precond``     multicolor Gauss-Seidel (greedy coloring, forward sweep).
 """
-from . import blockortho, krylov, checks  # noqa: F401
+from . import blockortho, krylov, checks, precond  # noqa: F401

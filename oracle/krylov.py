@@ -54,16 +54,18 @@ def mpk_sigma(A) -> float:
     return float(2.0 ** math.floor(math.log2(top)))
 
 
-def mpk(M, v: np.ndarray, s: int, sigma: float, theta=None) -> np.ndarray:
+def mpk(M, v: np.ndarray, s: int, sigma: float, theta=None, minv=None) -> np.ndarray:
     """Matrix powers kernel, standard (non communication-avoiding) form (§III):
     s sparse matrix-vector products in sequence, w_1 = (A v - theta_0 v)/sigma,
-    w_i = (A w_{i-1} - theta_{i-1} w_{i-1})/sigma.  Returns the n x s block."""
+    w_i = (A w_{i-1} - theta_{i-1} w_{i-1})/sigma.  With a right
+    preconditioner (``minv`` applies M^{-1}) each product is A M^{-1} w (the
+    preconditioner applied with every SpMV, §I).  Returns the n x s block."""
     n = v.shape[0]
     dt = v.dtype
     W = np.zeros((n, s), dtype=dt)
     prev = v
     for i in range(s):
-        y = M @ prev
+        y = M @ (prev if minv is None else minv(prev))
         if theta is not None and theta[i] != 0.0:
             y = y - dt.type(theta[i]) * prev
         W[:, i] = y / dt.type(sigma)
@@ -257,7 +259,7 @@ def newton_sigma(theta, fallback: float) -> float:
 
 def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=1000,
                 ortho="two_stage", sigma=None, theta=None, return_basis=False, basis_dtype=np.float64,
-                shift=False):
+                shift=False, precond=None):
     """s-step GMRES (Fig. 1, §III) with the chosen block orthogonalization.
 
     ``panel`` is the second step size s^ of the two-stage scheme (§V); it must
@@ -266,6 +268,10 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
     same block machinery), ``newton_shifts`` turns its Hessenberg matrix into s
     shifts, and every later cycle uses the Newton basis with them, scaled by
     ``newton_sigma`` unless ``sigma`` is given.  ``ortho`` in {"two_stage", "bcgs_pip2", "bcgs2_cholqr2"}.
+    ``precond="mcgs"`` (FP64 basis) preconditions from the right with one
+    forward multicolor Gauss-Seidel sweep (``oracle.precond``, the local
+    Gauss-Seidel of §VIII, Fig. 9): the MPK applies A M^{-1}, the correction is
+    x += M^{-1} Q y, and the MPK scale is 1 unless ``sigma`` is given.
     ``shift=True`` (two-stage, FP64 basis) runs stage 1 with the shifted
     Cholesky of ``blockortho.stage1_shifted`` and stage 2 as shifted CholQR3
     of the big panel (``blockortho.stage2_shifted``).
@@ -302,7 +308,14 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
     if m % s or panel % s or m % panel:
         raise ValueError("need s | panel | m")
     panel_req = panel
-    sig = mpk_sigma(A) if sigma is None else float(sigma)
+    minv = None
+    if precond is not None:
+        if precond != "mcgs" or lowp:
+            raise ValueError("precond must be 'mcgs' (FP64 basis)")
+        from . import precond as pc
+        colors = pc.greedy_coloring(M)
+        minv = lambda v: pc.gs_sweep(M, colors, v)  # noqa: E731
+    sig = (1.0 if minv is not None else mpk_sigma(A)) if sigma is None else float(sigma)
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     bnorm = np.linalg.norm(b)
     iters = 0
@@ -356,7 +369,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
                 where_blk = j
                 st = s * j
                 start_final[st] = final[st]
-                W = mpk(Mb, Q[:, st], s, sig, th)
+                W = mpk(Mb, Q[:, st], s, sig, th, minv)
                 cols = slice(st + 1, st + s + 1)
                 if ortho == "two_stage":
                     st1 = bo.stage1_lowp if lowp else (bo.stage1_shifted if shift else bo.stage1)
@@ -404,7 +417,8 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
             breakdown = (where_blk, e.pivot, e.value, e.margin)
             break
         y = gv.solve()
-        x = x + Q[:, :k_used].astype(f64) @ y
+        dx = Q[:, :k_used].astype(f64) @ y
+        x = x + (dx if minv is None else minv(dx))
         iters += k_used
         last = dict(Q=Q, H=H, g0=beta * C[0, 0], k=k_used, Rfin=Rfin, C=C)
         if auto and th is None:

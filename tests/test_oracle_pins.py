@@ -271,6 +271,104 @@ def test_shifted_sstep_gmres_solves_where_the_monomial_basis_breaks_down():
     assert np.linalg.norm(x - xt) / np.linalg.norm(xt) <= (hi / lo) * 1e-8
 
 
+# ---------------------------------------------------------------- multicolor Gauss-Seidel (§VIII, Fig. 9)
+def test_greedy_coloring_of_the_grid_stencils_is_red_black():
+    """Greedy coloring in natural order of the 5-point (7-point) stencil on a
+    lexicographic grid is the red-black coloring (i + j (+ k)) mod 2."""
+    from oracle import precond as pc
+    N = 9
+    c2 = pc.greedy_coloring(synth.laplace2d(N))
+    i, j = np.divmod(np.arange(N * N), N)
+    assert np.array_equal(c2, (i + j) % 2)
+    c3 = pc.greedy_coloring(synth.laplace3d(5))
+    a, rem = np.divmod(np.arange(125), 25)
+    b, c = np.divmod(rem, 5)
+    assert np.array_equal(c3, (a + b + c) % 2)
+
+
+def test_greedy_coloring_is_proper_and_greedy():
+    """No two coupled rows share a color (either triangle of the pattern), and
+    every row's color is the smallest one its earlier neighbors leave free."""
+    from oracle import precond as pc
+    A = synth.banded_random(400, 3, band=30)
+    M = kr.as_operator(A)
+    col = pc.greedy_coloring(A)
+    S = (abs(M) + abs(M).T).tocoo()
+    off = S.row != S.col
+    assert not np.any(col[S.row[off]] == col[S.col[off]])
+    Sc = S.tocsr()
+    for r in range(A.n):
+        nb = Sc.indices[Sc.indptr[r]:Sc.indptr[r + 1]]
+        earlier = {int(col[q]) for q in nb if q < r}
+        assert all(cc in earlier for cc in range(col[r])) and col[r] not in earlier
+
+
+def test_gs_sweep_is_the_lower_triangular_solve_in_color_order():
+    """z = (D + L)^{-1} r of the matrix permuted to color order (scipy's sparse
+    triangular solve), on a nonsymmetric matrix with many colors."""
+    from scipy.sparse.linalg import spsolve_triangular
+    from oracle import precond as pc
+    A = synth.banded_random(500, 4, band=40)
+    M = kr.as_operator(A)
+    col = pc.greedy_coloring(A)
+    r = synth.x_true(A.n, 3)
+    z = pc.gs_sweep(A, col, r)
+    perm = np.lexsort((np.arange(A.n), col))
+    Mp = M[perm][:, perm].tocsr()
+    zp = spsolve_triangular(sp_tril(Mp), r[perm], lower=True)
+    assert np.allclose(z[perm], zp, rtol=1e-13, atol=1e-13 * np.abs(zp).max())
+
+
+def sp_tril(M):
+    import scipy.sparse as sp
+    return sp.tril(M, format="csr")
+
+
+def test_gs_sweep_on_the_red_black_laplacian_by_hand():
+    """Red rows: z = r / 4; black rows: z = (r + sum of the red neighbors' z) / 4
+    (the 5-point stencil's off-diagonals are -1)."""
+    from oracle import precond as pc
+    N = 7
+    A = synth.laplace2d(N)
+    col = pc.greedy_coloring(A)
+    r = synth.x_true(A.n, 4)
+    z = pc.gs_sweep(A, col, r)
+    zr = np.where(col == 0, r / 4.0, 0.0)
+    ref = zr.copy()
+    for q in np.nonzero(col == 1)[0]:
+        i, j = divmod(int(q), N)
+        s_ = sum(zr[a * N + b] for a, b in ((i - 1, j), (i + 1, j), (i, j - 1), (i, j + 1)) if 0 <= a < N and 0 <= b < N)
+        ref[q] = (r[q] + s_) / 4.0
+    assert np.allclose(z, ref, rtol=1e-15, atol=1e-15)
+
+
+def test_preconditioned_cycle_is_the_minimal_residual_iterate():
+    """One restart cycle with the right preconditioner returns the x that
+    minimizes ||b - A x|| over x0 + M^{-1} K_m(A M^{-1}, r0) (brute force:
+    dense A M^{-1} from the sweep applied to the identity, power vectors, QR,
+    least squares), for the two-stage and BCGS-PIP2 schemes."""
+    from oracle import precond as pc
+    A = synth.convdiff2d(7, 5)
+    M = kr.as_operator(A).toarray()
+    n = A.n
+    col = pc.greedy_coloring(A)
+    Minv = np.column_stack([pc.gs_sweep(A, col, e) for e in np.eye(n)])
+    b = M @ synth.x_true(n, 1)
+    m = 6
+    K = np.zeros((n, m))
+    v = b / np.linalg.norm(b)
+    for i in range(m):
+        K[:, i] = v
+        v = M @ (Minv @ v)
+    Z = Minv @ np.linalg.qr(K)[0]
+    y, *_ = np.linalg.lstsq(M @ Z, b, rcond=None)
+    x_ref = Z @ y
+    for ortho, panel in (("two_stage", 6), ("bcgs_pip2", 3)):
+        x, info = kr.sstep_gmres(A, b, m=m, s=3, panel=panel, tol=1e-30, max_restarts=1, ortho=ortho,
+                                 precond="mcgs")
+        assert np.allclose(x, x_ref, rtol=1e-9, atol=1e-10 * np.abs(x_ref).max()), ortho
+
+
 # ---------------------------------------------------------------- least squares and Hessenberg
 def test_givens_solves_the_hessenberg_least_squares():
     g = synth.rng(19)
