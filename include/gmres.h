@@ -92,6 +92,18 @@ extern "C" {
                                       /* basis, two-stage or BCGS-PIP2 ortho, any arithmetic; not in the  */
                                       /* batched engine.  The paper has no measurement of it.           */
 
+#define GMRES_PRECOND_NONE         0  /* no preconditioner (default)                                 */
+#define GMRES_PRECOND_MCGS         1  /* multicolor Gauss-Seidel (§VIII, Fig. 9), from the right: the  */
+                                      /* MPK applies A M^{-1} and the correction is x += M^{-1} Q y,    */
+                                      /* M^{-1} one forward Gauss-Seidel sweep from zero over the rows  */
+                                      /* grouped by a greedy distance-1 coloring of the symmetrized     */
+                                      /* pattern in natural row order (red-black on the grid stencils),  */
+                                      /* colors in increasing order.  The rows need nonzero diagonals.   */
+                                      /* The MPK scale defaults to 1 (sigma = 0).  A M^{-1} has many     */
+                                      /* eigenvalues at or near 1, so the monomial basis loses rank fast: */
+                                      /* use it with GMRES_BASIS_NEWTON_AUTO.  FP64 basis; not in the    */
+                                      /* batched engine; gmres_mpk stays unpreconditioned.              */
+
 typedef struct gmres_opts {
     int32_t m;             /* restart length: m+1 basis vectors per cycle (Table 1)            */
     int32_t s;             /* step size of the first stage (Table 1), 1 <= s <= 16            */
@@ -108,7 +120,8 @@ typedef struct gmres_opts {
     int32_t max_ir;        /* mixed precision: maximum FP64 refinement steps                   */
     int32_t arith;         /* GMRES_ARITH_*: arithmetic of the Gram and block-update kernels   */
     int32_t shift;         /* GMRES_SHIFT_*: shifted CholQR in the two-stage scheme             */
-    int32_t reserved[5];
+    int32_t precond;       /* GMRES_PRECOND_*: right preconditioner applied inside the MPK     */
+    int32_t reserved[4];
 } gmres_opts;
 
 typedef struct gmres_result {
@@ -396,6 +409,13 @@ int gmres_server_get_stats(gmres_server* s, gmres_server_stats* st);
 /* Serves every queued and running request to completion, then joins the
  * worker and frees the server (results not collected are dropped). */
 int gmres_server_stop(gmres_server* s);
+
+/* z = M^{-1} r for the context's preconditioner (opts.precond = GMRES_PRECOND_MCGS):
+ * one forward multicolor Gauss-Seidel sweep from zero (§VIII, Fig. 9; the
+ * coloring and order of GMRES_PRECOND_MCGS).  r and z are n FP64 values in
+ * device memory, distinct; synchronizes the context's stream.  GMRES_ERR_ARG
+ * when the context has no preconditioner. */
+int gmres_precond_apply(gmres_ctx* c, const double* r, double* z);
 
 /* ------------------------------------------------ matrix powers kernel
  * MPK of §III (standard, not communication-avoiding): s products in sequence,

@@ -38,6 +38,8 @@ GMRES_ARITH_DD = 1
 GMRES_ARITH_TC = 2
 GMRES_SHIFT_NONE = 0
 GMRES_SHIFT_CHOLQR3 = 1
+GMRES_PRECOND_NONE = 0
+GMRES_PRECOND_MCGS = 1
 
 
 class gmres_opts(C.Structure):
@@ -45,7 +47,7 @@ class gmres_opts(C.Structure):
                 ("tol", C.c_double), ("sigma", C.c_double),
                 ("ortho", C.c_int32), ("precision", C.c_int32), ("basis", C.c_int32), ("timing", C.c_int32),
                 ("theta", C.c_double * 16), ("inner_tol", C.c_double), ("max_ir", C.c_int32),
-                ("arith", C.c_int32), ("shift", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("arith", C.c_int32), ("shift", C.c_int32), ("precond", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class gmres_server_stats(C.Structure):
@@ -85,6 +87,7 @@ SIGNATURES = {
     "ortho_workspace_bytes": (_sz, [_i64, _i32, _i32]),
     "ortho_stage1": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "ortho_stage1_shifted": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
+    "gmres_precond_apply": (_i32, [_vp, _vp, _vp]),
     "ortho_stage2": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "gmres_mpk": (_i32, [_vp, _vp, _vp, _i64, _i32, _dbl, C.POINTER(_dbl)]),
     "ortho_gram_chol": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
@@ -224,6 +227,10 @@ class Solver:
         out = res.as_dict()
         out["error"] = last_error() if rc < 0 else ""
         return rc, out
+
+    def precond_apply(self, r, z):
+        """z = M^{-1} r (device tensors of n FP64 values) for the context's preconditioner."""
+        return check(load().gmres_precond_apply(self.h, _ptr(r), _ptr(z)))
 
     def mpk(self, v, W, s, sigma, theta=None):
         lib = load()

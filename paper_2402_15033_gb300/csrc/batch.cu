@@ -513,6 +513,7 @@ static int check_batch_opts(const gmres_opts& o) {
     GM_ARG(o.ortho == GMRES_ORTHO_TWO_STAGE || o.ortho == GMRES_ORTHO_BCGS_PIP2,
            "ortho must be GMRES_ORTHO_TWO_STAGE or GMRES_ORTHO_BCGS_PIP2 for batches");
     GM_ARG(o.shift == GMRES_SHIFT_NONE, "shifted CholQR (opts.shift) is not available in the batched engine");
+    GM_ARG(o.precond == GMRES_PRECOND_NONE, "the Gauss-Seidel preconditioner is not available in the batched engine");
     GM_ARG(o.basis == GMRES_BASIS_MONOMIAL || o.basis == GMRES_BASIS_NEWTON,
            "basis must be GMRES_BASIS_MONOMIAL or GMRES_BASIS_NEWTON for batches (pass the shifts in opts.theta)");
     return GMRES_OK;

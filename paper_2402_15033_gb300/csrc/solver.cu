@@ -26,6 +26,7 @@
 #include <cmath>
 #include <vector>
 #include <algorithm>
+#include <type_traits>
 #include "solver_run.cuh"
 #include "tc_common.cuh"
 
@@ -80,6 +81,7 @@ struct gmres_ctx {
     size_t pip_bytes = 0;
     double* bscr = nullptr;      // BCGS2-CholQR2: the five reductions' factors (5 x kMaxCols^2)
     void* digits = nullptr;      // tensor-core arithmetic: digit basis of the m+1 columns (tc_common.cuh)
+    McGs gs;                     // multicolor Gauss-Seidel preconditioner (opts.precond)
     DevState* st = nullptr;      // device
     DevState* hst = nullptr;     // pinned host mirror
     std::vector<cudaEvent_t> ev;
@@ -190,8 +192,10 @@ size_t ctx_bytes(int64_t n, int64_t nnz, const gmres_opts& o) {
     if (mixed) b += up(nz * 4) + up(ldq * 8);
     b += up((size_t)(o.m + 1) * ldq * esz) + 2 * up(ldq * 8);
     b += up(norm_grid(n) * 8) + up(256) + up(pip_bytes_for(n, o)) + up(sizeof(DevState)) + up(16);
-    if (o.ortho == GMRES_ORTHO_BCGS2_CHOLQR2) b += up(5 * (size_t)kMaxCols * kMaxCols * sizeof(double));
+    if (o.ortho == GMRES_ORTHO_BCGS2_CHOLQR2 || o.shift != GMRES_SHIFT_NONE)
+        b += up(5 * (size_t)kMaxCols * kMaxCols * sizeof(double));
     if (uses_digits(o)) b += up(tc_digits_bytes(n, o.m + 1));
+    if (o.precond == GMRES_PRECOND_MCGS) b += up(n * 4) + 3 * up(ldq * 8);   // order, diagonal, two vectors
     return b;
 }
 
@@ -215,6 +219,9 @@ static int check_opts(const gmres_opts* o) {
     GM_ARG(o->arith == GMRES_ARITH_DD || o->arith == GMRES_ARITH_FP64 || o->arith == GMRES_ARITH_TC,
            "unknown arith");
     GM_ARG(o->shift == GMRES_SHIFT_NONE || o->shift == GMRES_SHIFT_CHOLQR3, "unknown shift");
+    GM_ARG(o->precond == GMRES_PRECOND_NONE || o->precond == GMRES_PRECOND_MCGS, "unknown precond");
+    GM_ARG(o->precond == GMRES_PRECOND_NONE || o->precision == GMRES_PREC_FP64,
+           "the Gauss-Seidel preconditioner needs an FP64 basis (precision = GMRES_PREC_FP64)");
     GM_ARG(o->shift == GMRES_SHIFT_NONE || (o->precision == GMRES_PREC_FP64 && o->ortho != GMRES_ORTHO_BCGS2_CHOLQR2),
            "shifted CholQR needs an FP64 basis and the two-stage or BCGS-PIP2 scheme");
     return GMRES_OK;
@@ -238,6 +245,10 @@ int gmres_destroy(gmres_ctx* c) {
     cudaFree(c->pip_work);
     cudaFree(c->bscr);
     cudaFree(c->digits);
+    cudaFree(c->gs.perm);
+    cudaFree(c->gs.diag);
+    cudaFree(c->gs.z);
+    cudaFree(c->gs.t);
     cudaFree(c->st);
     cudaFreeHost(c->hst);
     for (auto& g : c->graphs)
@@ -257,6 +268,75 @@ static int cuda_rc(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return GMRES_OK;
     set_error("%s: %s", what, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? GMRES_ERR_OOM : GMRES_ERR_CUDA;
+}
+
+// Multicolor Gauss-Seidel set-up (host): greedy distance-1 coloring of the
+// symmetrized pattern in natural row order (row i takes the smallest color no
+// neighbor j < i holds, a_ij != 0 or a_ji != 0), rows sorted by color (row
+// order within a color), the diagonal and two work vectors on the device.
+static int setup_mcgs(gmres_ctx* c) {
+    const int64_t n = c->n, nnz = c->A.nnz;
+    cudaStream_t s = c->stream;
+    std::vector<int32_t> rp(n + 1), ci(nnz > 0 ? nnz : 1);
+    cudaError_t e = cudaMemcpyAsync(rp.data(), c->A.rowptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpyAsync(ci.data(), c->A.colind, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_rc(e, "Gauss-Seidel set-up copy");
+    // transpose pattern (rows of A^T), so that both triangles count as neighbors
+    std::vector<int64_t> tp(n + 1, 0);
+    for (int64_t p = 0; p < nnz; ++p) ++tp[ci[p] + 1];
+    for (int64_t i = 0; i < n; ++i) tp[i + 1] += tp[i];
+    std::vector<int32_t> tr(nnz > 0 ? nnz : 1);
+    {
+        std::vector<int64_t> fill(tp.begin(), tp.end() - 1);
+        for (int64_t i = 0; i < n; ++i)
+            for (int32_t p = rp[i]; p < rp[i + 1]; ++p) tr[fill[ci[p]]++] = (int32_t)i;
+    }
+    std::vector<int32_t> color(n);
+    std::vector<int64_t> mark;
+    int ncol = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const size_t need = (size_t)(rp[i + 1] - rp[i]) + (size_t)(tp[i + 1] - tp[i]) + 1;
+        if (mark.size() < need) mark.resize(need, -1);
+        auto take = [&](int32_t j) {
+            if (j < i && (size_t)color[j] < mark.size()) mark[color[j]] = i;
+        };
+        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) take(ci[p]);
+        for (int64_t p = tp[i]; p < tp[i + 1]; ++p) take(tr[p]);
+        int cc = 0;
+        while (mark[cc] == i) ++cc;
+        color[i] = cc;
+        ncol = std::max(ncol, cc + 1);
+    }
+    c->gs.off.assign(ncol + 1, 0);
+    for (int64_t i = 0; i < n; ++i) ++c->gs.off[color[i] + 1];
+    for (int q = 0; q < ncol; ++q) c->gs.off[q + 1] += c->gs.off[q];
+    std::vector<int32_t> perm(n);
+    {
+        std::vector<int64_t> fill(c->gs.off.begin(), c->gs.off.end() - 1);
+        for (int64_t i = 0; i < n; ++i) perm[fill[color[i]]++] = (int32_t)i;
+    }
+    int rc = cuda_rc(cudaMalloc(&c->gs.perm, n * sizeof(int32_t)), "cudaMalloc Gauss-Seidel order");
+    if (!rc) rc = cuda_rc(cudaMalloc(&c->gs.diag, c->ldq * sizeof(double)), "cudaMalloc diagonal");
+    if (!rc) rc = cuda_rc(cudaMalloc(&c->gs.z, c->ldq * sizeof(double)), "cudaMalloc Gauss-Seidel vector");
+    if (!rc) rc = cuda_rc(cudaMalloc(&c->gs.t, c->ldq * sizeof(double)), "cudaMalloc Gauss-Seidel vector");
+    if (rc) return rc;
+    int32_t* bad = nullptr;
+    e = cudaMemcpyAsync(c->gs.perm, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMalloc(&bad, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = launch_diag(s, c->A, c->gs.diag, bad);
+    int32_t hb = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(bad);
+    if (e != cudaSuccess) return cuda_rc(e, "Gauss-Seidel set-up");
+    if (hb) {
+        set_error("the Gauss-Seidel preconditioner needs a nonzero, finite diagonal in every row");
+        return GMRES_ERR_ARG;
+    }
+    return GMRES_OK;
 }
 
 int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colind,
@@ -346,8 +426,10 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
         double rmax;
         std::memcpy(&rmax, &hm, 8);
         if (o.sigma > 0.0) c->sigma = o.sigma;
+        else if (o.precond != GMRES_PRECOND_NONE) c->sigma = 1.0;   // A M^{-1} is O(1) for a Gauss-Seidel M
         else c->sigma = (rmax > 0.0 && std::isfinite(rmax)) ? std::ldexp(1.0, (int)std::floor(std::log2(rmax))) : 1.0;
     }
+    if (o.precond == GMRES_PRECOND_MCGS) CK(setup_mcgs(c));
     const size_t esz = o.precision == GMRES_PREC_MIXED ? sizeof(float) : sizeof(double);
     CK(cuda_rc(cudaMalloc(&c->basis, (size_t)mp1 * c->ldq * esz), "cudaMalloc basis"));
     CK(cuda_rc(cudaMemsetAsync(c->basis, 0, (size_t)mp1 * c->ldq * esz, s), "memset basis"));
@@ -431,8 +513,18 @@ static int run_cycle(gmres_ctx* c, const CycleBasis& cb, std::vector<std::pair<i
         e = mark(PH_MPK);
         for (int i = 0; i < cb.s && e == cudaSuccess; ++i) {
             const double th = cb.theta[i];
-            e = launch_spmv(s, c->A, basis + (size_t)(st0 + i) * c->ldq, basis + (size_t)(st0 + i + 1) * c->ldq,
-                            th, sinv, done);
+            T* wi = basis + (size_t)(st0 + i) * c->ldq;
+            if constexpr (std::is_same<T, double>::value) {
+                if (c->gs.perm) {
+                    // right preconditioning: w_{i+1} = (A M^{-1} w_i - theta w_i) / sigma,
+                    // M^{-1} one multicolor Gauss-Seidel sweep (§VIII, Fig. 9)
+                    e = launch_gs_sweep(s, c->A, c->gs, wi, c->gs.z, done);
+                    if (e == cudaSuccess)
+                        e = launch_spmv(s, c->A, c->gs.z, basis + (size_t)(st0 + i + 1) * c->ldq, th, sinv, done, wi);
+                    continue;
+                }
+            }
+            e = launch_spmv(s, c->A, wi, basis + (size_t)(st0 + i + 1) * c->ldq, th, sinv, done);
         }
         if (e == cudaSuccess) e = mark(PH_MPK);
         if (e == cudaSuccess) e = mark(PH_S1);
@@ -558,7 +650,16 @@ static int run_cycle(gmres_ctx* c, const CycleBasis& cb, std::vector<std::pair<i
             ++panel_idx;
         }
     }
-    if (e == cudaSuccess) e = launch_xupdate(s, c->n, basis, c->ldq, c->x, ds);
+    if (e == cudaSuccess) {
+        if (c->gs.perm) {
+            // x += M^{-1} (Q y)
+            e = launch_xupdate(s, c->n, basis, c->ldq, c->gs.t, ds, true);
+            if (e == cudaSuccess) e = launch_gs_sweep(s, c->A, c->gs, c->gs.t, c->gs.z, nullptr);
+            if (e == cudaSuccess) e = launch_axpy1(s, c->n, c->gs.z, c->x, ds);
+        } else {
+            e = launch_xupdate(s, c->n, basis, c->ldq, c->x, ds);
+        }
+    }
     return cuda_rc(e, "cycle launch");
 }
 
@@ -1016,6 +1117,16 @@ int ortho_stage1_f32(void* stream, int64_t n, const float* Q, int64_t ldq, int32
 int ortho_stage2_f32(void* stream, int64_t n, const float* Q, int64_t ldq, int32_t k, float* V, int64_t ldv,
                      int32_t nb, double* R, int32_t ldr, void* d_work, size_t work_bytes, int32_t* d_status) {
     return ortho_pip(stream, n, Q, ldq, k, V, ldv, nb, R, ldr, d_work, work_bytes, d_status);
+}
+
+int gmres_precond_apply(gmres_ctx* c, const double* r, double* z) {
+    clear_error();
+    GM_ARG(c != nullptr && r != nullptr && z != nullptr && r != z, "need a context and distinct r, z");
+    GM_ARG(c->gs.perm != nullptr, "the context has no preconditioner (opts.precond = GMRES_PRECOND_NONE)");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = launch_gs_sweep(c->stream, c->A, c->gs, r, z, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_rc(e, "preconditioner launch");
 }
 
 int gmres_mpk(gmres_ctx* c, const double* v, double* W, int64_t ldw, int32_t s, double sigma, const double* theta) {

@@ -1,6 +1,7 @@
 // Device-resident state of one restart cycle and the launchers of the solver's
 // non-orthogonalization kernels.
 #pragma once
+#include <vector>
 #include "common.cuh"
 
 namespace gm {
@@ -13,6 +14,17 @@ struct DevCSR {
     int32_t* colind = nullptr;
     double* vals = nullptr;
     float* vals32 = nullptr;   // FP32 copy for the mixed-precision MPK (else null)
+};
+
+// Multicolor Gauss-Seidel preconditioner: the rows sorted by color (perm,
+// device; color c is perm[off[c] .. off[c+1]-1], host offsets), the diagonal
+// (device), and two work vectors of n (device).
+struct McGs {
+    int32_t* perm = nullptr;
+    std::vector<int64_t> off;
+    double* diag = nullptr;
+    double* z = nullptr;
+    double* t = nullptr;
 };
 
 // One restart cycle's scalars and small matrices (all FP64, column-major,
@@ -57,16 +69,22 @@ int newton_shifts(const double* H, int ldh, int k, int s, double* theta);
 double newton_sigma(const double* theta, int s, double fallback);
 
 int norm_grid(int64_t n);
+cudaError_t launch_gs_sweep(cudaStream_t st, const DevCSR& A, const McGs& gs, const double* r, double* z,
+                            const int32_t* d_skip);
+cudaError_t launch_diag(cudaStream_t st, const DevCSR& A, double* diag, int32_t* bad);
+cudaError_t launch_axpy1(cudaStream_t st, int64_t n, const double* z, double* x, const DevState* ds);
 cudaError_t launch_spmv(cudaStream_t st, const DevCSR& A, const double* x, double* y, double theta,
-                        double sinv, const int32_t* d_skip);
+                        double sinv, const int32_t* d_skip, const double* w = nullptr);
 cudaError_t launch_spmv(cudaStream_t st, const DevCSR& A, const float* x, float* y, double theta,
                         double sinv, const int32_t* d_skip);
 cudaError_t launch_residual(cudaStream_t st, const DevCSR& A, const double* b, const double* x, double* out,
                             double* partial, unsigned* counter, DevState* ds, int which);
 cudaError_t launch_scale(cudaStream_t st, int64_t n, const double* v, double* out, const DevState* ds);
 cudaError_t launch_scale(cudaStream_t st, int64_t n, const double* v, float* out, const DevState* ds);
-cudaError_t launch_xupdate(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, double* x, DevState* ds);
-cudaError_t launch_xupdate(cudaStream_t st, int64_t n, const float* Q, int64_t ldq, double* x, DevState* ds);
+cudaError_t launch_xupdate(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, double* x, DevState* ds,
+                           bool assign = false);
+cudaError_t launch_xupdate(cudaStream_t st, int64_t n, const float* Q, int64_t ldq, double* x, DevState* ds,
+                           bool assign = false);
 cudaError_t launch_narrow_vals(cudaStream_t st, int64_t m, const double* in, float* out);
 cudaError_t launch_validate_csr(cudaStream_t st, int64_t n, int64_t nnz, const int32_t* rowptr,
                                 const int32_t* colind, int32_t* bad);

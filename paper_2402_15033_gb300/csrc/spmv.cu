@@ -28,22 +28,67 @@ __device__ double block_sum(double v) {
     return t;  // valid in thread 0
 }
 
-// y = (A x - theta x) * sinv in the basis precision T (FP64, or FP32 for the
-// mixed-precision MPK with an FP32 copy of the values).
+// y = (A x - theta w) * sinv in the basis precision T (FP64, or FP32 for the
+// mixed-precision MPK with an FP32 copy of the values); w = x, or, with a
+// right preconditioner, the unpreconditioned vector x = M^{-1} w came from.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
 spmv_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
             const T* __restrict__ vals, const T* __restrict__ x, T* __restrict__ y,
-            T theta, T sinv, const int32_t* d_skip) {
+            T theta, T sinv, const int32_t* d_skip, const T* __restrict__ w) {
     if (d_skip && *d_skip) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t p0 = __ldg(rowptr + i), p1 = __ldg(rowptr + i + 1);
         T acc = T(0);
         for (int32_t p = p0; p < p1; ++p) acc = fma(__ldg(vals + p), __ldg(x + __ldg(colind + p)), acc);
-        if (theta != T(0)) acc = fma(-theta, x[i], acc);
+        if (theta != T(0)) acc = fma(-theta, w[i], acc);
         y[i] = acc * sinv;
     }
+}
+
+// One color of a forward multicolor Gauss-Seidel sweep (the local
+// Gauss-Seidel preconditioner of §VIII, Fig. 9): every row i of the color,
+// z_i = (r_i - sum_j a_ij z_j) / a_ii, the sum over the row in CSR order with
+// z_i itself still zero (rows of one color are not coupled, so they update at
+// once; colors already swept hold their values, later ones zero).
+__global__ void __launch_bounds__(kVecThreads)
+gs_color_kernel(int64_t cnt, const int32_t* __restrict__ rows, const int32_t* __restrict__ rowptr,
+                const int32_t* __restrict__ colind, const double* __restrict__ vals,
+                const double* __restrict__ diag, const double* __restrict__ r, double* z, const int32_t* d_skip) {
+    if (d_skip && *d_skip) return;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < cnt;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = __ldg(rows + q);
+        const int32_t p0 = __ldg(rowptr + i), p1 = __ldg(rowptr + i + 1);
+        double acc = 0.0;
+        for (int32_t p = p0; p < p1; ++p) acc = fma(__ldg(vals + p), z[__ldg(colind + p)], acc);
+        z[i] = (r[i] - acc) / __ldg(diag + i);
+    }
+}
+
+// a_ii of every row (0 where the row holds no diagonal entry; any zero or
+// non-finite diagonal sets *bad).
+__global__ void __launch_bounds__(kVecThreads)
+diag_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+            const double* __restrict__ vals, double* diag, int32_t* bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double d = 0.0;
+        for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+            if (colind[p] == (int32_t)i) d += vals[p];
+        diag[i] = d;
+        if (!(d != 0.0) || !isfinite(d)) atomicOr(bad, 1);
+    }
+}
+
+// x += z
+__global__ void __launch_bounds__(kVecThreads)
+axpy1_kernel(int64_t n, const double* __restrict__ z, double* __restrict__ x, const DevState* st) {
+    if (st->k_used == 0) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += z[i];
 }
 
 // r = b - A x (x may be null: r = b); r written to out; ||r||^2 reduced in a
@@ -100,11 +145,12 @@ scale_kernel(int64_t n, const double* v, T* out, const DevState* st) {
         out[i] = (T)(v[i] * s);
 }
 
-// x += Q[:, 0:k] y with k = st->k_used, y = st->y (FP64 accumulation); also
+// x += Q[:, 0:k] y with k = st->k_used, y = st->y (FP64 accumulation); with
+// assign, x = Q y (the correction a right preconditioner then maps); also
 // counts iterations.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
-xupdate_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, double* __restrict__ x, DevState* st) {
+xupdate_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, double* __restrict__ x, DevState* st, bool assign) {
     __shared__ double ys[kMaxCols];
     const int k = st->k_used;
     for (int c = threadIdx.x; c < k; c += blockDim.x) ys[c] = st->y[c];
@@ -112,7 +158,7 @@ xupdate_kernel(int64_t n, const T* __restrict__ Q, int64_t ldq, double* __restri
     if (k == 0) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        double acc = x[i];
+        double acc = assign ? 0.0 : x[i];
         for (int c = 0; c < k; ++c) acc = fma((double)__ldg(Q + (int64_t)c * ldq + i), ys[c], acc);
         x[i] = acc;
     }
@@ -178,16 +224,38 @@ int vec_grid(int64_t n) {
 int norm_grid(int64_t n) { return vec_grid(n); }
 
 cudaError_t launch_spmv(cudaStream_t st, const DevCSR& A, const double* x, double* y, double theta,
-                        double sinv, const int32_t* d_skip) {
+                        double sinv, const int32_t* d_skip, const double* w) {
     spmv_kernel<double><<<vec_grid(A.n), kVecThreads, 0, st>>>(A.n, A.rowptr, A.colind, A.vals, x, y, theta, sinv,
-                                                               d_skip);
+                                                               d_skip, w ? w : x);
     return cudaGetLastError();
 }
 
 cudaError_t launch_spmv(cudaStream_t st, const DevCSR& A, const float* x, float* y, double theta,
                         double sinv, const int32_t* d_skip) {
     spmv_kernel<float><<<vec_grid(A.n), kVecThreads, 0, st>>>(A.n, A.rowptr, A.colind, A.vals32, x, y, (float)theta,
-                                                              (float)sinv, d_skip);
+                                                              (float)sinv, d_skip, x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gs_sweep(cudaStream_t st, const DevCSR& A, const McGs& gs, const double* r, double* z,
+                            const int32_t* d_skip) {
+    cudaError_t e = cudaMemsetAsync(z, 0, A.n * sizeof(double), st);
+    for (size_t c = 0; c + 1 < gs.off.size() && e == cudaSuccess; ++c) {
+        const int64_t cnt = gs.off[c + 1] - gs.off[c];
+        gs_color_kernel<<<vec_grid(cnt), kVecThreads, 0, st>>>(cnt, gs.perm + gs.off[c], A.rowptr, A.colind, A.vals,
+                                                               gs.diag, r, z, d_skip);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+cudaError_t launch_diag(cudaStream_t st, const DevCSR& A, double* diag, int32_t* bad) {
+    diag_kernel<<<vec_grid(A.n), kVecThreads, 0, st>>>(A.n, A.rowptr, A.colind, A.vals, diag, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy1(cudaStream_t st, int64_t n, const double* z, double* x, const DevState* ds) {
+    axpy1_kernel<<<vec_grid(n), kVecThreads, 0, st>>>(n, z, x, ds);
     return cudaGetLastError();
 }
 
@@ -208,13 +276,15 @@ cudaError_t launch_scale(cudaStream_t st, int64_t n, const double* v, float* out
     return cudaGetLastError();
 }
 
-cudaError_t launch_xupdate(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, double* x, DevState* ds) {
-    xupdate_kernel<double><<<vec_grid(n), kVecThreads, 0, st>>>(n, Q, ldq, x, ds);
+cudaError_t launch_xupdate(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, double* x, DevState* ds,
+                           bool assign) {
+    xupdate_kernel<double><<<vec_grid(n), kVecThreads, 0, st>>>(n, Q, ldq, x, ds, assign);
     return cudaGetLastError();
 }
 
-cudaError_t launch_xupdate(cudaStream_t st, int64_t n, const float* Q, int64_t ldq, double* x, DevState* ds) {
-    xupdate_kernel<float><<<vec_grid(n), kVecThreads, 0, st>>>(n, Q, ldq, x, ds);
+cudaError_t launch_xupdate(cudaStream_t st, int64_t n, const float* Q, int64_t ldq, double* x, DevState* ds,
+                           bool assign) {
+    xupdate_kernel<float><<<vec_grid(n), kVecThreads, 0, st>>>(n, Q, ldq, x, ds, assign);
     return cudaGetLastError();
 }
 
