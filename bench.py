@@ -76,43 +76,49 @@ def tc_tile_count(k, nb):
 
 
 def tc_mma_flops(n, k, nb):
-    """bf16 tensor FLOPs the exact-slice Gram executes: per 128-row chunk and
-    tile, 8 k-steps x 28 digit-pair MMAs of 16 x 8 x 16; k + nb > 64 runs FP64."""
+    """f16 tensor FLOPs the exact-slice Gram executes: per 64-row chunk, 4
+    k-steps x 28 digit-pair MMAs of 16 x 8 x 16 for every M-tile (narrow
+    blocks, the streaming kernel) or every output tile not strictly below the
+    G diagonal (wide blocks); k + nb > 64 runs FP64."""
     if k + nb > 64:
         return 0.0
-    return math.ceil(n / 128) * tc_tile_count(k, nb) * 8 * 28 * 2 * 16 * 8 * 16
+    tiles = (k + nb + 15) // 16 if nb <= 8 else tc_tile_count(k, nb)
+    return math.ceil(n / 64) * tiles * 4 * 28 * 2 * 16 * 8 * 16
 
 
 def tc_update_mma_flops(n, k, nb):
-    """bf16 tensor FLOPs the exact-slice update executes: per 32-row chunk, 2 M-tiles
-    per N-tile of 8 columns, K steps up to the last nonzero row of the triangular
-    W, 28 digit-pair MMAs of 16 x 8 x 16 each."""
+    """f16 tensor FLOPs the exact-slice update executes: per 64-row chunk, 4
+    M-tiles per N-tile of 8 columns, every k-step over k + nb (narrow blocks)
+    or those up to the last nonzero row of the triangular W (wide blocks), 28
+    digit-pair MMAs of 16 x 8 x 16 each."""
     kx = k + nb
     if kx > 64:
         return 0.0
     nks = (kx + 15) // 16
-    steps = sum(min(nks, (k + 8 * nt + 7) // 16 + 1) for nt in range((nb + 7) // 8))
-    return math.ceil(n / 32) * 2 * steps * 28 * 2 * 16 * 8 * 16
+    if nb <= 8:
+        steps = nks
+    else:
+        steps = sum(min(nks, (k + 8 * nt + 7) // 16 + 1) for nt in range((nb + 7) // 8))
+    return math.ceil(n / 64) * 4 * steps * 28 * 2 * 16 * 8 * 16
 
 
 ARITH_TEXT = {"fp64": "FP64 pipe (native FP64 FMA)",
-              "tc": "Gram and update on bf16 tensor cores by exact 8-bit slicing (FP64 quality); "
-                    "resident digit basis: each column sliced once",
+              "tc": "Gram and update on f16 tensor cores by exact 8-bit slicing (FP64 quality); "
+                    "resident digit basis of 7 bytes per value: each column sliced once",
               "dd": "double-float (hi+lo FP32), ~2^-48 relative, FP64 in/out"}
 
-DTYPE_TEXT = {"fp64": "f64", "tc": "f64 in/out, products as exact bf16 digit slices", "dd": "f32x2 (double-float)"}
+DTYPE_TEXT = {"fp64": "f64", "tc": "f64 in/out, products as exact f16 digit slices", "dd": "f32x2 (double-float)"}
 
-FP64_PEAK_TFLOPS = 152 * 2070e6 * 2 * 2 / 1e12   # 2 FP64 FMA/clk/SM x 152 SMs x max clock
+FP64_PEAK_TFLOPS = 152 * 2070e6 * 2 * 2 / 1e12   # nominal: 2 FP64 FMA/clk/SM x 152 SMs x max clock (1.26)
+FP64_PROBE_TFLOPS = 1.19                          # an FMA-chain probe on this GPU (not a driver measurement)
 
 
 # DRAM bytes per launch from one ncu capture at n = 1,048,576 (profiles/),
 # scaled by 4 to the benchmark's n (traffic grows with n): the last stage-1
-# block (k = 56) and the stage-2 panel.  The FP64 kernels and the stage-2
-# tensor-core kernels move their algorithmic bytes; the stage-1 tensor-core
-# kernels read 14-byte digits instead of 8-byte values (the digit basis).
+# block (k = 56) and the stage-2 panel.  Entries are removed when the kernel
+# changes after its capture.
 NCU_TRAFFIC = {
-    "tc": {"stage1_gram": 4 * (998.1 + 24.9) * 1e6, "stage1_update": 4 * (985.8 + 116.1) * 1e6,
-           "stage2_update": 4 * (511.8 + 457.2) * 1e6},
+    "tc": {},
     "fp64": {"stage1_gram": 4 * (511.8 + 3.2) * 1e6, "stage2_gram": 4 * (514.7 + 3.5) * 1e6},
 }
 
@@ -130,17 +136,26 @@ def roofline_of(d, kernel, arith):
     traffic = NCU_TRAFFIC.get(arith, {}).get(kernel)
     tnote = ("ncu DRAM read+write of the k=56 launch (stage 1) or the panel launch (stage 2), "
              "captured at n=1,048,576 and scaled x4") if traffic else None
+    if arith == "dd":
+        # double-float runs on the FP32 pipe (about 20 FP32 operations per FP64
+        # product); its bytes are the FP64 algorithmic bytes, so it is reported
+        # against the HBM roof like the tensor-core arithmetic
+        return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(gbs / peaks["hbm_gbs"], 4), "traffic": None, "kernel": kernel, "peak_source": src}
     if arith == "tc" and d.get("tensor_flops"):
         tt = d["tensor_flops"] / t / 1e12
         return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(gbs / peaks["hbm_gbs"], 4), "traffic": traffic, "traffic_note": tnote,
                 "kernel": kernel, "peak_source": src,
-                "tensor": {"executed_tflops": round(tt, 2), "mma_sync_bf16_peak_tflops": MMA_SYNC_PEAK,
+                "tensor": {"executed_tflops": round(tt, 2), "mma_sync_f16_peak_tflops": MMA_SYNC_PEAK,
                            "frac": round(tt / MMA_SYNC_PEAK, 4),
-                           "peak_source": "measured mma.sync m16n8k16 bf16 throughput on this GPU"}}
+                           "peak_source": "mma.sync m16n8k16 throughput measured on this GPU (bf16; f16 "
+                                          "issues at the same rate)"}}
     return {"bound": "alu", "achieved": round(tfl, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
             "frac": round(tfl / FP64_PEAK_TFLOPS, 4), "traffic": traffic, "traffic_note": tnote, "kernel": kernel,
-            "peak_source": "FP64 FMA pipe: 2/clk/SM x 152 SMs x 2070 MHz", "hbm": hbm}
+            "peak_source": "nominal FP64 FMA pipe: 2/clk/SM x 152 SMs x 2070 MHz (no driver measurement of FP64)",
+            "frac_of_probe": round(tfl / FP64_PROBE_TFLOPS, 4),
+            "probe_tflops": FP64_PROBE_TFLOPS, "hbm": hbm}
 
 
 MMA_SYNC_PEAK = 604.0
@@ -446,54 +461,46 @@ def run_ours(args):
                       "max_abs_R_diff_vs_headline": float((R2 - R2_main).abs().max().item())}
     # leave the basis as the headline arithmetic produced it (e2e below re-copies it anyway)
 
-    # ---- end to end: pinned host basis in, Q and R out, every step.  Two device
-    # bases alternate on three streams, so that one step's copy in and the
-    # previous step's copy out overlap the current step's kernels
+    # ---- end to end through the library's own call on host buffers: every step
+    # ortho_plan_run copies the page-locked host basis in (block by block, while
+    # stage 1 runs), orthogonalizes it and copies Q and R back (in row ranges,
+    # while the stage-2 update runs); the plan's device buffers are allocated
+    # once, before the timed region
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.arith in ("tc", "fp64"):
+        ar = capi.GMRES_ARITH_TC if args.arith == "tc" else capi.GMRES_ARITH_FP64
+        plan = capi.OrthoPlan(n, S, NBLK, ar, stream)
         hostin = torch.from_numpy(host.T.copy()).pin_memory()
         hostin[0] /= torch.linalg.norm(hostin[0])
-        hostq = [torch.empty_like(hostin).pin_memory() for _ in range(2)]
-        hostr = [torch.empty(NCOL, NCOL, dtype=torch.float64).pin_memory() for _ in range(2)]
-        bufs = [basis, torch.empty_like(basis)]
-        Rhs = [Rh, torch.zeros_like(Rh)]
-        R2s = [R2, torch.zeros_like(R2)]
-        s_in, s_comp, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-        steps_ = [make_step(args.arith, bufs[i].T, Rhs[i], R2s[i], s_comp.cuda_stream) for i in range(2)]
-        ev_in = [torch.cuda.Event() for _ in range(2)]
-        ev_done = [torch.cuda.Event() for _ in range(2)]
-        ev_out = [torch.cuda.Event() for _ in range(2)]
-        torch.cuda.synchronize()
+        hostq = torch.empty_like(hostin).pin_memory()
+        hostrh = torch.zeros(NCOL, NCOL, dtype=torch.float64).pin_memory()
+        hostr2 = torch.zeros(NCOL, NCOL, dtype=torch.float64).pin_memory()
+        for _ in range(2):
+            rc, _ = plan.run(hostin.T, hostq.T, hostrh.T, hostr2.T, on_device=False)
+            if rc != 0:
+                raise RuntimeError("Cholesky breakdown in the end-to-end steps")
         ke = max(3, min(args.steps, 10))
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
-        a.record(s_in)
+        a.record()
         for i in range(ke):
-            j = i % 2
-            with torch.cuda.stream(s_in):
-                if i >= 2:
-                    s_in.wait_event(ev_out[j])          # buffer j's last results are out
-                bufs[j].copy_(hostin, non_blocking=True)
-                ev_in[j].record(s_in)
-            s_comp.wait_event(ev_in[j])
-            steps_[j]()
-            ev_done[j].record(s_comp)
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(ev_done[j])
-                hostq[j].copy_(bufs[j], non_blocking=True)
-                hostr[j].copy_(R2s[j].T, non_blocking=True)
-                ev_out[j].record(s_out)
-        s_out.wait_event(ev_out[(ke - 2) % 2])
-        b.record(s_out)
+            rc, _ = plan.run(hostin.T, hostq.T, hostrh.T, hostr2.T, on_device=False)
+            if rc != 0:
+                raise RuntimeError("Cholesky breakdown in the end-to-end steps")
+        b.record()
         torch.cuda.synchronize()
-        if int(st.abs().sum().item()) != 0:
-            raise RuntimeError("Cholesky breakdown in the end-to-end steps")
+        plan.close()
         ems = max_over_ranks(a.elapsed_time(b) / ke, world, dev)
         e2e = {"value": round(whole_job_gbs(bytes_step, ems, world), 3), "unit": "GB/s",
                "h2d_bytes_per_step": int(hostin.numel() * 8),
-               "d2h_bytes_per_step": int(hostq[0].numel() * 8 + hostr[0].numel() * 8),
+               "d2h_bytes_per_step": int(hostq.numel() * 8 + hostrh.numel() * 8 + hostr2.numel() * 8),
                "ms_per_step": round(ems, 3), "steps": ke,
-               "overlap": "two device bases on three streams: copy in, kernels, copy out"}
+               "call": "ortho_plan_run on page-locked host buffers (one library call per step)",
+               "overlap": "inside each call: columns in block by block during stage 1, Q out in row ranges "
+                          "during the stage-2 update"}
 
     # ---- the FP64 solver on the same grid: one restart cycle, and C1 to convergence
     solve = None
@@ -508,11 +515,13 @@ def run_ours(args):
 
     # ---- CPU oracle on a bounded sample of the same workload
     cpu = None
+    cpu_solver = None
     if rank == 0 and not args.no_cpu:
         rows, steps = n, 2
         val, dt = cpu_oracle_rate(rows, steps)
         cpu = {"value": round(val, 3), "unit": "GB/s", "cores": cpu_threads(), "kind": "oracle",
                "sample": f"{steps} steps on all {rows} rows (numpy FP64 oracle), {dt:.1f} s"}
+        cpu_solver = oracle_numbers(args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -525,7 +534,7 @@ def run_ours(args):
                 "other_arith": others, "e2e": e2e, "cpu_baseline": cpu,
                 "gpu_launches": (2 * NBLK + 2 + (1 if args.arith == "tc" and not args.no_digits else 0)) * args.steps,
                 "clocks": clk,
-                "solver": solve,
+                "solver": solve, "cpu_solver": cpu_solver,
                 "patterns": patterns}
         print(json.dumps(line))
     if world > 1:
@@ -533,77 +542,86 @@ def run_ours(args):
     return 0
 
 
+def _time_solve(capi, A, bd, dev, opts, reps=3):
+    """Median wall time of gmres_solve (device b and x) after one warm-up solve
+    (the warm-up captures the cycle graphs); the result dict of the last solve."""
+    import torch
+    S = capi.Solver.from_csr(A, opts)
+    xd = torch.zeros(A.n, dtype=torch.float64, device=dev)
+    S.solve(bd, xd)
+    times = []
+    for _ in range(reps):
+        xd.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, res = S.solve(bd, xd)
+        times.append(time.perf_counter() - t0)
+    S.close()
+    return statistics.median(times), rc, res
+
+
 def solver_numbers(capi, dev, args):
-    import numpy as np
+    """Time to solution of the s-step GMRES solver: the 64 x 64 case (C1) and
+    the 2048 x 2048 case (C2) at tol 1e-8 for the two-stage scheme and the
+    paper's comparisons (standard GMRES as s = 1, BCGS-PIP2 = two-stage with
+    s^ = s, BCGS2-CholQR2), monomial and automatic Newton basis, FP64 and
+    tensor-core arithmetic, with the Gauss-Seidel preconditioner and with
+    shifted CholQR; one timed restart cycle per scheme and s^ in {5, 20, 40,
+    60} with per-phase times (the layout of Table 2)."""
     import torch
     import synth
     from scipy.sparse import csr_matrix
     out = {}
-    # C1: 64 x 64 Laplace, tol 1e-8, FP64 two-stage, to convergence (time to solution)
-    A = synth.laplace2d(64)
-    xt = synth.x_true(A.n, 0)
-    b = csr_matrix((A.vals, A.colind, A.rowptr), shape=(A.n, A.n)) @ xt
-    S1 = capi.Solver.from_csr(A, capi.default_opts(m=60, s=5, panel=60, tol=1e-8))
-    bd = torch.tensor(b, device=dev)
-    xd = torch.zeros(A.n, dtype=torch.float64, device=dev)
-    S1.solve(bd, xd)
-    times = []
-    for _ in range(5):
-        xd.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rc, res = S1.solve(bd, xd)
-        times.append(time.perf_counter() - t0)
-    S1.close()
-    out["laplace64_fp64"] = {"time_to_solution_ms": round(1e3 * statistics.median(times), 3), "status": rc,
-                             "iters": res["iters"], "relres": res["relres_true"]}
-    # the same with the tensor-core arithmetic
-    S1 = capi.Solver.from_csr(A, capi.default_opts(m=60, s=5, panel=60, tol=1e-8, arith=capi.GMRES_ARITH_TC))
-    S1.solve(bd, xd)
-    times = []
-    for _ in range(5):
-        xd.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rc, res = S1.solve(bd, xd)
-        times.append(time.perf_counter() - t0)
-    S1.close()
-    out["laplace64_tc"] = {"time_to_solution_ms": round(1e3 * statistics.median(times), 3), "status": rc,
-                           "iters": res["iters"], "relres": res["relres_true"]}
-    # s = 10: the monomial basis breaks down on this system; the Newton basis with
-    # automatic shifts (first cycle standard GMRES) solves it
-    for aname, arith in (("fp64", capi.GMRES_ARITH_FP64), ("tc", capi.GMRES_ARITH_TC)):
-        S1 = capi.Solver.from_csr(A, capi.default_opts(m=60, s=10, panel=60, tol=1e-8, arith=arith,
-                                                       basis=capi.GMRES_BASIS_NEWTON_AUTO))
-        S1.solve(bd, xd)
-        times = []
-        for _ in range(5):
-            xd.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            rc, res = S1.solve(bd, xd)
-            times.append(time.perf_counter() - t0)
-        S1.close()
-        out[f"laplace64_s10_newton_auto_{aname}"] = {
-            "time_to_solution_ms": round(1e3 * statistics.median(times), 3), "status": rc, "iters": res["iters"],
-            "restarts": res["restarts"], "relres": res["relres_true"], "sigma": res["sigma"]}
-    # 2048 x 2048 Laplace: one restart cycle (60 iterations), per-phase times, for
-    # the two-stage scheme and the paper's one-stage comparisons (BCGS-PIP2 and the
-    # BCGS2-CholQR2 baseline of §VIII), FP64 and tensor-core arithmetic
-    if args.rows == N_ROWS:
-        A = synth.laplace2d(2048)
-        xt = synth.x_true(A.n, 0)
-        b = csr_matrix((A.vals, A.colind, A.rowptr), shape=(A.n, A.n)) @ xt
+    T, A = capi.GMRES_ARITH_TC, capi.GMRES_ARITH_FP64
+    NA, MO = capi.GMRES_BASIS_NEWTON_AUTO, capi.GMRES_BASIS_MONOMIAL
+
+    def tts_table(grid, variants, reps):
+        Am = synth.laplace2d(grid)
+        b = csr_matrix((Am.vals, Am.colind, Am.rowptr), shape=(Am.n, Am.n)) @ synth.x_true(Am.n, 0)
         bd = torch.tensor(b, device=dev)
-        xd = torch.zeros(A.n, dtype=torch.float64, device=dev)
-        schemes = [("two_stage", capi.GMRES_ORTHO_TWO_STAGE), ("bcgs_pip2", capi.GMRES_ORTHO_BCGS_PIP2),
-                   ("bcgs2_cholqr2", capi.GMRES_ORTHO_BCGS2_CHOLQR2)]
+        tab = {}
+        for name, kw in variants:
+            o = dict(m=60, s=5, panel=60, tol=1e-8, max_restarts=5000)
+            o.update(kw)
+            dt, rc, res = _time_solve(capi, Am, bd, dev, capi.default_opts(**o), reps)
+            tab[name] = {"time_to_solution_ms": round(1e3 * dt, 3), "status": rc, "iters": res["iters"],
+                         "restarts": res["restarts"], "relres": res["relres_true"]}
+        return tab
+
+    c1 = [("fp64", dict(arith=A)), ("tc", dict(arith=T)),
+          ("s10_newton_auto_fp64", dict(s=10, basis=NA, arith=A)), ("s10_newton_auto_tc", dict(s=10, basis=NA, arith=T)),
+          ("s10_monomial_shifted_fp64", dict(s=10, shift=1, arith=A)),
+          ("bcgs2_cholqr2_fp64", dict(ortho=capi.GMRES_ORTHO_BCGS2_CHOLQR2, arith=A))]
+    out["laplace64_time_to_solution"] = tts_table(64, c1, 5)
+    if args.rows == N_ROWS:
+        c2 = [("two_stage_fp64", dict(arith=A)), ("two_stage_tc", dict(arith=T)),
+              ("two_stage_s10_newton_auto_fp64", dict(s=10, basis=NA, arith=A)),
+              ("two_stage_s10_newton_auto_tc", dict(s=10, basis=NA, arith=T)),
+              ("two_stage_gauss_seidel_newton_auto_tc", dict(basis=NA, arith=T, precond=1)),
+              ("two_stage_s10_monomial_shifted_tc", dict(s=10, basis=MO, arith=T, shift=1)),
+              ("bcgs_pip2_fp64", dict(ortho=capi.GMRES_ORTHO_BCGS_PIP2, arith=A)),
+              ("bcgs2_cholqr2_fp64", dict(ortho=capi.GMRES_ORTHO_BCGS2_CHOLQR2, arith=A)),
+              ("bcgs2_cholqr2_tc", dict(ortho=capi.GMRES_ORTHO_BCGS2_CHOLQR2, arith=T)),
+              ("standard_gmres_s1_fp64", dict(s=1, panel=1, arith=A))]
+        tab = tts_table(2048, c2, 1)
+        base = tab["bcgs2_cholqr2_fp64"]["time_to_solution_ms"]
+        for v in tab.values():
+            v["speedup_vs_bcgs2_cholqr2_fp64"] = round(base / v["time_to_solution_ms"], 3)
+        out["laplace2048_time_to_solution"] = tab
+
+        # one restart cycle per scheme and s^, per phase (Table 2's columns)
+        Am = synth.laplace2d(2048)
+        b = csr_matrix((Am.vals, Am.colind, Am.rowptr), shape=(Am.n, Am.n)) @ synth.x_true(Am.n, 0)
+        bd = torch.tensor(b, device=dev)
+        xd = torch.zeros(Am.n, dtype=torch.float64, device=dev)
+        rows = [(f"two_stage_shat{p}", capi.GMRES_ORTHO_TWO_STAGE, p) for p in (5, 20, 40, 60)]
+        rows.append(("bcgs2_cholqr2", capi.GMRES_ORTHO_BCGS2_CHOLQR2, 5))
         cycles = {}
-        for name, ortho in schemes:
-            for aname, arith in (("fp64", capi.GMRES_ARITH_FP64), ("tc", capi.GMRES_ARITH_TC)):
-                opts = capi.default_opts(m=60, s=5, panel=60, tol=1e-14, max_restarts=1, timing=1, ortho=ortho,
+        for name, ortho, panel in rows:
+            for aname, arith in (("fp64", A), ("tc", T)):
+                opts = capi.default_opts(m=60, s=5, panel=panel, tol=1e-14, max_restarts=1, timing=1, ortho=ortho,
                                          arith=arith)
-                S2 = capi.Solver.from_csr(A, opts)
+                S2 = capi.Solver.from_csr(Am, opts)
                 S2.solve(bd, xd)
                 xd.zero_()
                 rc, res = S2.solve(bd, xd)
@@ -611,13 +629,40 @@ def solver_numbers(capi, dev, args):
                 cyc = res["t_total_ms"]
                 cycles[f"{name}_{aname}"] = {
                     "ms_per_restart_cycle": round(cyc, 3), "iters": res["iters"],
-                    "iters_per_s": round(res["iters"] / (cyc * 1e-3), 1), "t_mpk_ms": round(res["t_mpk_ms"], 3),
+                    "t_mpk_ms": round(res["t_mpk_ms"], 3), "t_ortho_ms": round(res["t_stage1_ms"] + res["t_stage2_ms"], 3),
                     "t_stage1_ms": round(res["t_stage1_ms"], 3), "t_stage2_ms": round(res["t_stage2_ms"], 3),
                     "t_ls_ms": round(res["t_ls_ms"], 3), "relres_after_one_cycle": res["relres_true"], "status": rc}
-        out["laplace2048_cycle"] = cycles
-        base = cycles["bcgs2_cholqr2_fp64"]["ms_per_restart_cycle"]
-        out["laplace2048_speedup_vs_bcgs2_cholqr2_fp64"] = {
-            k: round(base / v["ms_per_restart_cycle"], 3) for k, v in cycles.items()}
+        base = cycles["bcgs2_cholqr2_fp64"]
+        for v in cycles.values():
+            v["ortho_speedup_vs_bcgs2_cholqr2_fp64"] = round(base["t_ortho_ms"] / v["t_ortho_ms"], 3)
+            v["cycle_speedup_vs_bcgs2_cholqr2_fp64"] = round(base["ms_per_restart_cycle"] / v["ms_per_restart_cycle"], 3)
+        out["laplace2048_shat_sweep_cycle"] = cycles
+    return out
+
+
+def oracle_numbers(args):
+    """The CPU oracle (numpy FP64, all host cores) on the solver workloads: the
+    64 x 64 time to solution (C1) and one restart cycle of the 2048 x 2048 (C2)
+    and 160^3 (C3, FP64) systems, m = 60, s = 5, s^ = 60 (a bounded sample: a
+    full solve takes many cycles)."""
+    import synth
+    from oracle import krylov as kr
+    out = {"cores": cpu_threads(), "kind": "oracle"}
+    A = synth.laplace2d(64)
+    b = kr.as_operator(A) @ synth.x_true(A.n, 0)
+    t0 = time.perf_counter()
+    _, info = kr.sstep_gmres(A, b, m=60, s=5, panel=60, tol=1e-8)
+    out["laplace64_time_to_solution_ms"] = round(1e3 * (time.perf_counter() - t0), 1)
+    out["laplace64_iters"] = info["iters"]
+    if args.rows == N_ROWS and not args.no_oracle_cycles:
+        for name, A in (("laplace2048", synth.laplace2d(2048)), ("laplace3d_160", synth.laplace3d(160))):
+            b = kr.as_operator(A) @ synth.x_true(A.n, 0)
+            t0 = time.perf_counter()
+            _, info = kr.sstep_gmres(A, b, m=60, s=5, panel=60, tol=1e-30, max_restarts=1)
+            dt = time.perf_counter() - t0
+            out[name + "_one_cycle_ms"] = round(1e3 * dt, 1)
+            out[name + "_ms_per_iteration"] = round(1e3 * dt / max(info["iters"], 1), 2)
+            out[name + "_iters"] = info["iters"]
     return out
 
 
@@ -690,11 +735,22 @@ def batched_systems(nsys, seed, nmin, nmax):
     return mats
 
 
+def _rate(systems, converged, wall):
+    return {"systems": systems, "converged": int(converged), "wall_s": round(wall, 3),
+            "raw_solves_per_s": round(systems / wall, 3), "converged_per_s": round(converged / wall, 3),
+            "ms_per_converged": round(1e3 * wall / converged, 2) if converged else None}
+
+
 def batched_numbers(capi, args):
     """Batched configuration: 256 nonsymmetric systems, n log-uniform in
-    [1e4, 5e5], FP32 basis / FP64 Gram, s=5, m=40, s^=40, tol 1e-8, one
-    persistent launch per step under captured CUDA graphs, autotuned grids;
-    against the plain FP64 single-solve path on the same systems."""
+    [1e4, 5e5], s=5, m=40, s^=40, tol 1e-8, one persistent launch per step
+    under captured CUDA graphs, autotuned grids.  Like for like: the batched
+    engine and the single-system solver one system at a time with the same
+    algorithm (FP64, monomial: both see the same breakdowns), then the
+    precision pattern batched (FP32 basis, explicit projected Gram) against
+    FP64 one at a time with the basis that converges on every system (Newton,
+    automatic shifts) and with shifted CholQR.  Every arm: raw and converged
+    solves per second of wall time."""
     import numpy as np
     import synth
     from scipy.sparse import csr_matrix
@@ -703,53 +759,48 @@ def batched_numbers(capi, args):
     bs = [csr_matrix((A.vals, A.colind, A.rowptr), shape=(A.n, A.n)) @ synth.x_true(A.n, i)
           for i, A in enumerate(mats)]
     gen_s = time.perf_counter() - t0
-    o = capi.default_opts(m=40, s=5, panel=40, tol=1e-8, precision=capi.GMRES_PREC_MIXED, max_restarts=500)
-    B = capi.Batch(mats, o)
-    tune = B.autotune()
-    xs = [np.zeros(A.n) for A in mats]
-    B.solve(bs, [np.zeros(A.n) for A in mats])   # warm-up (graph capture)
-    t0 = time.perf_counter()
-    rc, res = B.solve(bs, xs)
-    bt = time.perf_counter() - t0
-    B.close()
-    ok = sum(1 for r in res if r["status"] == 0)
-    relres = [r["relres_true"] for r in res if r["status"] == 0]
-    # the same batch with the Gram accumulated in double-float (FP32 pipe) instead of FP64
-    odd = capi.default_opts(m=40, s=5, panel=40, tol=1e-8, precision=capi.GMRES_PREC_MIXED, max_restarts=500,
-                            arith=capi.GMRES_ARITH_DD)
-    Bd = capi.Batch(mats, odd)
-    Bd.autotune()
-    xd = [np.zeros(A.n) for A in mats]
-    Bd.solve(bs, [np.zeros(A.n) for A in mats])
-    t0 = time.perf_counter()
-    rcd, resd = Bd.solve(bs, xd)
-    btd = time.perf_counter() - t0
-    Bd.close()
-    okd = sum(1 for r in resd if r["status"] == 0)
-    relresd = [r["relres_true"] for r in resd if r["status"] == 0]
-    # plain FP64, one system at a time
-    o64 = capi.default_opts(m=40, s=5, panel=40, tol=1e-8, max_restarts=500)
-    t0 = time.perf_counter()
-    ok64 = 0
-    for A, b in zip(mats, bs):
-        S = capi.Solver.from_csr(A, o64)
-        x = np.zeros(A.n)
-        rc1, r1 = S.solve(b, x)
-        S.close()
-        ok64 += rc1 == 0
-    t64 = time.perf_counter() - t0
-    return {"systems": len(mats), "rows": int(sum(A.n for A in mats)), "nnz": int(sum(A.nnz for A in mats)),
-            "mixed_batched": {"solves_per_s": round(ok / bt, 3), "converged": ok, "wall_s": round(bt, 3),
-                              "max_relres": max(relres) if relres else None,
-                              "iters_median": int(np.median([r["iters"] for r in res]))},
-            "mixed_batched_dd_gram": {"solves_per_s": round(okd / btd, 3), "converged": okd, "wall_s": round(btd, 3),
-                                      "max_relres": max(relresd) if relresd else None,
-                                      "iters_median": int(np.median([r["iters"] for r in resd]))},
-            "fp64_one_at_a_time": {"solves_per_s": round(ok64 / t64, 3), "converged": int(ok64),
-                                   "wall_s": round(t64, 3),
-                                   "note": "includes per-system create/destroy; FP64 BCGS-PIP breaks down on "
-                                           "systems whose monomial blocks violate Eq. (5)"},
-            "autotune": tune, "generate_s": round(gen_s, 1)}
+    nsys = len(mats)
+    out = {"systems": nsys, "rows": int(sum(A.n for A in mats)), "nnz": int(sum(A.nnz for A in mats)),
+           "generate_s": round(gen_s, 1)}
+
+    def batched(name, o):
+        B = capi.Batch(mats, o)
+        tune = B.autotune()
+        B.solve(bs, [np.zeros(A.n) for A in mats])   # warm-up (graph capture)
+        xs = [np.zeros(A.n) for A in mats]
+        t0 = time.perf_counter()
+        rc, res = B.solve(bs, xs)
+        wall = time.perf_counter() - t0
+        B.close()
+        ok = [r for r in res if r["status"] == 0]
+        out[name] = dict(_rate(nsys, len(ok), wall), max_relres=max(r["relres_true"] for r in ok) if ok else None,
+                         iters_median=int(np.median([r["iters"] for r in res])), autotune=tune)
+
+    def one_at_a_time(name, o, note):
+        t0 = time.perf_counter()
+        ok = 0
+        for A, b in zip(mats, bs):
+            S = capi.Solver.from_csr(A, o)
+            x = np.zeros(A.n)
+            rc1, r1 = S.solve(b, x)
+            S.close()
+            ok += rc1 == 0
+        out[name] = dict(_rate(nsys, ok, time.perf_counter() - t0), note=note)
+
+    common = dict(m=40, s=5, panel=40, tol=1e-8, max_restarts=500)
+    batched("fp64_batched_monomial", capi.default_opts(**common))
+    one_at_a_time("fp64_one_at_a_time_monomial", capi.default_opts(**common),
+                  "the same algorithm as fp64_batched_monomial; includes per-system create/destroy")
+    batched("mixed_batched", capi.default_opts(precision=capi.GMRES_PREC_MIXED, **common))
+    batched("mixed_batched_dd_gram", capi.default_opts(precision=capi.GMRES_PREC_MIXED, arith=capi.GMRES_ARITH_DD,
+                                                       **common))
+    one_at_a_time("fp64_one_at_a_time_newton_auto",
+                  capi.default_opts(basis=capi.GMRES_BASIS_NEWTON_AUTO, **common),
+                  "FP64, automatic Newton shifts (the batched engine takes given shifts only)")
+    one_at_a_time("fp64_one_at_a_time_shifted_cholqr",
+                  capi.default_opts(shift=capi.GMRES_SHIFT_CHOLQR3, **common),
+                  "FP64, monomial, shifted CholQR (stage 1 shifted, stage 2 shifted CholQR3)")
+    return out
 
 
 def serving_numbers(capi, args):
@@ -792,7 +843,8 @@ def serving_numbers(capi, args):
            "served": "mixed precision (FP32 basis/MPK), double-float Gram accumulation, FP64 Cholesky, Hessenberg "
                      "and refinement, Newton basis with Leja-ordered Ritz shifts",
            "rates": []}
-    for rate in list(args.serve_rates) + [0.0]:
+
+    def serve(rate, opts_of):
         # rate 0: every request arrives at t = 0 (saturated server, peak solves/s)
         arr = np.cumsum(g.exponential(1.0 / rate, size=len(reqs))) if rate > 0 else np.zeros(len(reqs))
         srv = capi.Server(max_active=32)
@@ -801,40 +853,40 @@ def serving_numbers(capi, args):
         for (A, b, s, m), ta in zip(reqs, arr):
             while time.perf_counter() - t0 < ta:
                 time.sleep(0.001)
-            ids.append(srv.submit(A, b, opts=served_opts(s, m)))
+            ids.append(srv.submit(A, b, opts=opts_of(s, m)))
         res = [srv.wait(i) for i in ids]
+        wall = time.perf_counter() - t0
         st = srv.stats()
         srv.stop()
         conv = sum(1 for _, r in res if r["status"] == 0)
-        out["rates"].append({"rate_per_s": rate if rate > 0 else "saturated", "p50_ms": round(st["p50_ms"], 2),
-                             "p99_ms": round(st["p99_ms"], 2), "solves_per_s": round(st["solves_per_s"], 3),
-                             "converged_per_s": round(conv / st["busy_s"], 3) if st["busy_s"] > 0 else None,
-                             "converged": conv,
-                             "statuses": sorted(set(r["status"] for _, r in res))})
-    # the previous served configuration (FP64 Gram accumulation, monomial basis), saturated
-    srv = capi.Server(max_active=32)
-    t0 = time.perf_counter()
-    ids = [srv.submit(A, b, opts=served_opts(s, m, arith=capi.GMRES_ARITH_FP64, basis=capi.GMRES_BASIS_MONOMIAL))
-           for A, b, s, m in reqs]
-    res = [srv.wait(i) for i in ids]
-    st = srv.stats()
-    srv.stop()
-    conv = sum(1 for _, r in res if r["status"] == 0)
-    out["served_fp64_gram_monomial_saturated"] = {
-        "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2), "solves_per_s": round(st["solves_per_s"], 3),
-        "converged_per_s": round(conv / st["busy_s"], 3) if st["busy_s"] > 0 else None, "converged": conv}
-    t0 = time.perf_counter()
-    conv64 = 0
-    for A, b, s, m in reqs:
-        S = capi.Solver.from_csr(A, capi.default_opts(m=m, s=s, panel=m, tol=1e-8, max_restarts=args.serve_restarts))
-        x = np.zeros(A.n)
-        rc, r = S.solve(b, x)
-        S.close()
-        conv64 += rc == 0
-    t64 = time.perf_counter() - t0
-    out["fp64_one_at_a_time"] = {"solves_per_s": round(len(reqs) / t64, 3),
-                                 "converged_per_s": round(conv64 / t64, 3), "converged": int(conv64),
-                                 "wall_s": round(t64, 2)}
+        d = dict(_rate(len(reqs), conv, wall), p50_ms=round(st["p50_ms"], 2), p99_ms=round(st["p99_ms"], 2),
+                 server_busy_s=round(st["busy_s"], 3), statuses=sorted(set(r["status"] for _, r in res)))
+        return d
+
+    for rate in list(args.serve_rates) + [0.0]:
+        d = serve(rate, served_opts)
+        d["rate_per_s"] = rate if rate > 0 else "saturated"
+        out["rates"].append(d)
+    # the same requests served in plain FP64 (FP64 basis and Gram) with the same basis
+    out["served_fp64_newton_auto_saturated"] = serve(0.0, lambda s, m: served_opts(
+        s, m, precision=capi.GMRES_PREC_FP64, arith=capi.GMRES_ARITH_FP64))
+
+    def one_at_a_time(basis):
+        t0 = time.perf_counter()
+        conv = 0
+        for A, b, s, m in reqs:
+            S = capi.Solver.from_csr(A, capi.default_opts(m=m, s=s, panel=m, tol=1e-8, basis=basis,
+                                                          max_restarts=args.serve_restarts))
+            x = np.zeros(A.n)
+            rc, r = S.solve(b, x)
+            S.close()
+            conv += rc == 0
+        return _rate(len(reqs), conv, time.perf_counter() - t0)
+
+    # like for like: plain FP64 one request at a time with the served basis, and
+    # with the monomial basis (whose s = 10 requests break down)
+    out["fp64_one_at_a_time_newton_auto"] = one_at_a_time(capi.GMRES_BASIS_NEWTON_AUTO)
+    out["fp64_one_at_a_time_monomial"] = one_at_a_time(capi.GMRES_BASIS_MONOMIAL)
     return out
 
 
@@ -849,6 +901,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-oracle-cycles", action="store_true",
+                    help="skip the oracle's restart cycles on the 2048^2 and 160^3 systems (about 40 s of CPU)")
     ap.add_argument("--no-patterns", action="store_true", help="skip the mixed, batched and serving configurations")
     ap.add_argument("--no-dd", action="store_true", help="skip the double-float measurement")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core Gram measurement")

@@ -296,6 +296,37 @@ int ortho_update_tc(void* stream, int64_t n, const double* Q, int64_t ldq, int32
                     double* V, int64_t ldv, int32_t nb, const double* R, int32_t ldr,
                     const int32_t* d_status);
 
+/* Two-stage orthogonalization of one panel in one call, on host or device
+ * buffers (§V, Fig. 5): X = [x_0, V_0, ..., V_{nblk-1}] (n x (1 + s nblk),
+ * column-major, ld ldx; x_0 of unit norm, the first column of a restart cycle)
+ * goes through stage 1 (one BCGS-PIP of every block V_j against the
+ * 1 + s j accumulated columns) and stage 2 (one BCGS-PIP = CholQR of the whole
+ * panel).  Outputs: Q (n x (1 + s nblk), ld ldq) with X = Q R2 Rhat on the
+ * panel's columns; Rhat (stage-1 factors: block column j in rows
+ * 0 .. s(j+1), columns 1+sj .. s(j+1); column 0 untouched) and R2 (stage 2),
+ * each (1+s nblk)^2, ld ldr, or NULL.  The same kernels as the ortho_* calls:
+ * arith GMRES_ARITH_TC uses the digit basis (ortho_*_tcd), GMRES_ARITH_FP64 the
+ * FP64 pipe.
+ *   ortho_plan_create: allocates the device basis, digit basis, workspace and
+ *                      factors for n rows (n >= 64), 1 <= s <= 16, 1 + s nblk
+ *                      <= 64, on the current device; kernels run on `stream`.
+ *   ortho_plan_run:    ptr_on_device = 0: X, Q, Rhat, R2 in host memory (page-
+ *                      locked memory lets the copies overlap the kernels: the
+ *                      columns go in block by block while stage 1 runs, Q comes
+ *                      back in row ranges while the stage-2 update runs);
+ *                      = 1: device memory.  X may equal Q.  Allocates nothing;
+ *                      returns when the outputs are written.  block_status (host,
+ *                      nblk + 1 entries, or NULL) receives each stage's Cholesky
+ *                      status; any breakdown returns GMRES_ERR_BREAKDOWN.
+ *   ortho_plan_destroy: NULL-safe.
+ * The paper has no such call; it is the library's end-to-end entry point for
+ * the step that the orthogonalization benchmark times. */
+typedef struct ortho_plan ortho_plan;
+int ortho_plan_create(ortho_plan** out, int64_t n, int32_t s, int32_t nblk, int32_t arith, void* stream);
+int ortho_plan_run(ortho_plan* p, const double* X, int64_t ldx, double* Q, int64_t ldq, double* Rhat, double* R2,
+                   int32_t ldr, int32_t ptr_on_device, int32_t* block_status);
+int ortho_plan_destroy(ortho_plan* p);
+
 /* Digit basis: the seven digit slices that the tensor-core arithmetic makes of
  * every FP64 value (per 64-row chunk of a column), kept in device memory so that
  * a basis column is sliced once however many blocks later read it (stage 1

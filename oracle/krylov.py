@@ -263,7 +263,10 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
     """s-step GMRES (Fig. 1, §III) with the chosen block orthogonalization.
 
     ``panel`` is the second step size s^ of the two-stage scheme (§V); it must
-    satisfy s | s^ | m.  ``theta`` is None (monomial basis), s Newton shifts,
+    satisfy s | s^ and s | m.  When s^ does not divide m, the last big panel of
+    each restart cycle holds the remaining m mod s^ columns: stage 2 also runs
+    at the restart (the reading that Table 2's counts for s^ = 40, m = 60
+    imply: 60280 = 1004 * 60 + 40).  ``theta`` is None (monomial basis), s Newton shifts,
     or "auto": the first cycle runs with s = s^ = 1 (standard GMRES through the
     same block machinery), ``newton_shifts`` turns its Hessenberg matrix into s
     shifts, and every later cycle uses the Newton basis with them, scaled by
@@ -305,8 +308,8 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
         panel = m
     if ortho != "two_stage":
         panel = s
-    if m % s or panel % s or m % panel:
-        raise ValueError("need s | panel | m")
+    if m % s or panel % s or panel > m:
+        raise ValueError("need s | panel, s | m and panel <= m")
     panel_req = panel
     minv = None
     if precond is not None:
@@ -380,7 +383,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
                     t = st + s
                     if t < hi:
                         continue
-                    where_blk = m // s + (t // panel) - 1
+                    where_blk = m // s + (t - 1) // panel
                     st2 = bo.stage2_shifted if (shift and not lowp) else bo.stage2
                     Qn, P2, T2 = st2(Q[:, :lo].astype(f64), Q[:, lo:t + 1].astype(f64), f"cycle{cyc}/stage2@{t}")
                     Q[:, lo:t + 1] = Qn
@@ -391,7 +394,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
                     Rfin[:lo, lo:t + 1] = top
                     Rfin[lo:t + 1, lo:t + 1] = diag
                     c_lo = max(lo - 1, 0)
-                    lo, hi = t + 1, t + panel
+                    lo, hi = t + 1, min(t + panel, m)
                 else:
                     fn = bo.bcgs_pip2 if ortho == "bcgs_pip2" else bo.bcgs2_cholqr2
                     Qj, P, T = fn(Q[:, : st + 1].astype(f64), W.astype(f64), f"cycle{cyc}/block{j}")

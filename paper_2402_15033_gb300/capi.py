@@ -88,6 +88,9 @@ SIGNATURES = {
     "ortho_stage1": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "ortho_stage1_shifted": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "gmres_precond_apply": (_i32, [_vp, _vp, _vp]),
+    "ortho_plan_create": (_i32, [_vp, _i64, _i32, _i32, _i32, _vp]),
+    "ortho_plan_run": (_i32, [_vp, _vp, _i64, _vp, _i64, _vp, _vp, _i32, _i32, _vp]),
+    "ortho_plan_destroy": (_i32, [_vp]),
     "ortho_stage2": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
     "gmres_mpk": (_i32, [_vp, _vp, _vp, _i64, _i32, _dbl, C.POINTER(_dbl)]),
     "ortho_gram_chol": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i32, _vp, _sz, _vp]),
@@ -467,6 +470,49 @@ def ortho_stage1_noalloc(Q, V, R, status, k=None, stream=None):
                                              C.c_void_p(V.data_ptr()), int(V.stride(1)), int(nb),
                                              C.c_void_p(R.data_ptr()), int(R.stride(1)),
                                              C.c_void_p(status.data_ptr())))
+
+
+class OrthoPlan:
+    """ortho_plan_create / _run / _destroy: the two-stage orthogonalization of
+    an n x (1 + s nblk) panel in one call, on host (numpy or pinned torch CPU
+    tensors) or device (torch CUDA tensors) buffers."""
+
+    def __init__(self, n, s, nblk, arith=GMRES_ARITH_TC, stream=None):
+        h = C.c_void_p()
+        check(load().ortho_plan_create(C.byref(h), int(n), int(s), int(nblk), int(arith), C.c_void_p(stream or 0)))
+        self.h, self.n, self.ncol = h, int(n), 1 + int(s) * int(nblk)
+        self.nblk = int(nblk)
+
+    @staticmethod
+    def _addr(t):
+        return C.c_void_p(t.data_ptr()) if hasattr(t, "data_ptr") else t.ctypes.data_as(C.c_void_p)
+
+    def run(self, X, Q, Rhat=None, R2=None, on_device=None):
+        """X, Q: column-major (n x ncol) views (``t.T`` of a (ncol, ld) tensor, or
+        Fortran-ordered numpy arrays); Rhat, R2: (ncol x ncol) column-major or
+        None.  Returns (status, block statuses)."""
+        if on_device is None:
+            on_device = bool(getattr(X, "is_cuda", False))
+        ld = lambda a: (a.stride(1) if hasattr(a, "stride") and callable(a.stride) else a.strides[1] // 8)
+        st = (C.c_int32 * (self.nblk + 1))()
+        ldr = ld(Rhat) if Rhat is not None else (ld(R2) if R2 is not None else self.ncol)
+        rc = load().ortho_plan_run(self.h, self._addr(X), int(ld(X)), self._addr(Q), int(ld(Q)),
+                                   self._addr(Rhat) if Rhat is not None else None,
+                                   self._addr(R2) if R2 is not None else None, int(ldr), int(on_device), st)
+        if rc < 0 and rc != GMRES_ERR_BREAKDOWN:
+            raise GmresError(rc, last_error())
+        return rc, list(st)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().ortho_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ortho_stage1(Q, V, R, work, status, k=None, stream=None):

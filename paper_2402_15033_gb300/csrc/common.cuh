@@ -50,7 +50,7 @@ constexpr int kPipShift = 4;      // Gram kernel: factor G - P^T P + sigma I (sh
 // Arithmetic of the Gram and update kernels (gmres_opts.arith).
 constexpr int kArithFP64 = 0;     // native FP64 pipe (default)
 constexpr int kArithDD = 1;       // double-float on the FP32 pipe (df.cuh), ~2^-48 relative
-constexpr int kArithTC = 2;       // Gram on the bf16 tensor cores by exact slicing (gram_tc.cuh)
+constexpr int kArithTC = 2;       // Gram and update on the f16 tensor cores by exact slicing (tc_common.cuh)
 
 // ---------------------------------------------------------------- launchers
 // BCGS-PIP step 1+2: [P; G] = [Q, V]^T V split over n rows; the last CTA to

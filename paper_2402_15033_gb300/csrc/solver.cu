@@ -155,14 +155,25 @@ CycleBasis first_cycle_basis(const gmres_opts& o, double sigma) {
     return cb;
 }
 
+// Big panels of a restart cycle: stage 2 runs at every multiple of the panel
+// width and at the restart (t = m), so that when the width does not divide m
+// the last panel holds the remaining m mod width columns.  The first panel
+// starts at column 0 (it holds s^ + 1 vectors), later ones after the previous
+// panel's last column.
+static bool panel_end(int t, int panel, int m) { return t % panel == 0 || t == m; }
+static int panel_start(int t, int panel) {
+    const int prev = (t - 1) / panel * panel;
+    return prev == 0 ? 0 : prev + 1;
+}
+
 size_t pip_bytes_for(int64_t n, const gmres_opts& o) {
     size_t wb = 0;
     auto cover = [&](int s, int panel) {
         for (int st0 = 0; st0 < o.m; st0 += s) {
             wb = std::max(wb, ortho_workspace_bytes(n, st0 + 1, s));
             const int t = st0 + s;
-            if (t % panel == 0) {
-                const int lo = (t == panel) ? 0 : t - panel + 1;
+            if (panel_end(t, panel, o.m)) {
+                const int lo = panel_start(t, panel);
                 wb = std::max(wb, ortho_workspace_bytes(n, lo, t - lo + 1));
             }
         }
@@ -214,7 +225,8 @@ static int check_opts(const gmres_opts* o) {
     GM_ARG(o->basis == GMRES_BASIS_MONOMIAL || o->basis == GMRES_BASIS_NEWTON || o->basis == GMRES_BASIS_NEWTON_AUTO,
            "unknown basis");
     const int panel = o->ortho != GMRES_ORTHO_TWO_STAGE ? o->s : o->panel;
-    GM_ARG(panel >= o->s && panel % o->s == 0 && o->m % panel == 0, "need s | panel | m");
+    GM_ARG(panel >= o->s && panel % o->s == 0 && o->m % o->s == 0 && panel <= o->m,
+           "need s | panel, s | m and panel <= m");
     GM_ARG(o->sigma >= 0.0 && std::isfinite(o->sigma), "sigma must be >= 0");
     GM_ARG(o->arith == GMRES_ARITH_DD || o->arith == GMRES_ARITH_FP64 || o->arith == GMRES_ARITH_TC,
            "unknown arith");
@@ -473,7 +485,8 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
     CK(cuda_rc(cudaStreamSynchronize(s), "sync"));
     if (o.timing) {
         const CycleBasis f = first_cycle_basis(o, c->sigma);
-        const int per_cycle = 2 * (2 * (o.m / std::min(o.s, f.s)) + 2 * (o.m / std::min(o.panel, f.panel))) + 2;
+        const int per_cycle =
+            2 * (2 * (o.m / std::min(o.s, f.s)) + 2 * ((o.m + std::min(o.panel, f.panel) - 1) / std::min(o.panel, f.panel))) + 2;
         c->ev.resize(per_cycle);
         for (auto& e : c->ev) CK(cuda_rc(cudaEventCreate(&e), "cudaEventCreate"));
     }
@@ -594,8 +607,8 @@ static int run_cycle(gmres_ctx* c, const CycleBasis& cb, std::vector<std::pair<i
         }
         if (e == cudaSuccess) e = mark(PH_S1);
         const int t = st0 + cb.s;
-        if (e == cudaSuccess && t % cb.panel == 0) {
-            const int lo = (t == cb.panel) ? 0 : t - cb.panel + 1;
+        if (e == cudaSuccess && panel_end(t, cb.panel, o.m)) {
+            const int lo = panel_start(t, cb.panel);
             const int np = t - lo + 1;
             e = mark(PH_S2);
             w = pip_work_layout(c->pip_work, c->n, lo, np);
@@ -755,7 +768,7 @@ int run_decide(SolveRun* R) {
     r.relres_true = h.beta / R->bnorm;
     if (cyc > 0) r.relres_implicit = h.resid / R->bnorm;
     const int nb1 = o.m / R->ran.s;
-    const int nstat = nb1 + o.m / R->ran.panel;
+    const int nstat = nb1 + (o.m + R->ran.panel - 1) / R->ran.panel;
     for (int i = 0; i < nstat; ++i) {
         if (h.blkstat[i]) {
             r.breakdown_block = i;

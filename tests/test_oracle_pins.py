@@ -488,6 +488,11 @@ def test_convergence_tests_fall_on_panel_boundaries():
         _, info = kr.sstep_gmres(A, b, m=60, s=5, panel=panel, tol=1e-8, ortho=ortho)
         assert info["status"] == 0
         assert info["iters"] % step == 0
+    # s^ = 40 with m = 60: big panels of 40 and 20 columns per cycle, so the
+    # tests fall at 60 c + 40 and 60 c + 60, as Table 2's 60280 = 1004 * 60 + 40
+    assert gold["table2"]["two_stage"]["40"] % 60 == 40
+    _, info = kr.sstep_gmres(A, b, m=60, s=5, panel=40, tol=1e-8)
+    assert info["status"] == 0 and info["iters"] % 60 in (0, 40)
 
 
 def _krylov_minimizer(A, b, x0, m):
@@ -508,7 +513,8 @@ def _krylov_minimizer(A, b, x0, m):
 
 @pytest.mark.parametrize("ortho,s,panel,theta", [("two_stage", 5, 15, None), ("bcgs_pip2", 5, 5, None),
                                                  ("bcgs2_cholqr2", 5, 5, None),
-                                                 ("two_stage", 5, 15, (2.3, 1.7, 2.0, 1.5, 2.5))])
+                                                 ("two_stage", 5, 15, (2.3, 1.7, 2.0, 1.5, 2.5)),
+                                                 ("two_stage", 5, 10, None)])
 def test_one_cycle_is_the_minimal_residual_iterate(ortho, s, panel, theta):
     """GMRES' defining property (§I, §III): one restart cycle of m steps from
     x0 returns the minimizer of ||b - A x|| over x0 + K_m(A, r0), whatever the
