@@ -606,7 +606,7 @@ def solver_numbers(capi, dev, args):
         tab = tts_table(2048, c2, 1)
         base = tab["bcgs2_cholqr2_fp64"]["time_to_solution_ms"]
         for v in tab.values():
-            v["speedup_vs_bcgs2_cholqr2_fp64"] = round(base / v["time_to_solution_ms"], 3)
+            v["speedup_vs_bcgs2_cholqr2_fp64"] = round(base / v["time_to_solution_ms"], 3) if v["status"] == 0 else None
         out["laplace2048_time_to_solution"] = tab
 
         # one restart cycle per scheme and s^, per phase (Table 2's columns)

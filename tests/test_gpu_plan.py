@@ -46,7 +46,9 @@ def test_plan_equals_the_ortho_calls_on_host_and_device(lib, n, s, nblk, tc):
     ncol = 1 + s * nblk
     X = synth.tall_basis(n, ncol, seed=21)
     X[:, 0] /= np.linalg.norm(X[:, 0])
-    ref_Q, ref_Rh, ref_R2 = calls(capi, torch.tensor(X.T.copy(), device="cuda").T, s, nblk, tc)
+    buf = torch.zeros(ncol, n + n % 2, dtype=torch.float64, device="cuda")    # 16-byte aligned columns
+    buf[:, :n] = torch.tensor(X.T.copy())
+    ref_Q, ref_Rh, ref_R2 = calls(capi, buf.T[:n], s, nblk, tc)
     plan = capi.OrthoPlan(n, s, nblk, capi.GMRES_ARITH_TC if tc else capi.GMRES_ARITH_FP64)
     # host buffers (page-locked), two runs in a row
     Xh = torch.tensor(X.T.copy()).pin_memory()
@@ -76,7 +78,7 @@ def test_plan_reports_a_breakdown(lib):
     ncol = 1 + s * nblk
     X = synth.tall_basis(n, ncol, seed=22)
     X[:, 0] /= np.linalg.norm(X[:, 0])
-    X[:, 8] = X[:, 7]                         # block 1 is rank deficient
+    X[:, 8] = 0.0                             # block 1 holds a zero column: its Gram is singular
     plan = capi.OrthoPlan(n, s, nblk, capi.GMRES_ARITH_FP64)
     Q = np.empty_like(X, order="F")
     rc, st = plan.run(np.asfortranarray(X), Q, on_device=False)
