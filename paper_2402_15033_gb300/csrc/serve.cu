@@ -4,17 +4,22 @@
 // are queued on submit.  A worker thread repeats:
 //   1. admission: in arrival order, while the next request's device footprint
 //      (gmres_footprint: basis (m+1) n, CSR, workspace) fits the free memory
-//      budget and a slot is free, create its context on a stream of its own;
-//   2. one restart cycle for every active request, all enqueued before any
-//      waits, so the GPU overlaps their kernels;
-//   3. a convergence check per request (the FP64 restart residual); finished
-//      requests copy x out, release their memory and slot, and record their
-//      latency (submit to completion).
-// A request admitted while others are running joins them at the next cycle
-// boundary.  Every request keeps its Krylov basis, Hessenberg and Givens
-// state resident on the device until it finishes.  Each solve runs the same
-// kernels with the same reduction order as a lone gmres_solve, so its result
-// does not depend on what else is being served.
+//      budget and a slot is free, create its context in that slot and enqueue
+//      its first convergence check;
+//   2. a pass over the active requests that polls each one's stream: a request
+//      whose check has completed is decided at once and, if it goes on, gets
+//      its next restart cycle and the check after it enqueued back to back, so
+//      no request waits for another's cycle (the GPU overlaps their kernels);
+//   3. finished requests copy x out, return their memory and slot, and record
+//      their latency (submit to completion).
+// A request admitted while others are running joins them at once.  Every
+// request keeps its Krylov basis, Hessenberg and Givens state resident on the
+// device until it finishes.  Nothing on the worker's path allocates or frees
+// with a device-wide synchronization: the slots (stream, capture stream,
+// page-locked state mirror) are created with the server, and each context's
+// device buffers come from the server's stream-ordered memory pool, reserved
+// at start.  Each solve runs the same kernels with the same reduction order as
+// a lone gmres_solve, so its result does not depend on what else is served.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -45,6 +50,7 @@ struct Request {
     size_t bytes = 0;
     double t_submit = 0, t_admit = 0, t_done = 0;
     cudaStream_t stream = nullptr;
+    int slot = -1;
     gmres_ctx* ctx = nullptr;
     SolveRun run;
     gmres_result res{};
@@ -73,17 +79,22 @@ struct gmres_server {
     int64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, failed = 0;
     double t_first_submit = -1, t_last_done = -1;
     std::thread worker;
+    cudaMemPool_t pool = nullptr;
+    std::vector<CtxSlot> slots;
+    std::vector<cudaStream_t> streams;
+    std::vector<int> free_slots;
 };
 
 namespace {
 
 void retire(gmres_server* S, Request* q) {
     q->t_done = now_s();
-    gmres_destroy(q->ctx);
+    gmres_destroy(q->ctx);    // waits for this request's stream only; buffers go back to the pool
     q->ctx = nullptr;
-    if (q->stream) cudaStreamDestroy(q->stream);
-    q->stream = nullptr;
     std::lock_guard<std::mutex> lk(S->mu);
+    if (q->slot >= 0) S->free_slots.push_back(q->slot);
+    q->slot = -1;
+    q->stream = nullptr;
     S->used -= q->bytes;
     q->done = true;
     S->finished[q->id] = q;
@@ -94,87 +105,93 @@ void retire(gmres_server* S, Request* q) {
     S->cv_done.notify_all();
 }
 
-// Create the request's context and start its solve; errors finish the request.
-void admit_one(gmres_server* S, Request* q) {
+void finish(gmres_server* S, Request* q) {
+    int rc = run_finish(&q->run, q->x.data());
+    q->res = q->run.r;
+    q->status = rc ? rc : q->run.status;
+    q->res.status = q->status;
+    retire(S, q);
+}
+
+// Create the request's context in its slot and enqueue its first check;
+// returns false when the request finished already (an error or b = 0).
+bool admit_one(gmres_server* S, Request* q) {
     q->t_admit = now_s();
-    int rc = cudaStreamCreateWithFlags(&q->stream, cudaStreamNonBlocking) == cudaSuccess ? GMRES_OK : GMRES_ERR_CUDA;
-    if (!rc)
-        rc = gmres_create(&q->ctx, q->n, q->rowptr[q->n], q->rowptr.data(), q->colind.data(), q->vals.data(), 0,
-                          &q->opts, q->stream);
+    q->stream = S->streams[q->slot];
+    int rc = create_ctx(&q->ctx, q->n, q->rowptr[q->n], q->rowptr.data(), q->colind.data(), q->vals.data(), 0,
+                        &q->opts, q->stream, &S->slots[q->slot]);
     if (!rc) rc = run_begin(q->ctx, &q->run, q->b.data(), q->x.data(), 0);
     if (rc) {
         q->status = rc;
         q->res.status = rc;
         retire(S, q);
-        return;
+        return false;
     }
-    std::lock_guard<std::mutex> lk(S->mu);
-    S->active.push_back(q);
+    if (q->run.finished) {
+        finish(S, q);
+        return false;
+    }
+    if (run_enqueue_check(&q->run)) {
+        q->run.status = GMRES_ERR_CUDA;
+        finish(S, q);
+        return false;
+    }
+    return true;
 }
 
 void worker_main(gmres_server* S) {
     cudaSetDevice(S->device);
+    std::vector<Request*> act;
     for (;;) {
         std::vector<Request*> admit;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv_work.wait_for(lk, std::chrono::milliseconds(20), [&] {
-                return S->stopping || !S->pending.empty() || !S->active.empty();
-            });
-            while (!S->pending.empty() && (int)(S->active.size() + admit.size()) < S->max_active &&
+            if (act.empty())
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(20),
+                                    [&] { return S->stopping || !S->pending.empty(); });
+            while (!S->pending.empty() && !S->free_slots.empty() &&
                    S->used + S->pending.front()->bytes <= S->budget) {
                 Request* q = S->pending.front();
                 S->pending.pop_front();
                 S->used += q->bytes;
                 ++S->admitted;
+                q->slot = S->free_slots.back();
+                S->free_slots.pop_back();
                 admit.push_back(q);
             }
-            if (S->stopping && S->pending.empty() && S->active.empty() && admit.empty()) return;
+            if (S->stopping && S->pending.empty() && act.empty() && admit.empty()) return;
         }
-        for (Request* q : admit) admit_one(S, q);
-        std::vector<Request*> act;
-        {
-            std::lock_guard<std::mutex> lk(S->mu);
-            act = S->active;
-        }
-        if (act.empty()) continue;
-        // one convergence check + (if needed) one restart cycle per active request,
-        // enqueued for all of them before any wait
-        for (Request* q : act) {
-            if (!q->run.finished) {
-                int rc = run_enqueue_check(&q->run);
-                if (rc) { q->run.finished = true; q->run.status = rc; }
-            }
-        }
+        for (Request* q : admit)
+            if (admit_one(S, q)) act.push_back(q);
+        // one polling pass: every request whose check has landed moves on
+        bool progressed = false;
         std::vector<Request*> still;
         for (Request* q : act) {
-            bool stop = q->run.finished;
-            if (!stop) {
-                if (cudaStreamSynchronize(q->stream) != cudaSuccess) {
-                    q->run.status = GMRES_ERR_CUDA;
-                    stop = true;
-                } else if (run_decide(&q->run)) {
-                    stop = true;
-                } else if (run_enqueue_cycle(&q->run)) {
-                    q->run.status = GMRES_ERR_CUDA;
-                    stop = true;
-                }
-            }
-            if (stop) {
-                int rc = run_finish(&q->run, q->x.data());
-                q->res = q->run.r;
-                q->status = rc ? rc : q->run.status;
-                q->res.status = q->status;
-                retire(S, q);
-            } else {
+            const cudaError_t qe = cudaStreamQuery(q->stream);
+            if (qe == cudaErrorNotReady) {
                 still.push_back(q);
+                continue;
             }
+            progressed = true;
+            bool stop = false;
+            if (qe != cudaSuccess) {
+                q->run.status = GMRES_ERR_CUDA;
+                stop = true;
+            } else if (run_decide(&q->run)) {
+                stop = true;
+            } else if (run_enqueue_cycle(&q->run) || run_enqueue_check(&q->run)) {
+                q->run.status = GMRES_ERR_CUDA;
+                stop = true;
+            }
+            if (stop) finish(S, q);
+            else still.push_back(q);
         }
-        std::lock_guard<std::mutex> lk(S->mu);
-        std::vector<Request*> keep;
-        for (Request* q : S->active)
-            if (std::find(still.begin(), still.end(), q) != still.end()) keep.push_back(q);
-        S->active.swap(keep);
+        act.swap(still);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->active = act;
+        }
+        if (!progressed && admit.empty() && !act.empty()) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
 }
 
@@ -209,6 +226,40 @@ int gmres_server_start(gmres_server** out, size_t mem_budget, int32_t max_active
     }
     S->budget = mem_budget;
     S->max_active = max_active;
+    // the slots and the memory pool, before any request: the worker never
+    // creates a stream, allocates page-locked memory or frees device memory
+    // with a device-wide synchronization
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = S->device;
+    cudaError_t e = cudaMemPoolCreate(&S->pool, &props);
+    if (e == cudaSuccess) {
+        unsigned long long thr = (unsigned long long)mem_budget;
+        e = cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    S->slots.resize(max_active);
+    S->streams.resize(max_active, nullptr);
+    for (int i = 0; i < max_active && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&S->streams[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->slots[i].capture, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaMallocHost(&S->slots[i].host_state, sizeof(DevState));
+        S->slots[i].pool = S->pool;
+        S->free_slots.push_back(max_active - 1 - i);
+    }
+    if (e == cudaSuccess && !S->streams.empty()) {
+        // reserve up to 16 GB of the budget in the pool now; beyond that it grows on demand
+        void* p = nullptr;
+        const size_t reserve = std::min<size_t>(mem_budget, (size_t)16 << 30);
+        e = cudaMallocFromPoolAsync(&p, reserve, S->pool, S->streams[0]);
+        if (e == cudaSuccess) e = cudaFreeAsync(p, S->streams[0]);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->streams[0]);
+    }
+    if (e != cudaSuccess) {
+        set_error("gmres_server_start: %s", cudaGetErrorString(e));
+        gmres_server_stop(S);
+        return e == cudaErrorMemoryAllocation ? GMRES_ERR_OOM : GMRES_ERR_CUDA;
+    }
     S->worker = std::thread(worker_main, S);
     *out = S;
     return GMRES_OK;
@@ -324,6 +375,15 @@ int gmres_server_stop(gmres_server* S) {
     S->cv_work.notify_all();
     if (S->worker.joinable()) S->worker.join();
     for (auto& kv : S->finished) delete kv.second;
+    for (size_t i = 0; i < S->slots.size(); ++i) {
+        if (S->streams[i]) {
+            cudaStreamSynchronize(S->streams[i]);
+            cudaStreamDestroy(S->streams[i]);
+        }
+        if (S->slots[i].capture) cudaStreamDestroy(S->slots[i].capture);
+        if (S->slots[i].host_state) cudaFreeHost(S->slots[i].host_state);
+    }
+    if (S->pool) cudaMemPoolDestroy(S->pool);
     delete S;
     return GMRES_OK;
 }

@@ -95,6 +95,11 @@ struct gmres_ctx {
     };
     cudaStream_t cap = nullptr;
     CycleGraph graphs[2];
+    // serving: device buffers from the server's memory pool (stream-ordered,
+    // no device-wide synchronization), and the slot's capture stream and
+    // page-locked state mirror, all owned by the server
+    cudaMemPool_t pool = nullptr;
+    bool external_slot = false;
     unsigned long long graph_tick = 0;
     bool no_graphs = false;
 };
@@ -212,6 +217,26 @@ size_t ctx_bytes(int64_t n, int64_t nnz, const gmres_opts& o) {
 
 }  // namespace gm
 
+namespace gm {
+
+// Device memory of a context: cudaMalloc, or the server's pool (stream
+// ordered on the context's stream).
+static cudaError_t dev_malloc(gmres_ctx* c, void** p, size_t bytes) {
+    if (c->pool) return cudaMallocFromPoolAsync(p, bytes, c->pool, c->stream);
+    return cudaMalloc(p, bytes);
+}
+template <typename P>
+static cudaError_t dev_malloc(gmres_ctx* c, P** p, size_t bytes) {
+    return dev_malloc(c, reinterpret_cast<void**>(p), bytes);
+}
+static void dev_free(gmres_ctx* c, void* p) {
+    if (!p) return;
+    if (c->pool) cudaFreeAsync(p, c->stream);
+    else cudaFree(p);
+}
+
+}  // namespace gm
+
 extern "C" {
 static int check_opts(const gmres_opts* o) {
     GM_ARG(o->m >= 1 && o->m + 1 <= kMaxCols, "m must be in [1, %d]", kMaxCols - 1);
@@ -244,28 +269,17 @@ int gmres_destroy(gmres_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     for (auto e : c->ev) cudaEventDestroy(e);
-    cudaFree(c->A.rowptr);
-    cudaFree(c->A.colind);
-    cudaFree(c->A.vals);
-    cudaFree(c->A.vals32);
-    cudaFree(c->r);
-    cudaFree(c->basis);
-    cudaFree(c->b);
-    cudaFree(c->x);
-    cudaFree(c->red_partial);
-    cudaFree(c->red_counter);
-    cudaFree(c->pip_work);
-    cudaFree(c->bscr);
-    cudaFree(c->digits);
-    cudaFree(c->gs.perm);
-    cudaFree(c->gs.diag);
-    cudaFree(c->gs.z);
-    cudaFree(c->gs.t);
-    cudaFree(c->st);
-    cudaFreeHost(c->hst);
     for (auto& g : c->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
-    if (c->cap) cudaStreamDestroy(c->cap);
+    for (void* p : {(void*)c->A.rowptr, (void*)c->A.colind, (void*)c->A.vals, (void*)c->A.vals32, (void*)c->r,
+                    c->basis, (void*)c->b, (void*)c->x, (void*)c->red_partial, (void*)c->red_counter, c->pip_work,
+                    (void*)c->bscr, c->digits, (void*)c->gs.perm, (void*)c->gs.diag, (void*)c->gs.z, (void*)c->gs.t,
+                    (void*)c->st})
+        dev_free(c, p);
+    if (!c->external_slot) {
+        cudaFreeHost(c->hst);
+        if (c->cap) cudaStreamDestroy(c->cap);
+    }
     delete c;
     return GMRES_OK;
 }
@@ -329,20 +343,20 @@ static int setup_mcgs(gmres_ctx* c) {
         std::vector<int64_t> fill(c->gs.off.begin(), c->gs.off.end() - 1);
         for (int64_t i = 0; i < n; ++i) perm[fill[color[i]]++] = (int32_t)i;
     }
-    int rc = cuda_rc(cudaMalloc(&c->gs.perm, n * sizeof(int32_t)), "cudaMalloc Gauss-Seidel order");
-    if (!rc) rc = cuda_rc(cudaMalloc(&c->gs.diag, c->ldq * sizeof(double)), "cudaMalloc diagonal");
-    if (!rc) rc = cuda_rc(cudaMalloc(&c->gs.z, c->ldq * sizeof(double)), "cudaMalloc Gauss-Seidel vector");
-    if (!rc) rc = cuda_rc(cudaMalloc(&c->gs.t, c->ldq * sizeof(double)), "cudaMalloc Gauss-Seidel vector");
+    int rc = cuda_rc(dev_malloc(c, &c->gs.perm, n * sizeof(int32_t)), "cudaMalloc Gauss-Seidel order");
+    if (!rc) rc = cuda_rc(dev_malloc(c, &c->gs.diag, c->ldq * sizeof(double)), "cudaMalloc diagonal");
+    if (!rc) rc = cuda_rc(dev_malloc(c, &c->gs.z, c->ldq * sizeof(double)), "cudaMalloc Gauss-Seidel vector");
+    if (!rc) rc = cuda_rc(dev_malloc(c, &c->gs.t, c->ldq * sizeof(double)), "cudaMalloc Gauss-Seidel vector");
     if (rc) return rc;
     int32_t* bad = nullptr;
     e = cudaMemcpyAsync(c->gs.perm, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMalloc(&bad, sizeof(int32_t));
+    if (e == cudaSuccess) e = dev_malloc(c, &bad, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = launch_diag(s, c->A, c->gs.diag, bad);
     int32_t hb = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(bad);
+    dev_free(c, bad);
     if (e != cudaSuccess) return cuda_rc(e, "Gauss-Seidel set-up");
     if (hb) {
         set_error("the Gauss-Seidel preconditioner needs a nonzero, finite diagonal in every row");
@@ -353,6 +367,16 @@ static int setup_mcgs(gmres_ctx* c) {
 
 int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colind,
                  const double* vals, int32_t ptr_on_device, const gmres_opts* opts, void* stream) {
+    return create_ctx(out, n, nnz, rowptr, colind, vals, ptr_on_device, opts, stream, nullptr);
+}
+
+}  // extern "C"
+
+namespace gm {
+
+int create_ctx(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colind,
+               const double* vals, int32_t ptr_on_device, const gmres_opts* opts, void* stream,
+               const CtxSlot* slot) {
     clear_error();
     GM_ARG(out != nullptr, "out is NULL");
     *out = nullptr;
@@ -370,6 +394,12 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
     c->opts = o;
     c->n = n;
     c->stream = static_cast<cudaStream_t>(stream);
+    if (slot) {
+        c->pool = slot->pool;
+        c->cap = slot->capture;
+        c->hst = slot->host_state;
+        c->external_slot = true;
+    }
     CK(cuda_rc(cudaGetDevice(&c->device), "cudaGetDevice"));
     cudaStream_t s = c->stream;
     c->ldq = (n + 31) / 32 * 32;
@@ -377,16 +407,16 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
 
     c->A.n = n;
     c->A.nnz = nnz;
-    CK(cuda_rc(cudaMalloc(&c->A.rowptr, (n + 1) * sizeof(int32_t)), "cudaMalloc rowptr"));
-    CK(cuda_rc(cudaMalloc(&c->A.colind, (nnz > 0 ? nnz : 1) * sizeof(int32_t)), "cudaMalloc colind"));
-    CK(cuda_rc(cudaMalloc(&c->A.vals, (nnz > 0 ? nnz : 1) * sizeof(double)), "cudaMalloc vals"));
+    CK(cuda_rc(dev_malloc(c, &c->A.rowptr, (n + 1) * sizeof(int32_t)), "cudaMalloc rowptr"));
+    CK(cuda_rc(dev_malloc(c, &c->A.colind, (nnz > 0 ? nnz : 1) * sizeof(int32_t)), "cudaMalloc colind"));
+    CK(cuda_rc(dev_malloc(c, &c->A.vals, (nnz > 0 ? nnz : 1) * sizeof(double)), "cudaMalloc vals"));
     if (ptr_on_device) {
         int64_t* tmp = nullptr;
-        CK(cuda_rc(cudaMalloc(&tmp, (n + 1) * sizeof(int64_t)), "cudaMalloc tmp"));
+        CK(cuda_rc(dev_malloc(c, &tmp, (n + 1) * sizeof(int64_t)), "cudaMalloc tmp"));
         cudaError_t e = cudaMemcpyAsync(tmp, rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = launch_rowptr_narrow(s, n + 1, tmp, c->A.rowptr, nnz);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        cudaFree(tmp);
+        dev_free(c, tmp);
         CK(cuda_rc(e, "rowptr copy"));
         if (nnz > 0) {
             CK(cuda_rc(cudaMemcpyAsync(c->A.colind, colind, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s), "colind copy"));
@@ -413,7 +443,7 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
     {
         int32_t* bad = nullptr;
         unsigned long long* mx = nullptr;
-        CK(cuda_rc(cudaMalloc(&bad, 16), "cudaMalloc"));
+        CK(cuda_rc(dev_malloc(c, &bad, 16), "cudaMalloc"));
         mx = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(bad) + 8);
         cudaError_t e = cudaMemsetAsync(bad, 0, 16, s);
         if (e == cudaSuccess) e = launch_validate_csr(s, n, nnz, c->A.rowptr, c->A.colind, bad);
@@ -421,7 +451,7 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
         unsigned long long hm = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess || hb) cudaFree(bad);
+        if (e != cudaSuccess || hb) dev_free(c, bad);
         CK(cuda_rc(e, "CSR validation"));
         if (hb) {
             set_error("invalid CSR (code %d): rowptr must start at 0, be nondecreasing and end at nnz; "
@@ -433,7 +463,7 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
         e = launch_rowabs(s, c->A, mx);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hm, mx, 8, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        cudaFree(bad);
+        dev_free(c, bad);
         CK(cuda_rc(e, "row sums"));
         double rmax;
         std::memcpy(&rmax, &hm, 8);
@@ -443,38 +473,38 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
     }
     if (o.precond == GMRES_PRECOND_MCGS) CK(setup_mcgs(c));
     const size_t esz = o.precision == GMRES_PREC_MIXED ? sizeof(float) : sizeof(double);
-    CK(cuda_rc(cudaMalloc(&c->basis, (size_t)mp1 * c->ldq * esz), "cudaMalloc basis"));
+    CK(cuda_rc(dev_malloc(c, &c->basis, (size_t)mp1 * c->ldq * esz), "cudaMalloc basis"));
     CK(cuda_rc(cudaMemsetAsync(c->basis, 0, (size_t)mp1 * c->ldq * esz, s), "memset basis"));
     if (o.precision == GMRES_PREC_MIXED) {
-        CK(cuda_rc(cudaMalloc(&c->A.vals32, (nnz > 0 ? nnz : 1) * sizeof(float)), "cudaMalloc vals32"));
+        CK(cuda_rc(dev_malloc(c, &c->A.vals32, (nnz > 0 ? nnz : 1) * sizeof(float)), "cudaMalloc vals32"));
         if (nnz > 0) CK(cuda_rc(launch_narrow_vals(s, nnz, c->A.vals, c->A.vals32), "narrow vals"));
-        CK(cuda_rc(cudaMalloc(&c->r, c->ldq * sizeof(double)), "cudaMalloc r"));
+        CK(cuda_rc(dev_malloc(c, &c->r, c->ldq * sizeof(double)), "cudaMalloc r"));
     }
-    CK(cuda_rc(cudaMalloc(&c->b, c->ldq * sizeof(double)), "cudaMalloc b"));
-    CK(cuda_rc(cudaMalloc(&c->x, c->ldq * sizeof(double)), "cudaMalloc x"));
+    CK(cuda_rc(dev_malloc(c, &c->b, c->ldq * sizeof(double)), "cudaMalloc b"));
+    CK(cuda_rc(dev_malloc(c, &c->x, c->ldq * sizeof(double)), "cudaMalloc x"));
     const int ng = norm_grid(n);
-    CK(cuda_rc(cudaMalloc(&c->red_partial, ng * sizeof(double)), "cudaMalloc partial"));
-    CK(cuda_rc(cudaMalloc(&c->red_counter, 256), "cudaMalloc counter"));
+    CK(cuda_rc(dev_malloc(c, &c->red_partial, ng * sizeof(double)), "cudaMalloc partial"));
+    CK(cuda_rc(dev_malloc(c, &c->red_counter, 256), "cudaMalloc counter"));
     CK(cuda_rc(cudaMemsetAsync(c->red_counter, 0, 256, s), "memset counter"));
     // PIP workspace: the largest of the cycle's calls
     const size_t wb = pip_bytes_for(n, o);
     c->pip_bytes = wb;
-    CK(cuda_rc(cudaMalloc(&c->pip_work, wb), "cudaMalloc workspace"));
+    CK(cuda_rc(dev_malloc(c, &c->pip_work, wb), "cudaMalloc workspace"));
     CK(cuda_rc(cudaMemsetAsync(c->pip_work, 0, wb, s), "memset workspace"));
     if (uses_digits(o)) {
         const size_t db = tc_digits_bytes(n, o.m + 1);
-        CK(cuda_rc(cudaMalloc(&c->digits, db), "cudaMalloc digit basis"));
+        CK(cuda_rc(dev_malloc(c, &c->digits, db), "cudaMalloc digit basis"));
         CK(cuda_rc(cudaMemsetAsync(c->digits, 0, db, s), "memset digit basis"));
     }
     if (o.ortho == GMRES_ORTHO_BCGS2_CHOLQR2 || o.shift != GMRES_SHIFT_NONE) {
         // BCGS2-CholQR2: the five reductions' factors; shifted CholQR3: the
         // second and third stage-2 passes' factors and two combine blocks
         const size_t sb = 5 * (size_t)kMaxCols * kMaxCols * sizeof(double);
-        CK(cuda_rc(cudaMalloc(&c->bscr, sb), "cudaMalloc bcgs2 scratch"));
+        CK(cuda_rc(dev_malloc(c, &c->bscr, sb), "cudaMalloc bcgs2 scratch"));
         CK(cuda_rc(cudaMemsetAsync(c->bscr, 0, sb, s), "memset bcgs2 scratch"));
     }
-    CK(cuda_rc(cudaMalloc(&c->st, sizeof(DevState)), "cudaMalloc state"));
-    CK(cuda_rc(cudaMallocHost(&c->hst, sizeof(DevState)), "cudaMallocHost state"));
+    CK(cuda_rc(dev_malloc(c, &c->st, sizeof(DevState)), "cudaMalloc state"));
+    if (!slot) CK(cuda_rc(cudaMallocHost(&c->hst, sizeof(DevState)), "cudaMallocHost state"));
     std::memset(c->hst, 0, sizeof(DevState));
     c->hst->m = o.m;
     c->hst->s = o.s;
@@ -493,6 +523,10 @@ int gmres_create(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr,
     *out = c;
     return GMRES_OK;
 }
+
+}  // namespace gm
+
+extern "C" {
 
 
 }  // extern "C"

@@ -6,6 +6,20 @@
 
 namespace gm {
 
+// What a serving slot lends a context: a memory pool for its device buffers
+// (stream-ordered allocation, no device-wide synchronization), the stream to
+// capture its cycle graphs on, and a page-locked mirror of its DevState.
+struct CtxSlot {
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t capture = nullptr;
+    DevState* host_state = nullptr;
+};
+
+// gmres_create with an optional slot (nullptr: the context allocates and owns
+// everything, as gmres_create does).
+int create_ctx(gmres_ctx** out, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colind,
+               const double* vals, int32_t ptr_on_device, const gmres_opts* opts, void* stream, const CtxSlot* slot);
+
 struct SolveRun {
     gmres_ctx* c = nullptr;
     gmres_result r{};
