@@ -21,10 +21,12 @@
 // SM per clock (1.19 TFLOP/s measured): the Gram and the update are bound by
 // FP64 arithmetic, not by HBM, at the paper's block sizes.
 #include <algorithm>
+#include <cstdlib>
 #include <type_traits>
 #include "pip_body.cuh"
 #include "gram_tc.cuh"
 #include "gram_tcq.cuh"
+#include "gram_t5.cuh"
 #include "update_tc.cuh"
 #include "update_tcd.cuh"
 
@@ -102,6 +104,34 @@ cudaError_t launch_gram_tcq(cudaStream_t st, int64_t n, int k, const double* V, 
     const int G = std::min(grid, num_sms());
     gram_tcq_kernel<<<G, kGqThreads, gram_tcq_smem(k), st>>>(n, V, ldv, k, nb, R, ldr, w.partial, w.counter,
                                                              w.gram, d_status, d_skip, mode, dig, dex, capc);
+    return cudaGetLastError();
+}
+
+// Narrow Gram on the fifth-generation tensor cores (gram_t5.cuh): one
+// warp-specialized CTA per SM.
+__global__ void __launch_bounds__(kG5Threads, 1)
+gram_t5_kernel(int64_t n, const double* __restrict__ V, int64_t ldv, int k, int nb, double* __restrict__ R, int ldr,
+               double* partial, unsigned* counter, double* gram, int32_t* d_status, int32_t* d_skip, int mode,
+               const uint4* dig, const int* dex, int capc) {
+    extern __shared__ __align__(1024) char g5_smem[];
+    if (d_skip && *d_skip) return;
+    const int G = gridDim.x;
+    const size_t ps = (size_t)kMaxNB * nb;
+    gram_t5_part(n, V, ldv, k, nb, blockIdx.x, G, partial + blockIdx.x * ps, g5_smem, dig, dex, capc);
+    pip_finish(k, nb, 0, 1, G, R, ldr, partial, ps, counter, gram, d_status, d_skip,
+               reinterpret_cast<double*>(g5_smem), mode, n);
+}
+
+cudaError_t launch_gram_t5(cudaStream_t st, int64_t n, int k, const double* V, int64_t ldv, int nb, double* R,
+                           int ldr, const PipWork& w, int32_t* d_status, int32_t* d_skip, int grid, int mode,
+                           const void* digits, int capc) {
+    static const cudaError_t attr = smem_limit(gram_t5_kernel, kG5Smem);
+    if (attr != cudaSuccess) return attr;
+    const uint4* dig = static_cast<const uint4*>(digits);
+    const int* dex = reinterpret_cast<const int*>(dig + tc_digits_units(n, capc));
+    const int G = std::min(grid, num_sms());
+    gram_t5_kernel<<<G, kG5Threads, kG5Smem, st>>>(n, V, ldv, k, nb, R, ldr, w.partial, w.counter, w.gram, d_status,
+                                                   d_skip, mode, dig, dex, capc);
     return cudaGetLastError();
 }
 
@@ -498,6 +528,9 @@ cudaError_t launch_gram_tc_digits(cudaStream_t st, int64_t n, const double* Q, i
                                   int64_t ldv, int nb, double* R, int ldr, const PipWork& w, int32_t* d_status,
                                   int grid, const void* digits, int capc, int kc, int32_t* d_skip, int mode) {
     // narrow blocks against a Q held entirely in the digit basis: per-warp streaming
+    static const bool t5 = [] { const char* e = getenv("GMRES_T5"); return !(e && e[0] == '0'); }();
+    if (t5 && nb <= kG5MaxNB && kc == k && k + nb >= kG5MinKX && k + nb <= kG5MaxKX)
+        return launch_gram_t5(st, n, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode, digits, capc);
     if (nb <= kGqMaxNB && kc == k && k + nb <= kGqMaxKX)
         return launch_gram_tcq(st, n, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode, digits, capc);
     return launch_gram_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode, digits, capc, kc);
