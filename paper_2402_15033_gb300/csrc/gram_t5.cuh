@@ -37,6 +37,8 @@
 //               slice V's rows (a half warp per column, prefetched a chunk
 //               ahead) into A and B;
 //   warps 10-13 combiners: exchange, release the stage, combine, accumulate.
+// Role-internal hand-offs are mbarriers too (never bar.sync), so that a role
+// that gives up after a timed-out wait cannot leave another waiting forever.
 #pragma once
 #include "pip_body.cuh"
 #include "tc_common.cuh"
@@ -67,8 +69,9 @@ static_assert((size_t)128 * kG5RedLd * 4 <= (size_t)kG5ATile, "exchange tile fit
 __device__ void gram_t5_part(int64_t n, const double* __restrict__ V, int64_t ldv, int k, int nb, int b, int G,
                              double* slot, char* smem, const uint4* __restrict__ dig, const int* __restrict__ dex,
                              int capc) {
-    // [0..1] raw full, [2..3] raw empty, [4..5] A/B full, [6..7] MMAs done, [8..9] stage exchanged
-    __shared__ __align__(8) uint64_t bars[10];
+    // [0..1] raw full, [2..3] raw empty, [4..5] A/B full, [6..7] MMAs done, [8..9] stage exchanged,
+    // [10..11] exchange tile written
+    __shared__ __align__(8) uint64_t bars[12];
     __shared__ uint32_t tslot;
     __shared__ int exq[2][kG5MaxKX];            // a stage's Q column exponents
     __shared__ int vex[2][kG5MaxNB];            // its V column exponents
@@ -78,6 +81,7 @@ __device__ void gram_t5_part(int64_t n, const double* __restrict__ V, int64_t ld
     uint64_t* a_full = bars + 4;
     uint64_t* d_full = bars + 6;
     uint64_t* s_empty = bars + 8;
+    uint64_t* x_ready = bars + 10;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int kx = k + nb;
     smem += (1024 - (t5_smem(smem) & 1023)) & 1023;   // swizzle atoms are 1024-aligned
@@ -93,6 +97,7 @@ __device__ void gram_t5_part(int64_t n, const double* __restrict__ V, int64_t ld
             t5_bar_init(&a_full[q], 8);
             t5_bar_init(&d_full[q], 1);
             t5_bar_init(&s_empty[q], 4);
+            t5_bar_init(&x_ready[q], 4);
         }
         t5_bar_init_fence();
         s_fail = 0;
@@ -271,7 +276,10 @@ __device__ void gram_t5_part(int64_t n, const double* __restrict__ V, int64_t ld
                 }
             }
             t5_fence_before_sync();
-            t5_named_sync(1, 128);
+            __syncwarp();
+            if (lane == 0) t5_bar_arrive(&x_ready[s]);
+            if (!t5_bar_wait(&x_ready[s], (uint32_t)(u & 1))) s_fail = 1;
+            if (s_fail) break;
             // per (c, j): I_t = lane (0, c) column (t, j) + lane (1, c) column (t - 1, j),
             // combined exactly, then the FP64 accumulation S * 2^(E_c + E_j - 50)
             long long S[4];

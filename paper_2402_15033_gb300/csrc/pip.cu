@@ -21,7 +21,6 @@
 // SM per clock (1.19 TFLOP/s measured): the Gram and the update are bound by
 // FP64 arithmetic, not by HBM, at the paper's block sizes.
 #include <algorithm>
-#include <cstdlib>
 #include <type_traits>
 #include "pip_body.cuh"
 #include "gram_tc.cuh"
@@ -527,9 +526,10 @@ cudaError_t launch_pip_update(cudaStream_t st, int64_t n, const float* Q, int64_
 cudaError_t launch_gram_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, const double* V,
                                   int64_t ldv, int nb, double* R, int ldr, const PipWork& w, int32_t* d_status,
                                   int grid, const void* digits, int capc, int kc, int32_t* d_skip, int mode) {
-    // narrow blocks against a Q held entirely in the digit basis: per-warp streaming
-    static const bool t5 = [] { const char* e = getenv("GMRES_T5"); return !(e && e[0] == '0'); }();
-    if (t5 && nb <= kG5MaxNB && kc == k && k + nb >= kG5MinKX && k + nb <= kG5MaxKX)
+    // narrow blocks against a Q held entirely in the digit basis: wider than 32
+    // columns on tcgen05 (gram_t5.cuh), narrower ones on mma.sync with per-warp
+    // streaming (gram_tcq.cuh)
+    if (nb <= kG5MaxNB && kc == k && k + nb >= kG5MinKX && k + nb <= kG5MaxKX)
         return launch_gram_t5(st, n, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode, digits, capc);
     if (nb <= kGqMaxNB && kc == k && k + nb <= kGqMaxKX)
         return launch_gram_tcq(st, n, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode, digits, capc);

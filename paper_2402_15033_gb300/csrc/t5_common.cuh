@@ -61,10 +61,6 @@ __device__ __forceinline__ bool t5_bar_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ void t5_bar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(t5_smem(bar)) : "memory");
 }
-// Barrier among the `count` threads (whole warps) of a role, hardware barrier `id` (1..15).
-__device__ __forceinline__ void t5_named_sync(int id, int count) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
 // One arrival that also expects `bytes` of asynchronous copies in this phase.
 __device__ __forceinline__ void t5_bar_arrive_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(t5_smem(bar)), "r"(bytes) : "memory");
