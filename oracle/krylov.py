@@ -54,23 +54,57 @@ def mpk_sigma(A) -> float:
     return float(2.0 ** math.floor(math.log2(top)))
 
 
-def mpk(M, v: np.ndarray, s: int, sigma: float, theta=None, minv=None) -> np.ndarray:
+def mpk(M, v: np.ndarray, s: int, sigma: float, theta=None, minv=None, cheb=False) -> np.ndarray:
     """Matrix powers kernel, standard (non communication-avoiding) form (§III):
     s sparse matrix-vector products in sequence, w_1 = (A v - theta_0 v)/sigma,
     w_i = (A w_{i-1} - theta_{i-1} w_{i-1})/sigma.  With a right
     preconditioner (``minv`` applies M^{-1}) each product is A M^{-1} w (the
-    preconditioner applied with every SpMV, §I).  Returns the n x s block."""
+    preconditioner applied with every SpMV, §I).  ``cheb``: the three-term
+    recurrence of the Chebyshev basis (``cheb_coeffs``), with y_0 = v and
+    y_{i+1} = (A y_i - theta_i y_i - nu_i y_{i-1}) / sigma_i.  Returns the
+    n x s block [y_1 .. y_s]."""
     n = v.shape[0]
     dt = v.dtype
     W = np.zeros((n, s), dtype=dt)
-    prev = v
+    prev, prev2 = v, None
     for i in range(s):
         y = M @ (prev if minv is None else minv(prev))
         if theta is not None and theta[i] != 0.0:
             y = y - dt.type(theta[i]) * prev
-        W[:, i] = y / dt.type(sigma)
-        prev = W[:, i]
+        sig_i, nu_i = cheb_coeffs(i, sigma) if cheb else (sigma, 0.0)
+        if nu_i != 0.0:
+            y = y - dt.type(nu_i) * prev2
+        W[:, i] = y / dt.type(sig_i)
+        prev, prev2 = W[:, i], prev
     return W
+
+
+def cheb_coeffs(i: int, sigma: float):
+    """Coefficients (sigma_i, nu_i) of product i (0-based within an s-step block)
+    of the Chebyshev basis, A y_i = sigma_i y_{i+1} + c y_i + nu_i y_{i-1}: the
+    Chebyshev polynomials T_i((z - c) / delta) of the interval [c - delta,
+    c + delta] (Bai, Hu and Reichel 1994, named with the Newton basis in §VI),
+    T_1 = x, T_{i+1} = 2 x T_i - T_{i-1}, give sigma_0 = delta and sigma_i = nu_i
+    = delta / 2 for i >= 1; with sigma = delta / 2 that is (2 sigma, 0) for the
+    block's first product and (sigma, sigma) for the others."""
+    return (2.0 * sigma, 0.0) if i == 0 else (sigma, sigma)
+
+
+def cheb_interval(H):
+    """Interval [c - delta, c + delta] of the Chebyshev basis from the Ritz values
+    of a first standard GMRES cycle (the eigenvalues of the square k x k
+    Hessenberg matrix H_k): c and delta are the midpoint and half-length of the
+    range of their real parts.  Ritz values that span no interval give delta =
+    |c| (or 1 when c = 0), so that the basis stays defined."""
+    Hk = np.asarray(H, dtype=np.float64)
+    if Hk.shape[0] == 0:
+        return 0.0, 1.0
+    re = np.linalg.eigvals(Hk).real
+    lo, hi = float(re.min()), float(re.max())
+    c, d = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    if not (d > 0.0) or not math.isfinite(d):
+        d = abs(c) if c != 0.0 else 1.0
+    return c, d
 
 
 class Givens:
@@ -169,7 +203,7 @@ def gmres_cgs2(A, b, x0=None, m=60, tol=1e-8, max_restarts=1000):
     return x, dict(status=status, iters=iters, restarts=restarts, relres=hist[-1], history=hist)
 
 
-def hessenberg_columns(Rfin, C, start_final, s, sigma, theta, c_lo, c_hi, H):
+def hessenberg_columns(Rfin, C, start_final, s, sigma, theta, c_lo, c_hi, H, cheb=False):
     """Columns c_lo..c_hi-1 of the upper Hessenberg H with A Q_{1:k} = Q_{1:k+1} H.
 
     SpMV number c (0-based) reads input y_c and writes raw column c+1, with
@@ -178,19 +212,30 @@ def hessenberg_columns(Rfin, C, start_final, s, sigma, theta, c_lo, c_hi, H):
       a_c = C[:, c]    if c starts a block from a pre-processed column q^_c,
       a_c = Rfin[:, c] otherwise (y_c is the raw MPK output w_c);
       b_c = sigma Rfin[:, c+1] + theta_c a_c.
+    With the Chebyshev basis (``cheb``) A y_c = sigma_c w_{c+1} + theta_c y_c +
+    nu_c y_{c-1} (``cheb_coeffs`` of c mod s), so b_c = sigma_c Rfin[:, c+1] +
+    theta_c a_c + nu_c a_{c-1}; nu_c = 0 at a block's first column, so a_{c-1}
+    is always a column of the same block.
     With A_k = [a_0..a_{k-1}] upper triangular and B_k = [b_0..b_{k-1}],
     H = B_k A_k^{-1}, solved one column at a time (H A = B)."""
     mp1 = Rfin.shape[0]
-    for c in range(c_lo, c_hi):
+
+    def coords(c):
         if c % s == 0:
             a = np.zeros(mp1)
             if start_final[c]:
                 a[c] = 1.0
             else:
                 a[:] = C[:, c]
-        else:
-            a = Rfin[:, c].copy()
-        bcol = sigma * Rfin[:, c + 1] + (theta[c % s] * a if theta is not None else 0.0)
+            return a
+        return Rfin[:, c].copy()
+
+    for c in range(c_lo, c_hi):
+        a = coords(c)
+        sig_c, nu_c = cheb_coeffs(c % s, sigma) if cheb else (sigma, 0.0)
+        bcol = sig_c * Rfin[:, c + 1] + (theta[c % s] * a if theta is not None else 0.0)
+        if nu_c != 0.0:
+            bcol = bcol + nu_c * coords(c - 1)
         acc = bcol.copy()
         for i in range(c):
             acc -= H[:, i] * a[i]
@@ -259,7 +304,7 @@ def newton_sigma(theta, fallback: float) -> float:
 
 def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=1000,
                 ortho="two_stage", sigma=None, theta=None, return_basis=False, basis_dtype=np.float64,
-                shift=False, precond=None):
+                shift=False, precond=None, cheb=None):
     """s-step GMRES (Fig. 1, §III) with the chosen block orthogonalization.
 
     ``panel`` is the second step size s^ of the two-stage scheme (§V); it must
@@ -270,7 +315,11 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
     or "auto": the first cycle runs with s = s^ = 1 (standard GMRES through the
     same block machinery), ``newton_shifts`` turns its Hessenberg matrix into s
     shifts, and every later cycle uses the Newton basis with them, scaled by
-    ``newton_sigma`` unless ``sigma`` is given.  ``ortho`` in {"two_stage", "bcgs_pip2", "bcgs2_cholqr2"}.
+    ``newton_sigma`` unless ``sigma`` is given.  ``cheb`` selects the Chebyshev
+    basis instead (``cheb_coeffs``): an interval (c, delta), or "auto", where the
+    first cycle is standard GMRES as for theta = "auto" and ``cheb_interval``
+    turns its Hessenberg matrix into the interval; the MPK shift is c and its
+    scale delta / 2.  ``ortho`` in {"two_stage", "bcgs_pip2", "bcgs2_cholqr2"}.
     ``precond="mcgs"`` (FP64 basis) preconditions from the right with one
     forward multicolor Gauss-Seidel sweep (``oracle.precond``, the local
     Gauss-Seidel of §VIII, Fig. 9): the MPK applies A M^{-1}, the correction is
@@ -297,9 +346,12 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
     M = as_operator(A)
     n = b.shape[0]
     lowp = np.dtype(basis_dtype) == np.float32
-    auto = isinstance(theta, str)
-    if auto and theta != "auto":
-        raise ValueError("theta must be None, s shifts or 'auto'")
+    if cheb is not None and theta is not None:
+        raise ValueError("theta and cheb are exclusive")
+    auto = isinstance(theta, str) or isinstance(cheb, str)
+    if auto and (theta if cheb is None else cheb) != "auto":
+        raise ValueError("theta must be None, s shifts or 'auto'; cheb None, (c, delta) or 'auto'")
+    use_cheb = cheb is not None
     th = None if auto else theta
     s_req = s
     Mb = M.astype(np.float32) if lowp else M
@@ -319,6 +371,12 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
         colors = pc.greedy_coloring(M)
         minv = lambda v: pc.gs_sweep(M, colors, v)  # noqa: E731
     sig = (1.0 if minv is not None else mpk_sigma(A)) if sigma is None else float(sigma)
+    cheb_on = False                     # the current cycle's basis is the Chebyshev one
+    if use_cheb and not auto:
+        c0, d0 = float(cheb[0]), float(cheb[1])
+        if not (d0 > 0.0):
+            raise ValueError("the Chebyshev half-width delta must be positive")
+        th, sig, cheb_on = np.full(s, c0), 0.5 * d0, True
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     bnorm = np.linalg.norm(b)
     iters = 0
@@ -372,7 +430,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
                 where_blk = j
                 st = s * j
                 start_final[st] = final[st]
-                W = mpk(Mb, Q[:, st], s, sig, th, minv)
+                W = mpk(Mb, Q[:, st], s, sig, th, minv, cheb=cheb_on)
                 cols = slice(st + 1, st + s + 1)
                 if ortho == "two_stage":
                     st1 = bo.stage1_lowp if lowp else (bo.stage1_shifted if shift else bo.stage1)
@@ -407,7 +465,7 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
                     c_lo = st
                 if gv is None:
                     gv = Givens(m, beta * C[0, 0])
-                hessenberg_columns(Rfin, C, start_final, s, sig, th, c_lo, t, H)
+                hessenberg_columns(Rfin, C, start_final, s, sig, th, c_lo, t, H, cheb=cheb_on)
                 for c in range(c_lo, t):
                     gv.add_column(H[: c + 2, c])
                 k_used = t
@@ -425,16 +483,20 @@ def sstep_gmres(A, b, x0=None, m=60, s=5, panel=None, tol=1e-8, max_restarts=100
         iters += k_used
         last = dict(Q=Q, H=H, g0=beta * C[0, 0], k=k_used, Rfin=Rfin, C=C)
         if auto and th is None:
-            th = newton_shifts(H[:k_used, :k_used], s_req)
-            if sigma is None:
-                sig = newton_sigma(th, sig)
+            if use_cheb:
+                c0, d0 = cheb_interval(H[:k_used, :k_used])
+                th, sig, cheb_on = np.full(s_req, c0), 0.5 * d0, True
+            else:
+                th = newton_shifts(H[:k_used, :k_used], s_req)
+                if sigma is None:
+                    sig = newton_sigma(th, sig)
     else:
         r = b - M @ x
         hist.append(np.linalg.norm(r) / bnorm)
     info = dict(status=status, iters=iters, restarts=restarts, relres=hist[-1], history=hist,
                 sigma=sig, where=err_where, breakdown_block=breakdown[0], breakdown_pivot=breakdown[1],
                 breakdown_value=breakdown[2], breakdown_margin=breakdown[3],
-                theta=None if th is None else np.asarray(th, dtype=np.float64))
+                theta=None if th is None else np.asarray(th, dtype=np.float64), cheb=cheb_on)
     if return_basis:
         info.update(last)
     return x, info

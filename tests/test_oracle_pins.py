@@ -9,6 +9,7 @@ import math
 import os
 
 import numpy as np
+import scipy.sparse as sp
 import pytest
 
 import synth
@@ -838,3 +839,101 @@ def test_auto_newton_basis_solves_where_the_monomial_basis_breaks_down(ortho, s)
     assert lo - 1e-9 <= info["theta"].min() and info["theta"].max() <= hi + 1e-9
     k = info["k"]
     assert checks.arnoldi_residual(M, info["Q"], info["H"], k) < 1e-12
+
+
+def test_chebyshev_basis_of_a_diagonal_matrix_is_the_chebyshev_polynomials():
+    """For A = diag(lambda) and v = 1 the MPK block of the Chebyshev basis on
+    [c - delta, c + delta] is T_j(x), x = (lambda - c) / delta, j = 1..s, in
+    closed form: cos(j arccos x) inside the interval, cosh(j arccosh |x|)
+    sign(x)^j outside (Bai, Hu and Reichel 1994).  Pins the scale of the first
+    product (delta), of the later ones (delta / 2) and the three-term term."""
+    lam = np.concatenate([np.linspace(-3.0, 7.0, 41), [7.5, 9.0, -3.5]])
+    A = sp.diags(lam).tocsr()
+    c, d, s = 2.0, 5.0, 8
+    W = kr.mpk(A, np.ones(lam.size), s, d / 2.0, np.full(s, c), cheb=True)
+    x = (lam - c) / d
+    inside = np.abs(x) <= 1.0
+    for j in range(1, s + 1):
+        ref = np.where(inside, np.cos(j * np.arccos(np.clip(x, -1.0, 1.0))),
+                       np.sign(x) ** j * np.cosh(j * np.arccosh(np.maximum(np.abs(x), 1.0))))
+        assert np.allclose(W[:, j - 1], ref, rtol=1e-12, atol=1e-12), j
+    assert kr.cheb_coeffs(0, 1.25) == (2.5, 0.0) and kr.cheb_coeffs(3, 1.25) == (1.25, 1.25)
+
+
+def test_chebyshev_interval_is_the_range_of_the_ritz_values():
+    """The interval spans the real parts of the eigenvalues of H (an orthogonal
+    similarity of diag(d) in Hessenberg form, and a rotation block with a
+    conjugate pair); Ritz values without spread give delta = |c|."""
+    import scipy.linalg as sla
+    g = synth.rng(41)
+    d = np.array([0.5, 1.0, 2.5, 3.0, 4.75, 6.0, 7.5, 8.0])
+    Qo, _ = np.linalg.qr(g.standard_normal((8, 8)))
+    Hh = sla.hessenberg(Qo @ np.diag(d) @ Qo.T)
+    c, dl = kr.cheb_interval(Hh)
+    assert c == pytest.approx(4.25, abs=1e-12) and dl == pytest.approx(3.75, abs=1e-12)
+    R = np.array([[2.0, -3.0, 0.0], [3.0, 2.0, 1.0], [0.0, 0.5, -4.0]])
+    re = np.linalg.eigvals(R).real
+    c, dl = kr.cheb_interval(R)
+    assert c == pytest.approx(0.5 * (re.min() + re.max())) and dl == pytest.approx(0.5 * (re.max() - re.min()))
+    assert kr.cheb_interval(np.array([[3.0]])) == (3.0, 3.0)
+    assert kr.cheb_interval(np.array([[0.0]])) == (0.0, 1.0)
+
+
+def test_chebyshev_basis_is_better_conditioned_than_the_monomial_basis():
+    """On the spectral interval of the 64x64 Laplacian (closed-form extreme
+    eigenvalues) an s = 10 Chebyshev block is far better conditioned than the
+    scaled monomial one (column-equilibrated condition numbers)."""
+    A = synth.laplace2d(64)
+    M = kr.as_operator(A)
+    v = M @ synth.x_true(A.n, 0)
+    v /= np.linalg.norm(v)
+    lo, hi = checks.laplace2d_extreme_eigs(64)
+    c, d = 0.5 * (lo + hi), 0.5 * (hi - lo)
+
+    def econd(W):
+        W = np.column_stack([v, W])
+        return np.linalg.cond(W / np.linalg.norm(W, axis=0))
+    c_mono = econd(kr.mpk(M, v, 10, kr.mpk_sigma(A)))
+    c_cheb = econd(kr.mpk(M, v, 10, d / 2.0, np.full(10, c), cheb=True))
+    assert c_mono > 1e7 and c_cheb < 1e-4 * c_mono
+
+
+@pytest.mark.parametrize("ortho,s", [("two_stage", 10), ("two_stage", 15), ("bcgs_pip2", 15)])
+def test_auto_chebyshev_basis_solves_where_the_monomial_basis_breaks_down(ortho, s):
+    """Large s on the 64x64 Laplacian: the monomial basis breaks down, the
+    Chebyshev basis on the interval of the first cycle's Ritz values converges
+    to 1e-8 with the forward error within kappa(A) * relres; the interval lies
+    in [lambda_min, lambda_max] (interlacing) and the final cycle keeps the
+    Arnoldi relation A Q_k = Q_{k+1} H to 1e-12 (which fails if the three-term
+    term of the change of basis is dropped)."""
+    N = 64
+    A = synth.laplace2d(N)
+    M = kr.as_operator(A)
+    xt = synth.x_true(A.n, 0)
+    b = M @ xt
+    x, info = kr.sstep_gmres(A, b, m=60, s=s, tol=1e-8, ortho=ortho, cheb="auto", return_basis=True)
+    assert info["status"] == 0 and info["restarts"] >= 2 and info["cheb"]
+    rel = np.linalg.norm(M @ x - b) / np.linalg.norm(b)
+    assert rel <= 1e-8
+    lo, hi = checks.laplace2d_extreme_eigs(N)
+    assert np.linalg.norm(x - xt) / np.linalg.norm(xt) <= (hi / lo) * rel
+    c, sig = info["theta"][0], info["sigma"]
+    assert np.all(info["theta"] == c)
+    assert lo - 1e-9 <= c - 2.0 * sig and c + 2.0 * sig <= hi + 1e-9
+    assert checks.arnoldi_residual(M, info["Q"], info["H"], info["k"]) < 1e-12
+
+
+def test_explicit_chebyshev_interval_matches_the_auto_one_on_the_spectrum():
+    """With the interval given (the closed-form spectrum of the Laplacian) the
+    solve takes the same basis in every cycle and converges; a non-positive
+    half-width is rejected."""
+    A = synth.laplace2d(32)
+    M = kr.as_operator(A)
+    b = M @ synth.x_true(A.n, 0)
+    lo, hi = checks.laplace2d_extreme_eigs(32)
+    x, info = kr.sstep_gmres(A, b, m=60, s=10, tol=1e-8, cheb=(0.5 * (lo + hi), 0.5 * (hi - lo)))
+    assert info["status"] == 0 and info["sigma"] == pytest.approx(0.25 * (hi - lo))
+    with pytest.raises(ValueError):
+        kr.sstep_gmres(A, b, m=60, s=10, cheb=(4.0, 0.0))
+    with pytest.raises(ValueError):
+        kr.sstep_gmres(A, b, m=60, s=10, cheb=(4.0, 1.0), theta="auto")
