@@ -62,6 +62,17 @@ extern "C" {
                                       /* again starts again from s = 1.  A breakdown in the first   */
                                       /* cycle is numbered in its own blocks (m stage-1 blocks of   */
                                       /* s = 1, then m panels).  Not in the batched engine.          */
+#define GMRES_BASIS_CHEBYSHEV      3  /* Chebyshev basis (named with the Newton basis in §VI):       */
+                                      /* per s-step block y_1 = (A - c I) y_0 / delta and          */
+                                      /* y_{i+1} = 2 (A - c I) y_i / delta - y_{i-1}, i.e. the      */
+                                      /* Chebyshev polynomials T_i((z - c) / delta) of the interval */
+                                      /* [c - delta, c + delta]; c = opts.theta[0], delta =         */
+                                      /* opts.theta[1] > 0 (opts.sigma is not used).  The change of */
+                                      /* basis is tridiagonal.  Not in the batched engine.          */
+#define GMRES_BASIS_CHEBYSHEV_AUTO 4  /* Chebyshev basis on the interval spanned by the real parts   */
+                                      /* of the first cycle's Ritz values (first cycle as for      */
+                                      /* GMRES_BASIS_NEWTON_AUTO).  The result reports c in        */
+                                      /* theta[0..s-1] and delta / 2 in sigma.                       */
 #define GMRES_ARITH_FP64           0  /* native FP64 pipe (default)                                 */
 #define GMRES_ARITH_DD             1  /* opt-in: double-float (hi + lo FP32) on the FP32 pipe:      */
                                       /* error-free products, renormalized sums, ~2^-48 relative;   */
@@ -139,7 +150,9 @@ typedef struct gmres_result {
     double  sigma;             /* MPK scale of the last restart cycle                      */
     double  theta[16];         /* its MPK shifts theta_0..theta_{s-1} (0: monomial); with  */
                                /* GMRES_BASIS_NEWTON_AUTO the shifts the solve chose, which */
-                               /* a later solve can pass as opts.theta (basis = NEWTON)     */
+                               /* a later solve can pass as opts.theta (basis = NEWTON);    */
+                               /* with a Chebyshev basis the center c in every entry and    */
+                               /* delta / 2 in sigma                                         */
 } gmres_result;
 
 typedef struct gmres_ctx gmres_ctx;   /* opaque: device CSR copy, Krylov basis, workspace */

@@ -33,6 +33,8 @@ GMRES_PREC_MIXED = 1
 GMRES_BASIS_MONOMIAL = 0
 GMRES_BASIS_NEWTON = 1
 GMRES_BASIS_NEWTON_AUTO = 2
+GMRES_BASIS_CHEBYSHEV = 3
+GMRES_BASIS_CHEBYSHEV_AUTO = 4
 GMRES_ARITH_FP64 = 0
 GMRES_ARITH_DD = 1
 GMRES_ARITH_TC = 2

@@ -258,6 +258,24 @@ int newton_shifts(const double* H, int ldh, int k, int s, double* theta) {
     return GMRES_OK;
 }
 
+int chebyshev_interval(const double* H, int ldh, int k, double* c, double* delta) {
+    *c = 0.0;
+    *delta = 1.0;
+    if (k == 0) return GMRES_OK;
+    Hess hm(H, ldh, k);
+    std::vector<double> re, im;
+    if (!hm.eigenvalues(re, im)) {
+        set_error("the QR iteration for the Ritz values did not converge (k = %d)", k);
+        return GMRES_ERR_EIG;
+    }
+    const double lo = *std::min_element(re.begin(), re.end()), hi = *std::max_element(re.begin(), re.end());
+    *c = 0.5 * (lo + hi);
+    *delta = 0.5 * (hi - lo);
+    // Ritz values without spread: delta = |c| (or 1), so that the basis stays defined
+    if (!(*delta > 0.0) || !std::isfinite(*delta)) *delta = *c != 0.0 ? std::fabs(*c) : 1.0;
+    return GMRES_OK;
+}
+
 }  // namespace gm
 
 extern "C" {

@@ -10,6 +10,7 @@ __global__ void cycle_begin_kernel(DevState* st, CycleBasis cb) {
         st->s = cb.s;
         st->panel = cb.panel;
         st->sigma = cb.sigma;
+        st->cheb = cb.cheb;
     }
     if (threadIdx.x < 16) st->theta[threadIdx.x] = cb.theta[threadIdx.x];
     cycle_begin_body(st, 0);

@@ -5,7 +5,11 @@
 //
 // Change of basis.  SpMV number c (0-based) reads y_c and writes the raw MPK
 // column c+1, A y_c = sigma w_{c+1} + theta_c y_c (§III, monomial basis of §VI
-// scaled by a power of two).  After stage 2 of the big panel [lo, t] (§V):
+// scaled by a power of two); with the Chebyshev basis A y_c = sigma_c w_{c+1} +
+// theta_c y_c + nu_c y_{c-1} (cheb_coeffs of c mod s; nu_c = 0 at a block's
+// first column, so y_{c-1} is a column of the same block, and
+// b_c = sigma_c Rfin[:, c+1] + theta_c a_c + nu_c a_{c-1}).  After stage 2 of
+// the big panel [lo, t] (§V):
 //   Rfin[:, c] = E Rhat[:, c],  E = identity on columns < lo, Cm on [lo, t],
 // where Rhat are the stage-1 factors (raw w = Q^ Rhat) and Cm the stage-2
 // factors (Q^ = Q Cm).  In the orthonormal basis Q:
@@ -45,7 +49,7 @@ constexpr int kLsThreads = 512;
 __host__ __device__ constexpr size_t hessenberg_ls_smem() { return (size_t)4 * kLsLd * kLsLd * sizeof(double); }
 
 __device__ inline void hessenberg_ls_body(DevState* st, int lo, int t, double* dyn) {
-    __shared__ double a[kLsLd];
+    __shared__ double a2[2][kLsLd];             // a_c and a_{c-1} (alternating)
     __shared__ double sg[kLsLd + 1];
     __shared__ double scs[kLsLd], ssn[kLsLd];
     __shared__ double sy[kLsLd];
@@ -106,9 +110,12 @@ __device__ inline void hessenberg_ls_body(DevState* st, int lo, int t, double* d
     __syncthreads();
 
     // 2. Hessenberg columns c_lo .. t-1 from H a_c = b_c
+    const int cheb = st->cheb;
     for (int c = c_lo; c < t; ++c) {
         const bool bstart = (c % s) == 0;
         const bool sfinal = bstart && c > 0 && (c % panel) == 0;
+        double* a = a2[(c - c_lo) & 1];
+        const double* ap = a2[(c - c_lo + 1) & 1];   // a_{c-1}, written in the previous pass
         for (int i = tid; i <= m; i += blockDim.x) {
             const double ai = bstart ? (sfinal ? (i == c ? 1.0 : 0.0) : sCm[i + (c - c_lo) * kLsLd])
                                      : sRf[i + (c - c_lo) * kLsLd];
@@ -117,10 +124,13 @@ __device__ inline void hessenberg_ls_body(DevState* st, int lo, int t, double* d
         }
         __syncthreads();
         const double th = st->theta[c % s];
+        double sig_c, nu_c;
+        cheb_coeffs(cheb, c % s, sigma, &sig_c, &nu_c);
         const double inv_ac = s_inv;
         for (int i = tid; i <= m; i += blockDim.x) {
-            double acc = sigma * sRf[i + (c + 1 - c_lo) * kLsLd];
+            double acc = sig_c * sRf[i + (c + 1 - c_lo) * kLsLd];
             if (th != 0.0) acc = fma(th, a[i], acc);
+            if (nu_c != 0.0) acc = fma(nu_c, ap[i], acc);
             for (int p = 0; p < c; ++p) acc = fma(-sH[i + p * kLsLd], a[p], acc);
             sH[i + c * kLsLd] = acc * inv_ac;
         }

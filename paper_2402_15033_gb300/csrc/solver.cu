@@ -152,11 +152,17 @@ namespace gm {
 // wide panel of s = 1 blocks loses orthogonality as the residual falls).
 CycleBasis first_cycle_basis(const gmres_opts& o, double sigma) {
     CycleBasis cb;
-    const bool aut = o.basis == GMRES_BASIS_NEWTON_AUTO;
+    const bool aut = o.basis == GMRES_BASIS_NEWTON_AUTO || o.basis == GMRES_BASIS_CHEBYSHEV_AUTO;
     cb.s = aut ? 1 : o.s;
     cb.panel = (o.ortho == GMRES_ORTHO_TWO_STAGE && !aut) ? o.panel : cb.s;
     cb.sigma = sigma;
     for (int i = 0; i < 16; ++i) cb.theta[i] = (o.basis == GMRES_BASIS_NEWTON && i < o.s) ? o.theta[i] : 0.0;
+    if (o.basis == GMRES_BASIS_CHEBYSHEV) {
+        // the interval [c - delta, c + delta]: shift c, scale delta / 2 (cheb_coeffs)
+        cb.cheb = 1;
+        cb.sigma = 0.5 * o.theta[1];
+        for (int i = 0; i < 16; ++i) cb.theta[i] = i < o.s ? o.theta[0] : 0.0;
+    }
     return cb;
 }
 
@@ -247,8 +253,12 @@ static int check_opts(const gmres_opts* o) {
                o->ortho == GMRES_ORTHO_BCGS2_CHOLQR2,
            "unknown ortho");
     GM_ARG(o->precision == GMRES_PREC_FP64 || o->precision == GMRES_PREC_MIXED, "unknown precision");
-    GM_ARG(o->basis == GMRES_BASIS_MONOMIAL || o->basis == GMRES_BASIS_NEWTON || o->basis == GMRES_BASIS_NEWTON_AUTO,
+    GM_ARG(o->basis == GMRES_BASIS_MONOMIAL || o->basis == GMRES_BASIS_NEWTON || o->basis == GMRES_BASIS_NEWTON_AUTO ||
+               o->basis == GMRES_BASIS_CHEBYSHEV || o->basis == GMRES_BASIS_CHEBYSHEV_AUTO,
            "unknown basis");
+    GM_ARG(o->basis != GMRES_BASIS_CHEBYSHEV ||
+               (std::isfinite(o->theta[0]) && o->theta[1] > 0.0 && std::isfinite(o->theta[1])),
+           "the Chebyshev basis needs a finite center theta[0] and half-width theta[1] > 0");
     const int panel = o->ortho != GMRES_ORTHO_TWO_STAGE ? o->s : o->panel;
     GM_ARG(panel >= o->s && panel % o->s == 0 && o->m % o->s == 0 && panel <= o->m,
            "need s | panel, s | m and panel <= m");
@@ -537,7 +547,6 @@ static int run_cycle(gmres_ctx* c, const CycleBasis& cb, std::vector<std::pair<i
     DevState* ds = c->st;
     int32_t* done = &ds->done;
     T* basis = static_cast<T*>(c->basis);
-    const double sinv = 1.0 / cb.sigma;
     PipWork w{};
     int evi = 0;
     auto mark = [&](int phase) -> cudaError_t {
@@ -560,18 +569,26 @@ static int run_cycle(gmres_ctx* c, const CycleBasis& cb, std::vector<std::pair<i
         e = mark(PH_MPK);
         for (int i = 0; i < cb.s && e == cudaSuccess; ++i) {
             const double th = cb.theta[i];
+            double sig_i, nu_i;
+            cheb_coeffs(cb.cheb, i, cb.sigma, &sig_i, &nu_i);
+            const double sinv = 1.0 / sig_i;
             T* wi = basis + (size_t)(st0 + i) * c->ldq;
+            T* zi = i > 0 ? basis + (size_t)(st0 + i - 1) * c->ldq : nullptr;   // Chebyshev: y_{i-1}
             if constexpr (std::is_same<T, double>::value) {
                 if (c->gs.perm) {
-                    // right preconditioning: w_{i+1} = (A M^{-1} w_i - theta w_i) / sigma,
+                    // right preconditioning: w_{i+1} = (A M^{-1} w_i - theta w_i - nu w_{i-1}) / sigma_i,
                     // M^{-1} one multicolor Gauss-Seidel sweep (§VIII, Fig. 9)
                     e = launch_gs_sweep(s, c->A, c->gs, wi, c->gs.z, done);
                     if (e == cudaSuccess)
-                        e = launch_spmv(s, c->A, c->gs.z, basis + (size_t)(st0 + i + 1) * c->ldq, th, sinv, done, wi);
+                        e = launch_spmv(s, c->A, c->gs.z, basis + (size_t)(st0 + i + 1) * c->ldq, th, sinv, done, wi,
+                                        zi, nu_i);
                     continue;
                 }
+                e = launch_spmv(s, c->A, wi, basis + (size_t)(st0 + i + 1) * c->ldq, th, sinv, done, nullptr, zi,
+                                nu_i);
+            } else {
+                e = launch_spmv(s, c->A, wi, basis + (size_t)(st0 + i + 1) * c->ldq, th, sinv, done, zi, nu_i);
             }
-            e = launch_spmv(s, c->A, wi, basis + (size_t)(st0 + i + 1) * c->ldq, th, sinv, done);
         }
         if (e == cudaSuccess) e = mark(PH_MPK);
         if (e == cudaSuccess) e = mark(PH_S1);
@@ -733,7 +750,7 @@ int run_begin(gmres_ctx* c, SolveRun* R, const double* b, const double* x, int o
     cudaStream_t s = c->stream;
     const gmres_opts& o = c->opts;
     R->cb = R->ran = first_cycle_basis(o, c->sigma);
-    R->auto_pending = o.basis == GMRES_BASIS_NEWTON_AUTO;
+    R->auto_pending = o.basis == GMRES_BASIS_NEWTON_AUTO || o.basis == GMRES_BASIS_CHEBYSHEV_AUTO;
     R->r.sigma = R->cb.sigma;
     for (int i = 0; i < 16; ++i) R->r.theta[i] = R->cb.theta[i];
     const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -820,17 +837,31 @@ int run_decide(SolveRun* R) {
     }
     if (cyc > 0 && R->auto_pending) {
         // the first cycle was standard GMRES: its k x k Hessenberg matrix gives
-        // the Ritz values; the Newton basis takes them as shifts from now on
+        // the Ritz values; from now on the Newton basis takes them as shifts, or
+        // the Chebyshev basis the interval of their real parts
         CycleBasis& nb = R->cb;
         nb.s = o.s;
         nb.panel = o.ortho == GMRES_ORTHO_TWO_STAGE ? o.panel : o.s;
         for (int i = 0; i < 16; ++i) nb.theta[i] = 0.0;
-        const int rc = newton_shifts(h.H, kMaxCols, h.k_used, o.s, nb.theta);
-        if (rc) {
-            R->status = rc;
-            return (R->finished = true), 1;
+        if (o.basis == GMRES_BASIS_CHEBYSHEV_AUTO) {
+            // the Chebyshev basis on the interval of the Ritz values' real parts
+            double cc = 0.0, dl = 1.0;
+            const int rc = chebyshev_interval(h.H, kMaxCols, h.k_used, &cc, &dl);
+            if (rc) {
+                R->status = rc;
+                return (R->finished = true), 1;
+            }
+            for (int i = 0; i < o.s; ++i) nb.theta[i] = cc;
+            nb.sigma = 0.5 * dl;
+            nb.cheb = 1;
+        } else {
+            const int rc = newton_shifts(h.H, kMaxCols, h.k_used, o.s, nb.theta);
+            if (rc) {
+                R->status = rc;
+                return (R->finished = true), 1;
+            }
+            nb.sigma = o.sigma > 0.0 ? c->sigma : newton_sigma(nb.theta, o.s, c->sigma);
         }
-        nb.sigma = o.sigma > 0.0 ? c->sigma : newton_sigma(nb.theta, o.s, c->sigma);
         R->auto_pending = false;
         r.sigma = nb.sigma;
         for (int i = 0; i < 16; ++i) r.theta[i] = nb.theta[i];
@@ -841,8 +872,8 @@ int run_decide(SolveRun* R) {
 }
 
 static bool same_basis(const CycleBasis& a, const CycleBasis& b) {
-    return a.s == b.s && a.panel == b.panel && std::memcmp(&a.sigma, &b.sigma, sizeof(double)) == 0 &&
-           std::memcmp(a.theta, b.theta, sizeof(a.theta)) == 0;
+    return a.s == b.s && a.panel == b.panel && a.cheb == b.cheb &&
+           std::memcmp(&a.sigma, &b.sigma, sizeof(double)) == 0 && std::memcmp(a.theta, b.theta, sizeof(a.theta)) == 0;
 }
 
 static int enqueue_eager(gmres_ctx* c, const CycleBasis& cb, std::vector<std::pair<int, int>>* marks,

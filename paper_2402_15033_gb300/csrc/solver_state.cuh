@@ -38,6 +38,7 @@ struct DevState {
     double resid;         // |g_k| after the latest least-squares update
     double sigma;         // MPK scale
     double theta[16];     // MPK shifts (zero for the monomial basis)
+    int32_t cheb;         // 1: Chebyshev basis (three-term MPK recurrence, cheb_coeffs)
     int32_t m, s, panel;
     int32_t k_used;       // iterations used by this cycle (0 until decided)
     int32_t done;         // 1: the rest of the cycle's kernels return at once
@@ -62,10 +63,23 @@ struct CycleBasis {
     int32_t s = 1, panel = 1;
     double sigma = 1.0;
     double theta[16] = {};
+    int32_t cheb = 0;
 };
+
+// Coefficients of product i (0-based within an s-step block) of the Chebyshev
+// basis: A y_i = sig y_{i+1} + c y_i + nu y_{i-1}, with sigma = delta / 2 the
+// first product has (2 sigma, 0) and the others (sigma, sigma) (the
+// recurrence of T_i((z - c) / delta)); other bases have (sigma, 0).
+__host__ __device__ inline void cheb_coeffs(int cheb, int i, double sigma, double* sig, double* nu) {
+    *sig = (cheb && i == 0) ? 2.0 * sigma : sigma;
+    *nu = (cheb && i != 0) ? sigma : 0.0;
+}
 
 // Newton-basis shifts and scale from a k x k Hessenberg matrix (newton.cu, host)
 int newton_shifts(const double* H, int ldh, int k, int s, double* theta);
+// Chebyshev interval [c - delta, c + delta] spanning the real parts of the
+// eigenvalues of a k x k Hessenberg matrix (newton.cu, host)
+int chebyshev_interval(const double* H, int ldh, int k, double* c, double* delta);
 double newton_sigma(const double* theta, int s, double fallback);
 
 int norm_grid(int64_t n);
@@ -74,9 +88,10 @@ cudaError_t launch_gs_sweep(cudaStream_t st, const DevCSR& A, const McGs& gs, co
 cudaError_t launch_diag(cudaStream_t st, const DevCSR& A, double* diag, int32_t* bad);
 cudaError_t launch_axpy1(cudaStream_t st, int64_t n, const double* z, double* x, const DevState* ds);
 cudaError_t launch_spmv(cudaStream_t st, const DevCSR& A, const double* x, double* y, double theta,
-                        double sinv, const int32_t* d_skip, const double* w = nullptr);
+                        double sinv, const int32_t* d_skip, const double* w = nullptr, const double* z = nullptr,
+                        double nu = 0.0);
 cudaError_t launch_spmv(cudaStream_t st, const DevCSR& A, const float* x, float* y, double theta,
-                        double sinv, const int32_t* d_skip);
+                        double sinv, const int32_t* d_skip, const float* z = nullptr, double nu = 0.0);
 cudaError_t launch_residual(cudaStream_t st, const DevCSR& A, const double* b, const double* x, double* out,
                             double* partial, unsigned* counter, DevState* ds, int which);
 cudaError_t launch_scale(cudaStream_t st, int64_t n, const double* v, double* out, const DevState* ds);

@@ -28,14 +28,16 @@ __device__ double block_sum(double v) {
     return t;  // valid in thread 0
 }
 
-// y = (A x - theta w) * sinv in the basis precision T (FP64, or FP32 for the
-// mixed-precision MPK with an FP32 copy of the values); w = x, or, with a
-// right preconditioner, the unpreconditioned vector x = M^{-1} w came from.
+// y = (A x - theta w - nu z) * sinv in the basis precision T (FP64, or FP32
+// for the mixed-precision MPK with an FP32 copy of the values); w = x, or,
+// with a right preconditioner, the unpreconditioned vector x = M^{-1} w came
+// from; z the basis vector before w (the three-term term of the Chebyshev
+// basis, nu = 0 otherwise).
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
 spmv_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
             const T* __restrict__ vals, const T* __restrict__ x, T* __restrict__ y,
-            T theta, T sinv, const int32_t* d_skip, const T* __restrict__ w) {
+            T theta, T sinv, const int32_t* d_skip, const T* __restrict__ w, const T* __restrict__ z, T nu) {
     if (d_skip && *d_skip) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -43,6 +45,7 @@ spmv_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __rest
         T acc = T(0);
         for (int32_t p = p0; p < p1; ++p) acc = fma(__ldg(vals + p), __ldg(x + __ldg(colind + p)), acc);
         if (theta != T(0)) acc = fma(-theta, w[i], acc);
+        if (nu != T(0)) acc = fma(-nu, z[i], acc);
         y[i] = acc * sinv;
     }
 }
@@ -224,16 +227,17 @@ int vec_grid(int64_t n) {
 int norm_grid(int64_t n) { return vec_grid(n); }
 
 cudaError_t launch_spmv(cudaStream_t st, const DevCSR& A, const double* x, double* y, double theta,
-                        double sinv, const int32_t* d_skip, const double* w) {
+                        double sinv, const int32_t* d_skip, const double* w, const double* z, double nu) {
     spmv_kernel<double><<<vec_grid(A.n), kVecThreads, 0, st>>>(A.n, A.rowptr, A.colind, A.vals, x, y, theta, sinv,
-                                                               d_skip, w ? w : x);
+                                                               d_skip, w ? w : x, z ? z : x, z ? nu : 0.0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_spmv(cudaStream_t st, const DevCSR& A, const float* x, float* y, double theta,
-                        double sinv, const int32_t* d_skip) {
+                        double sinv, const int32_t* d_skip, const float* z, double nu) {
     spmv_kernel<float><<<vec_grid(A.n), kVecThreads, 0, st>>>(A.n, A.rowptr, A.colind, A.vals32, x, y, (float)theta,
-                                                              (float)sinv, d_skip, x);
+                                                              (float)sinv, d_skip, x, z ? z : x,
+                                                              z ? (float)nu : 0.0f);
     return cudaGetLastError();
 }
 
