@@ -107,7 +107,9 @@ def test_shifted_solver_matches_oracle(lib, arith, N, m, s, panel):
 @pytest.mark.parametrize("panel", [60, 20])
 def test_shifted_solver_s10_monomial(lib, arith, panel):
     """s = 10 with the monomial basis on the 64^2 Laplacian: the plain scheme
-    breaks down in its first cycle on both sides; with the shift both
+    breaks down in the oracle with a breakdown margin below 1
+    (its pivot is decided by rounding, R-8), so the GPU breaks down too or, if
+    rounding lets it through, converges to the tolerance; with the shift both
     converge.  The basis is so ill conditioned (the shift engages in every
     block) that rounding decides the path: x is compared where it is unique,
     within the closed-form forward-error bound kappa(A) tol of x_true (and
@@ -118,8 +120,11 @@ def test_shifted_solver_s10_monomial(lib, arith, panel):
     A = synth.laplace2d(64)
     xt = synth.x_true(A.n, 0)
     b = kr.as_operator(A) @ xt
-    rc0, _, _ = solve(capi, A, b, m=60, s=10, panel=panel, tol=1e-8, arith=arith)
-    assert rc0 == capi.GMRES_ERR_BREAKDOWN
+    rc0, res0, _ = solve(capi, A, b, m=60, s=10, panel=panel, tol=1e-8, arith=arith)
+    _, info0 = kr.sstep_gmres(A, b, m=60, s=10, panel=panel, tol=1e-8)
+    # (the cycle in which it breaks down differs between x86 and Arm numpy)
+    assert info0["status"] == kr.STATUS_BREAKDOWN and info0["breakdown_margin"] < 1.0
+    assert rc0 == capi.GMRES_ERR_BREAKDOWN or (rc0 == capi.GMRES_OK and res0["relres_true"] <= 1e-8)
     rc, res, x = solve(capi, A, b, m=60, s=10, panel=panel, tol=1e-8, arith=arith, shift=1)
     xr, info = kr.sstep_gmres(A, b, m=60, s=10, panel=panel, tol=1e-8, shift=True)
     assert info["status"] == 0
