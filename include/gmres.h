@@ -354,8 +354,10 @@ int ortho_plan_destroy(ortho_plan* p);
  *                       which must hold exactly those columns' current values;
  *                       bit-identical to ortho_gram_chol_tc, except that with
  *                       kc = k and nb <= 8 a streaming kernel (each warp copies
- *                       the digit bytes of its own chunks) runs and agrees to
- *                       rounding.
+ *                       the digit bytes of its own chunks) runs, and with
+ *                       kc = k + nb, nb >= 9 and k + nb <= 64 a kernel that sums
+ *                       each CTA's chunks exactly and rounds once runs; both
+ *                       agree to rounding.
  *   ortho_update_tcd:   ortho_update_tc that also writes the digits of the new V
  *                       into digit columns k .. k+nb-1; for nb <= 8 it reads Q's
  *                       digits from digit columns 0 .. k-1 (which must hold Q)

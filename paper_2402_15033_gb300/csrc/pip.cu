@@ -26,6 +26,7 @@
 #include "gram_tc.cuh"
 #include "gram_tcq.cuh"
 #include "gram_t5.cuh"
+#include "gram_w5.cuh"
 #include "update_tc.cuh"
 #include "update_tcd.cuh"
 
@@ -131,6 +132,32 @@ cudaError_t launch_gram_t5(cudaStream_t st, int64_t n, int k, const double* V, i
     const int G = std::min(grid, num_sms());
     gram_t5_kernel<<<G, kG5Threads, kG5Smem, st>>>(n, V, ldv, k, nb, R, ldr, w.partial, w.counter, w.gram, d_status,
                                                    d_skip, mode, dig, dex, capc);
+    return cudaGetLastError();
+}
+
+// Wide Gram over columns all in the digit basis (the stage-2 panel) on the
+// fifth-generation tensor cores (gram_w5.cuh): one warp-specialized CTA per SM.
+__global__ void __launch_bounds__(kW5Threads, 1)
+gram_w5_kernel(int64_t n, int k, int nb, double* __restrict__ R, int ldr, double* partial, unsigned* counter,
+               double* gram, int32_t* d_status, int32_t* d_skip, int mode, const uint4* dig, const int* dex, int capc) {
+    extern __shared__ __align__(1024) char w5_smem_buf[];
+    if (d_skip && *d_skip) return;
+    const int G = gridDim.x;
+    const size_t ps = (size_t)kMaxNB * nb;
+    gram_w5_part(n, k, nb, blockIdx.x, G, partial + blockIdx.x * ps, w5_smem_buf, dig, dex, capc);
+    pip_finish(k, nb, 0, 1, G, R, ldr, partial, ps, counter, gram, d_status, d_skip,
+               reinterpret_cast<double*>(w5_smem_buf), mode, n);
+}
+
+cudaError_t launch_gram_w5(cudaStream_t st, int64_t n, int k, int nb, double* R, int ldr, const PipWork& w,
+                           int32_t* d_status, int32_t* d_skip, int grid, int mode, const void* digits, int capc) {
+    static const cudaError_t attr = smem_limit(gram_w5_kernel, (int)w5_smem(kW5MaxKX));
+    if (attr != cudaSuccess) return attr;
+    const uint4* dig = static_cast<const uint4*>(digits);
+    const int* dex = reinterpret_cast<const int*>(dig + tc_digits_units(n, capc));
+    const int G = std::min(grid, num_sms());
+    gram_w5_kernel<<<G, kW5Threads, w5_smem(k + nb), st>>>(n, k, nb, R, ldr, w.partial, w.counter, w.gram, d_status,
+                                                          d_skip, mode, dig, dex, capc);
     return cudaGetLastError();
 }
 
@@ -531,6 +558,10 @@ cudaError_t launch_gram_tc_digits(cudaStream_t st, int64_t n, const double* Q, i
     // streaming (gram_tcq.cuh)
     if (nb <= kG5MaxNB && kc == k && k + nb >= kG5MinKX && k + nb <= kG5MaxKX)
         return launch_gram_t5(st, n, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode, digits, capc);
+    // every column in the digit basis (the stage-2 panel, wide blocks): tcgen05
+    // with exact per-CTA accumulation (gram_w5.cuh)
+    if (nb >= kW5MinNB && kc == k + nb && k + nb <= kW5MaxKX)
+        return launch_gram_w5(st, n, k, nb, R, ldr, w, d_status, d_skip, grid, mode, digits, capc);
     if (nb <= kGqMaxNB && kc == k && k + nb <= kGqMaxKX)
         return launch_gram_tcq(st, n, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode, digits, capc);
     return launch_gram_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, w, d_status, d_skip, grid, mode, digits, capc, kc);

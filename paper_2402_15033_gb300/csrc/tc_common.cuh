@@ -32,6 +32,7 @@ namespace gm {
 constexpr int kTcSlices = 7;                  // balanced base-256 digits
 constexpr int kTcWp = 34;                     // 16-byte units per (column, digit half): 32 pairs + 2 pad
 constexpr int kTcBadExp = 1 << 20;            // exponent marking a NaN or infinity in the group
+constexpr int kTcZeroExp = -(1 << 20);        // stored exponent of an all-zero chunk column (digits all zero)
 constexpr int kTcShift = 50;                  // x_i x_j = S 2^(E_i + E_j - kTcShift), S from tc_combine
 constexpr uint32_t kTcF16Hi = 0x64646464u;    // f16 exponent byte of 1024, for the widening permutes
 constexpr uint32_t kTcF16Bias = 0x64806480u;  // f16x2 (1152, 1152)
@@ -196,8 +197,10 @@ __device__ __forceinline__ void tc_stage64(const double* Q, int64_t ldq, int k, 
 // mma.sync fragment reads in k-step w, so a Gram lane widens each byte once
 // and the update lane takes rows r, r+8 of two columns with one permute.
 // exps[ch * tc_dex_stride(capc) + c] holds the chunk column's unbiased exponent
-// E (kTcBadExp for a NaN or infinity).  The exponents follow the units in one
-// buffer; a chunk's row of exponents starts on a 16-byte boundary.
+// E (kTcBadExp for a NaN or infinity, kTcZeroExp for a chunk column whose
+// entries are all zero or subnormal: its digits are all zero, and the marker
+// keeps it out of any largest-exponent scan).  The exponents follow the units
+// in one buffer; a chunk's row of exponents starts on a 16-byte boundary.
 constexpr int kTcB8Units = 28;                // 16-byte units per (chunk, column)
 constexpr int kTcB8Bytes = kTcB8Units * 16;   // 448
 
@@ -232,8 +235,8 @@ __device__ __forceinline__ void tc_b8_store(const double (&x)[4], uint4* units, 
     int eb = max(max(tc_bexp(x[0]), tc_bexp(x[1])), max(tc_bexp(x[2]), tc_bexp(x[3])));
 #pragma unroll
     for (int off = 8; off > 0; off >>= 1) eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, off));
-    const bool bad = eb == 0x7FF;
-    if (bad || eb == 0) eb = 1023;
+    const bool bad = eb == 0x7FF, zero = eb == 0;
+    if (bad || zero) eb = 1023;
     const uint2 s0 = tc_slice(x[0], eb), s1 = tc_slice(x[1], eb), s2 = tc_slice(x[2], eb), s3 = tc_slice(x[3], eb);
     uint32_t* u = reinterpret_cast<uint32_t*>(units) + g * 4 + w;   // unit 4p + g, word w
     u[0 * 16] = tc_b8_word<0>(s0, s1, s2, s3);
@@ -243,7 +246,7 @@ __device__ __forceinline__ void tc_b8_store(const double (&x)[4], uint4* units, 
     u[4 * 16] = tc_b8_word<4>(s0, s1, s2, s3);
     u[5 * 16] = tc_b8_word<5>(s0, s1, s2, s3);
     u[6 * 16] = tc_b8_word<6>(s0, s1, s2, s3);
-    if (h == 0) *ex = bad ? kTcBadExp : eb - 1023;
+    if (h == 0) *ex = bad ? kTcBadExp : (zero ? kTcZeroExp : eb - 1023);
 }
 
 }  // namespace gm

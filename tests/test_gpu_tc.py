@@ -246,7 +246,9 @@ def test_digit_basis_gram_is_bit_identical(lib, n, k, nb):
     """The Gram that reads Q's and V's digits from the digit basis equals the
     one that slices them, bit for bit (the digits are the same).  With only Q
     cached and nb <= 8 the streaming kernel runs instead: V's digits are taken
-    against 16-row groups, so it agrees to rounding (2^-46 of the column norms)."""
+    against 16-row groups, so it agrees to rounding (2^-46 of the column norms);
+    so does the tcgen05 kernel that takes every column from the basis when
+    nb >= 9 and k + nb <= 64 (exact sums per CTA, rounded once)."""
     from paper_2402_15033_gb300 import capi
     g = synth.rng(1300 + n + k)
     pad = n % 2
@@ -267,7 +269,11 @@ def test_digit_basis_gram_is_bit_identical(lib, n, k, nb):
         torch.cuda.synchronize()
         assert int(st.item()) == 0
         outs.append(R.cpu().numpy())
-    assert np.array_equal(outs[0], outs[2])
+    scale = np.linalg.norm(outs[0], axis=0)
+    if nb >= 9 and k + nb <= 64:
+        assert np.all(np.abs(outs[2] - outs[0]) <= 2.0 ** -46 * scale[None, :])
+    else:
+        assert np.array_equal(outs[0], outs[2])
     if nb <= 8:
         scale = np.linalg.norm(outs[0], axis=0)
         assert np.all(np.abs(outs[1] - outs[0]) <= 2.0 ** -46 * scale[None, :])
@@ -384,6 +390,30 @@ def test_all_cached_digit_gram_matches_oracle(lib, n, k, nb):
     V = g.standard_normal((n, nb)) / np.sqrt(n) + (Q @ g.standard_normal((k, nb)) / 4 if k else 0.0)
     Vg, Rg, st = run_gram_stream(capi, Q, V, ld_pad=n % 2, cached_v=True)
     assert_parity(Q, V, Vg, Rg, st)
+
+
+def test_all_cached_digit_gram_zero_chunks_far_from_unit_scale(lib):
+    """Columns that vanish over whole 64-row chunks, next to entries near 2^-300
+    and 2^280: a zero chunk column carries the digit basis's zero marker, so it
+    never sets the scale of the per-CTA exact sums (a zero chunk taken at
+    exponent 0 would truncate every 2^-300 product); entries within 2^-48 of
+    the exact rational sums."""
+    from paper_2402_15033_gb300 import capi
+    g = synth.rng(4412)
+    n, k, nb = 8000, 3, 10
+    Q = bo.hhqr(g.standard_normal((n, k)))[0]
+    V = g.standard_normal((n, nb)) / np.sqrt(n) + Q @ g.standard_normal((k, nb)) / 4
+    V[:640, 0::2] = 0.0
+    V[64 * 50:64 * 60, 1] = 0.0
+    V[:, 0::3] *= 2.0 ** -300
+    V[:, 1::3] *= 2.0 ** 280
+    _, Rg, st = run_gram_stream(capi, Q, V, ld_pad=0, update=False, cached_v=True)
+    assert st == 0
+    nq, nv = np.linalg.norm(Q, axis=0), np.linalg.norm(V, axis=0)
+    err = np.abs(Rg[:k] - checks.exact_gram(Q, V)) / np.outer(nq, nv)
+    assert err.max() <= 2.0 ** -48, err.max()
+    G_rec = Rg[k:].T @ Rg[k:] + Rg[:k].T @ Rg[:k]
+    assert np.max(np.abs(G_rec - checks.exact_gram(V, V)) / np.outer(nv, nv)) <= 1e-13
 
 
 def test_all_cached_digit_gram_exact_rationals_scaling_nan(lib):
