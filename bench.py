@@ -79,9 +79,14 @@ def tc_mma_flops(n, k, nb):
     """f16 tensor FLOPs the exact-slice Gram executes: per 64-row chunk, 4
     k-steps x 28 digit-pair MMAs of 16 x 8 x 16 for every M-tile (narrow
     blocks, the streaming kernel) or every output tile not strictly below the
-    G diagonal (wide blocks); k + nb > 64 runs FP64."""
+    G diagonal (wide blocks, the mma.sync kernel); for wide blocks whose
+    columns are all in the digit basis (the stage-2 panel, as benchmarked) the
+    tcgen05 kernel's 4 k-steps x six M = 128 MMAs of N = 1024 columns in all;
+    k + nb > 64 runs FP64."""
     if k + nb > 64:
         return 0.0
+    if nb >= 9:
+        return math.ceil(n / 64) * 4 * 2 * 128 * 1024 * 16
     tiles = (k + nb + 15) // 16 if nb <= 8 else tc_tile_count(k, nb)
     return math.ceil(n / 64) * tiles * 4 * 28 * 2 * 16 * 8 * 16
 
@@ -119,7 +124,7 @@ FP64_PROBE_TFLOPS = 1.19                          # an FMA-chain probe on this G
 # changes after its capture.
 NCU_TRAFFIC = {
     "tc": {"stage1_gram": 4 * (457.3 + 3.4) * 1e6, "stage1_update": 4 * (457.3 + 65.4) * 1e6,
-           "stage2_gram": 4 * (456.4 + 5.3) * 1e6, "stage2_update": 4 * (511.8 + 457.3) * 1e6},
+           "stage2_gram": 4 * (457.3 + 3.6) * 1e6, "stage2_update": 4 * (511.8 + 457.3) * 1e6},
     "fp64": {"stage1_gram": 4 * (511.8 + 3.2) * 1e6, "stage2_gram": 4 * (514.7 + 3.5) * 1e6},
 }
 
