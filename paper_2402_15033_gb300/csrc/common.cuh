@@ -89,7 +89,7 @@ cudaError_t launch_gram_tc_digits(cudaStream_t st, int64_t n, const double* Q, i
                                   int mode = 0);
 cudaError_t launch_update_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, double* V,
                                     int64_t ldv, int nb, const double* R, int ldr, const int32_t* d_status,
-                                    void* digits, int capc, const int32_t* d_skip = nullptr);
+                                    void* digits, int capc, const int32_t* d_skip = nullptr, int mode = 0);
 cudaError_t launch_digits_fill_cols(cudaStream_t st, int64_t n, const double* X, int64_t ldx, int c0, int nc,
                                     void* digits, int capc);
 

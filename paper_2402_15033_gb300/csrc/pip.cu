@@ -568,10 +568,10 @@ cudaError_t launch_gram_tc_digits(cudaStream_t st, int64_t n, const double* Q, i
 }
 cudaError_t launch_update_tc_digits(cudaStream_t st, int64_t n, const double* Q, int64_t ldq, int k, double* V,
                                     int64_t ldv, int nb, const double* R, int ldr, const int32_t* d_status,
-                                    void* digits, int capc, const int32_t* d_skip) {
+                                    void* digits, int capc, const int32_t* d_skip, int mode) {
     // narrow blocks read Q's digits instead of slicing its rows
-    if (nb <= kUdMaxNB) return launch_update_tcd(st, n, k, V, ldv, nb, R, ldr, d_status, d_skip, 0, digits, capc);
-    return launch_update_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, d_skip, 0, digits, capc);
+    if (nb <= kUdMaxNB) return launch_update_tcd(st, n, k, V, ldv, nb, R, ldr, d_status, d_skip, mode, digits, capc);
+    return launch_update_tc(st, n, Q, ldq, k, V, ldv, nb, R, ldr, d_status, d_skip, mode, digits, capc);
 }
 cudaError_t launch_digits_fill_cols(cudaStream_t st, int64_t n, const double* X, int64_t ldx, int c0, int nc,
                                     void* digits, int capc) {

@@ -200,8 +200,7 @@ size_t pip_bytes_for(int64_t n, const gmres_opts& o) {
 // The tensor-core arithmetic keeps a digit basis of the FP64 basis (every column
 // sliced once; stage 1 reads the accumulated columns' digits).
 bool uses_digits(const gmres_opts& o) {
-    return o.arith == GMRES_ARITH_TC && o.precision == GMRES_PREC_FP64 && o.ortho != GMRES_ORTHO_BCGS2_CHOLQR2 &&
-           o.m + 1 <= kMaxNB;
+    return o.arith == GMRES_ARITH_TC && o.precision == GMRES_PREC_FP64 && o.m + 1 <= kMaxNB;
 }
 
 size_t ctx_bytes(int64_t n, int64_t nnz, const gmres_opts& o) {
@@ -614,12 +613,28 @@ static int run_cycle(gmres_ctx* c, const CycleBasis& cb, std::vector<std::pair<i
                 for (int q = 0; q < 5 && e == cudaSuccess; ++q) {
                     const Step& st_ = steps[q];
                     const PipWork& wq = st_.kk ? w : w0;
+                    if (dig && st_.kk) {
+                        // the projections on the tensor cores read the accumulated
+                        // columns' digits from the digit basis
+                        const double* Bd = reinterpret_cast<const double*>(basis);
+                        double* Vd = reinterpret_cast<double*>(V);
+                        e = launch_gram_tc_digits(s, c->n, Bd, c->ldq, k, Vd, c->ldq, cb.s, st_.R, kMaxCols, wq, stat,
+                                                  grid, dig, capc, k, done, st_.gmode);
+                        if (e == cudaSuccess)
+                            e = launch_update_tc_digits(s, c->n, Bd, c->ldq, k, Vd, c->ldq, cb.s, st_.R, kMaxCols,
+                                                        stat, dig, capc, done, st_.umode);
+                        continue;
+                    }
                     e = launch_pip_gram_chol(s, c->n, basis, c->ldq, st_.kk, V, c->ldq, cb.s, st_.R, kMaxCols, wq, stat,
                                              done, grid, st_.gmode, o.arith);
                     if (e == cudaSuccess)
                         e = launch_pip_update(s, c->n, basis, c->ldq, st_.kk, V, c->ldq, cb.s, st_.R, kMaxCols, stat,
                                               done, st_.umode, o.arith);
                 }
+                // the block's final columns into the digit basis for the blocks after it
+                if (e == cudaSuccess && dig && st0 + cb.s < o.m)
+                    e = launch_digits_fill_cols(s, c->n, reinterpret_cast<const double*>(V), c->ldq, k, cb.s, dig,
+                                                capc);
                 if (e == cudaSuccess) e = launch_bcgs2_combine(s, ds, k, cb.s, S, R);
             } else if (sizeof(T) == sizeof(double) && dig) {
                 // BCGS-PIP (Fig. 4a) on the tensor cores, the accumulated columns'

@@ -89,11 +89,13 @@ def test_bcgs_pip2_mode_matches_oracle(lib):
     assert rc == 0
 
 
-@pytest.mark.parametrize("N,m,s,arith", [(48, 60, 5, 0), (40, 30, 5, 2), (33, 24, 4, 0)])
+@pytest.mark.parametrize("N,m,s,arith", [(48, 60, 5, 0), (40, 30, 5, 2), (33, 24, 4, 0), (48, 60, 5, 2), (33, 24, 4, 2)])
 def test_bcgs2_cholqr2_mode_matches_oracle(lib, N, m, s, arith):
     """The paper's baseline scheme (§IV-B, Fig. 2b with CholQR2: BCGS, CholQR2,
     BCGS, CholQR per block, five reductions) on the GPU against the oracle's
-    bcgs2_cholqr2 arm: same status, x within 1e-6, iterations within s."""
+    bcgs2_cholqr2 arm: same status, x within 1e-6, iterations within s.  With
+    the tensor cores (arith 2) the two projections read the accumulated
+    columns from the digit basis."""
     from paper_2402_15033_gb300 import capi
     A = synth.laplace2d(N)
     b = kr.as_operator(A) @ synth.x_true(A.n, 5)
