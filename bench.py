@@ -604,6 +604,7 @@ def solver_numbers(capi, dev, args):
               ("two_stage_s10_newton_auto_fp64", dict(s=10, basis=NA, arith=A)),
               ("two_stage_s10_newton_auto_tc", dict(s=10, basis=NA, arith=T)),
               ("two_stage_gauss_seidel_newton_auto_tc", dict(basis=NA, arith=T, precond=1)),
+              ("two_stage_monomial_shifted_tc", dict(basis=MO, arith=T, shift=1)),
               ("two_stage_s10_monomial_shifted_tc", dict(s=10, basis=MO, arith=T, shift=1)),
               ("bcgs_pip2_fp64", dict(ortho=capi.GMRES_ORTHO_BCGS_PIP2, arith=A)),
               ("bcgs2_cholqr2_fp64", dict(ortho=capi.GMRES_ORTHO_BCGS2_CHOLQR2, arith=A)),
