@@ -25,9 +25,10 @@
 // sit in TMEM quarters q and q ^ 2 (warps paired by rank); per group of 8
 // columns each hands the partner the cells of the partner's four columns
 // through shared memory, so that (0, c) completes the even columns and (1, c)
-// the odd ones: I_t = cell(0, t) + cell(1, t - 1) (an exact FP32 sum), then
-// S = sum_t I_t 2^(8(5 - t)) (64-bit integer, the 2^-8 tail rounded once as in
-// tc_combine; FP32 to integer by an exact addition).  The CTA's chunks are
+// the odd ones: I_t = cell(0, t) + cell(1, t - 1), each cell converted to an
+// integer by one exact FP32 addition (|cell| <= 2^22) and the two added as
+// integers, then S = sum_t I_t 2^(8(5 - t)) (64-bit integer, the 2^-8 tail
+// rounded to nearest in integer arithmetic).  The CTA's chunks are
 // pre-scanned for each column's largest exponent Emax_c (all-zero chunk
 // columns, whose digits are zero, carry a marker and are skipped), and
 // S 2^(E_c + E_j' - 50) is accumulated exactly as the 128-bit fixed-point
@@ -88,20 +89,17 @@ constexpr int kW5Magic = 0x4B400000;
 __device__ __forceinline__ int w5_bits(uint32_t xbits) {
     return __float_as_int(__fadd_rn(__uint_as_float(xbits), 12582912.0f));
 }
-// tc_combine's S = sum_t I_t 2^(8(5-t)) for t <= 4 plus I_5 + I_6 / 256 rounded,
-// for cells of |I_t| <= 2^22, from the biased bit patterns B_t = 0x4B400000 +
-// I_t (the FP32 -> integer conversion unit is slower than these additions):
-// the top two weights in 32 bits (the true value fits; the wrap-around of the
-// intermediate products cancels), the lower four by 64-bit multiply-adds.
-__device__ __forceinline__ long long w5_combine(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t a4,
-                                                uint32_t a5, uint32_t a6) {
-    const float t = __fmaf_rn(__uint_as_float(a6), 0.00390625f, __uint_as_float(a5));
-    const uint32_t u = (uint32_t)w5_bits(a0) * 256u + (uint32_t)w5_bits(a1) - 257u * (uint32_t)kW5Magic;
-    long long low = (long long)w5_bits(__float_as_uint(t)) - (long long)kW5Magic * (16777216ll + 65536 + 256 + 1);
-    low += (long long)w5_bits(a4) * 256;
-    low += (long long)w5_bits(a3) * 65536;
-    low += (long long)w5_bits(a2) * 16777216;
-    return (long long)((unsigned long long)(long long)(int)u << 32) + low;
+// S = sum_t I_t 2^(8(5-t)) for t <= 4, plus I_5 + I_6 / 256 rounded to nearest
+// (halves up) in integer arithmetic, from the seven exact integer weight sums
+// (|I_t| < 2^23): the top two weights in 32 bits, the lower four by 64-bit
+// multiply-adds.
+__device__ __forceinline__ long long w5_combine(const int (&I)[7]) {
+    const int u = I[0] * 256 + I[1];
+    long long low = (long long)I[5] + ((I[6] + 128) >> 8);
+    low += (long long)I[4] * 256;
+    low += (long long)I[3] * 65536;
+    low += (long long)I[2] * 16777216;
+    return (long long)((unsigned long long)(long long)u << 32) + low;
 }
 
 // a (128-bit, little-endian pair) += S 2^sh, |S| < 2^62, sh <= 48, without
@@ -119,8 +117,9 @@ __device__ __forceinline__ void w5_add2(ulonglong2& a, long long S, int sh) {
 // (1 - D, c) of quarter q ^ 2): v[t] holds this lane's part of weight t for
 // columns j0 .. j0 + 7.  The lane sends the cells of the columns its partner
 // completes (D = 0 sends the odd ones, D = 1 the even ones) through xs, takes
-// the partner's cells of its own four columns, adds them (exact: both are
-// integers and the sum is at most 7 x 64 x 2^14 < 2^24), combines and
+// the partner's cells of its own four columns, converts both cells of each
+// weight to integers (each at most 4 x 64 x 2^14 = 2^22, the exact range of
+// w5_bits; their sum can exceed it) and adds them as integers, combines and
 // accumulates.  n counts the pair's exchange rounds (x_full / x_empty phases).
 template <int D>
 __device__ __forceinline__ void w5_group(const uint32_t (&v)[7][8], float* xs, uint64_t* x_full, uint64_t* x_empty,
@@ -146,10 +145,10 @@ __device__ __forceinline__ void w5_group(const uint32_t (&v)[7][8], float* xs, u
         const int jj = 2 * h + D;
         const float4 p0 = in[(2 * h) * 32 + lane], p1 = in[(2 * h + 1) * 32 + lane];
         const float w[7] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z};
-        uint32_t I[7];
+        int I[7];
 #pragma unroll
-        for (int t = 0; t < 7; ++t) I[t] = __float_as_uint(__fadd_rn(__uint_as_float(v[t][jj]), w[t]));
-        S[h] = w5_combine(I[0], I[1], I[2], I[3], I[4], I[5], I[6]);
+        for (int t = 0; t < 7; ++t) I[t] = w5_bits(v[t][jj]) + w5_bits(__float_as_uint(w[t])) - 2 * kW5Magic;
+        S[h] = w5_combine(I);
     }
     __syncwarp();
     if (lane == 0) t5_bar_arrive(x_empty);

@@ -416,6 +416,26 @@ def test_all_cached_digit_gram_zero_chunks_far_from_unit_scale(lib):
     assert np.max(np.abs(G_rec - checks.exact_gram(V, V)) / np.outer(nv, nv)) <= 1e-13
 
 
+def test_all_cached_digit_gram_large_digit_sums(lib):
+    """Rows whose digits 1..6 all equal -128 (x = -0x808080808080 2^-53 under a
+    chunk maximum of 1, whose own digits are 32, 0, ..., 0): the weight-6 digit
+    sum of that column with itself reaches 63 x 5 x 2^14 > 2^22, beyond the
+    exact range of a single FP32-to-integer addition; the Gram still meets the
+    1e-13 bar against exact rational sums."""
+    from paper_2402_15033_gb300 import capi
+    g = synth.rng(4413)
+    n, nb = 2560, 10
+    V = g.standard_normal((n, nb)) / np.sqrt(n)
+    col = np.full(n, -float(0x808080808080) * 2.0 ** -53)
+    col[::64] = 1.0
+    V[:, 0] = col
+    _, Rg, st = run_gram_stream(capi, None, V, ld_pad=0, update=False, cached_v=True)
+    assert st == 0
+    nv = np.linalg.norm(V, axis=0)
+    G_rec = Rg.T @ Rg
+    assert np.max(np.abs(G_rec - checks.exact_gram(V, V)) / np.outer(nv, nv)) <= 1e-13
+
+
 def test_all_cached_digit_gram_exact_rationals_scaling_nan(lib):
     """Gram entries within 2^-48 of exact rational sums on hard digits; a
     power-of-two scale of V scales R exactly; a NaN in V fails its pivot; two
