@@ -123,8 +123,7 @@ FP64_PROBE_TFLOPS = 1.19                          # an FMA-chain probe on this G
 # block (k = 56) and the stage-2 panel.  Entries are removed when the kernel
 # changes after its capture.
 NCU_TRAFFIC = {
-    "tc": {"stage1_gram": 4 * (457.3 + 3.4) * 1e6, "stage1_update": 4 * (457.3 + 65.4) * 1e6,
-           "stage2_gram": 4 * (457.3 + 3.6) * 1e6, "stage2_update": 4 * (511.8 + 457.3) * 1e6},
+    "tc": {"stage1_gram": 4 * (457.3 + 3.4) * 1e6},
     "fp64": {"stage1_gram": 4 * (511.8 + 3.2) * 1e6, "stage2_gram": 4 * (514.7 + 3.5) * 1e6},
 }
 

@@ -207,16 +207,8 @@ __device__ inline void pip_finish(int k, int nb, int g, int groups, int G, doubl
         if (!needed(c, j, k)) continue;
         const double* p = partial0 + e;
         double acc = 0.0;
-        // in slot order; sixteen loads in flight per thread (the slots sit in L2)
-        int bb = 0;
-        for (; bb + 16 <= G; bb += 16) {
-            double x[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) x[q] = __ldcg(p + (size_t)(bb + q) * ps);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) acc += x[q];
-        }
-        for (; bb < G; ++bb) acc += __ldcg(p + (size_t)bb * ps);
+#pragma unroll 8
+        for (int bb = 0; bb < G; ++bb) acc += __ldcg(p + (size_t)bb * ps);
         gram[c + (size_t)j * kx] = acc;
     }
     __threadfence();
